@@ -1,0 +1,381 @@
+#!/usr/bin/env python3
+"""Throughput of the 3D XY sweep path on B300: spin updates per ns.
+
+Headline workload (one GPU): a 160^3 periodic lattice, one replica,
+beta = 0.4542, sweeps of 1 Metropolis + 5 over-relaxation passes, the
+lattice sums measured every 10 sweeps.  One step = 10 sweeps + the fused
+measurement = 10 * 6 * 160^3 = 245,760,000 spin updates.  The lattice
+(16.4 MB) is smaller than L2, so L2 is flushed (a 256 MB write) before every
+timed step, outside its CUDA-event bracket.
+
+Also reported (extra keys): the batched parallel-tempering workload (64^3 x
+32 replicas, 1 + 3 passes, exchange every sweep) in one persistent
+cooperative launch vs the plain per-replica launch loop, the ragged batch,
+and reweighting throughput.
+
+--impl reference runs the FP64 CPU oracle (the reference arm of this build)
+on the host cores, on bounded samples of the same workload.
+
+Under torchrun every rank runs an independent replica (the path has no
+exchange between GPUs); rank 0 prints one JSON line.
+"""
+
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+SEED = 0x5EED2012
+L_MAIN, BETA_MAIN, NM_MAIN, NOR_MAIN, SWEEPS_PER_STEP = 160, 0.4542, 1, 5, 10
+UPDATES_PER_STEP = SWEEPS_PER_STEP * (NM_MAIN + NOR_MAIN) * L_MAIN ** 3
+METRIC = "XY spin updates/ns at L=160, plain vs batched PT; % of HBM/SFU roofline"
+UNIT = "spin updates/ns"
+WORKLOAD = ("160^3 periodic XY lattice, 1 replica, beta=0.4542, sweep = 1 Metropolis + 5 "
+            "over-relaxation passes, lattice sums every 10 sweeps; step = 10 sweeps")
+# Algorithmic bytes of one site update: read own angle 4 B, write it 4 B,
+# read the other colour once 4 B (halo re-reads excluded).
+BYTES_PER_UPDATE = 12
+
+
+def dist_env():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d.get("hbm_gbs", 6400.0)), "measured"
+    return 6400.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def allreduce_max(value: float, world: int) -> float:
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+# ---------------------------------------------------------------- CPU oracle
+
+def oracle_rate(seconds: float, threads: int | None = None):
+    """FP64 oracle on the host cores: 160^3 sweeps (1 + 5 passes) until about
+    `seconds` have passed.  Returns (updates/ns, threads, sweeps)."""
+    import oracle
+    n = threads or os.cpu_count() or 1
+    oracle.set_threads(n)
+    th = oracle.init_uniform((L_MAIN,) * 3, SEED, 0)
+    done, elapsed = 0, 0.0
+    mpass = 0
+    while elapsed < seconds or done == 0:
+        t0 = time.perf_counter()
+        oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, 1, 0)
+        elapsed += time.perf_counter() - t0
+        done += 1
+        mpass += NM_MAIN
+    upd = done * (NM_MAIN + NOR_MAIN) * L_MAIN ** 3
+    return upd / (elapsed * 1e9), n, done
+
+
+def run_reference(args):
+    world, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    n = os.cpu_count() or 1
+    oracle.set_threads(n)
+    th = oracle.init_uniform((L_MAIN,) * 3, SEED, 0)
+    mpass = 0
+    for _ in range(args.warmup):
+        oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, 1, 0)
+        mpass += NM_MAIN
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, 1, 1)
+        times.append(time.perf_counter() - t0)
+        mpass += NM_MAIN
+    upd = (NM_MAIN + NOR_MAIN) * L_MAIN ** 3
+    total = sum(times)
+    value = args.steps * upd / (total * 1e9)
+    sample = f"{args.steps} sweeps (1 Metropolis + 5 over-relaxation passes) of the 160^3 lattice, one per step"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD + " (reference step = 1 sweep)"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+
+def time_kernel(fn, stream, n, warm=5):
+    import torch
+    for _ in range(warm):
+        fn()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    torch.cuda.synchronize()
+    for a, b in evs:
+        a.record(stream)
+        fn()
+        b.record(stream)
+    torch.cuda.synchronize()
+    return sum(a.elapsed_time(b) for a, b in evs) / n  # ms
+
+
+def bench_pt(steps: int, warmup: int):
+    """64^3 x 32 replicas, beta in [0.450, 0.458], 1 + 3 passes, exchange
+    every sweep: persistent cooperative launch vs the plain per-replica
+    launch loop (one context per replica, kernels issued replica by
+    replica)."""
+    import torch
+    from paper_1211_0780_b300 import xy
+    L, R, sweeps = 64, 32, 10
+    betas = np.linspace(0.450, 0.458, R)
+    upd = sweeps * 4 * R * L ** 3
+    st = torch.cuda.current_stream()
+    s = xy.Simulation(L, R, betas, SEED, series_capacity=4 * sweeps * (steps + warmup + 2))
+    s.autotune(1, 3)
+    s.set_exec(xy.EXEC_PERSISTENT)
+    for _ in range(warmup):
+        s.sweep(1, 3, sweeps, measure_every=1, pt_swap_every=1)
+        s.read_series()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(st)
+    for _ in range(steps):
+        s.sweep(1, 3, sweeps, measure_every=1, pt_swap_every=1)
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_p = e0.elapsed_time(e1) / steps
+    s.read_series()
+    tiles = s.get_tile(0)
+    # plain loop: one context per replica, kernel-by-kernel launches
+    reps = [xy.Simulation(L, 1, [b], SEED + i) for i, b in enumerate(betas)]
+    for r in reps:
+        r.set_tile(0, *tiles)
+    def one_step():
+        for _ in range(sweeps):
+            for r in reps:
+                r.sweep(1, 3, 1)
+    for _ in range(warmup):
+        one_step()
+    torch.cuda.synchronize()
+    e0.record(st)
+    for _ in range(max(1, steps // 2)):
+        one_step()
+    e1.record(st)
+    torch.cuda.synchronize()
+    ms_l = e0.elapsed_time(e1) / max(1, steps // 2)
+    return {"workload": "64^3 x 32 replicas, beta=linspace(0.450,0.458,32), 1+3 passes, exchange+measure every sweep",
+            "batched_persistent": upd / (ms_p * 1e6), "plain_per_replica_loop": upd / (ms_l * 1e6),
+            "unit": UNIT, "tile": list(tiles), "ms_per_10_sweeps_persistent": ms_p}
+
+
+def run_gpu(args):
+    import torch
+    from paper_1211_0780_b300 import xy
+    world, rank, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.cuda.current_device()
+    st = torch.cuda.current_stream()
+    sim = xy.Simulation(L_MAIN, 1, [BETA_MAIN], SEED + rank, series_capacity=args.steps + args.warmup + 4)
+    tile = sim.autotune(NM_MAIN, NOR_MAIN)[0]
+    sim.set_exec(xy.EXEC_GRAPH)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def step():
+        sim.sweep(NM_MAIN, NOR_MAIN, SWEEPS_PER_STEP, measure_every=SWEEPS_PER_STEP)
+
+    for _ in range(args.warmup):
+        flush.zero_()
+        step()
+    sim.read_series()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(dev)
+    clocks.start()
+    time.sleep(0.3)
+    for a, b in evs:
+        flush.zero_()
+        a.record(st)
+        step()
+        b.record(st)
+    torch.cuda.synchronize()
+    barrier(world)
+    clk = clocks.stop()
+    ms_local = sum(a.elapsed_time(b) for a, b in evs)
+    ms_total = allreduce_max(ms_local, world)
+    recs = sim.read_series()
+    assert len(recs) == args.steps and np.all(np.isfinite(recs["E"]))
+    value = world * args.steps * UPDATES_PER_STEP / (ms_total * 1e6)
+    launches_per_step = SWEEPS_PER_STEP * (NM_MAIN + NOR_MAIN) * 2 + 2  # half-sweeps + finish + advance
+
+    # --- per-kernel durations (CUDA events on the launching stream) ----------
+    ms_or = time_kernel(lambda: sim.overrelax_half(1), st, 60)
+    ms_met = time_kernel(lambda: sim.metropolis_half(0, 1 << 40), st, 60)
+    half = L_MAIN ** 3 // 2
+    hbm, src = measured_peaks()
+    ach = BYTES_PER_UPDATE * half / (ms_or * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(prof):
+        with open(prof) as f:
+            traffic = json.load(f).get("overrelax_L160_bytes_per_launch")
+    roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
+                "traffic": traffic, "kernel": "k_half<over-relaxation>, 160^3 half-sweep",
+                "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
+                "note": "12 B/update algorithmic; lattice is L2-resident (16.4 MB < 126 MB)"}
+    kernels = {"overrelax_half_ms": ms_or, "metropolis_half_ms": ms_met,
+               "overrelax_updates_per_ns": half / (ms_or * 1e6), "metropolis_updates_per_ns": half / (ms_met * 1e6)}
+
+    # --- end to end through the C-ABI with host buffers --------------------
+    pinned = torch.empty(sim.n_angles(), dtype=torch.float32, pin_memory=True)
+    sim.get_packed(pinned)
+    e2e_steps = max(3, args.steps // 2)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        sim.set_packed(pinned)   # H2D of the step's input state (pinned)
+        step()
+        r = sim.read_series()    # D2H of the step's measurement (synchronises)
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": world * e2e_steps * UPDATES_PER_STEP / (t_e2e * 1e9), "unit": UNIT,
+           "h2d_bytes_per_step": int(sim.n_angles() * 4), "d2h_bytes_per_step": int(r.nbytes)}
+
+    extras = {}
+    if not args.no_extras and rank == 0:
+        try:
+            extras["batched_pt"] = bench_pt(max(3, args.steps // 2), 2)
+        except Exception as exc:  # report, do not hide
+            extras["batched_pt"] = {"error": repr(exc)}
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        v, n, done = oracle_rate(args.cpu_seconds)
+        cpu = {"value": v, "unit": UNIT, "cores": n, "kind": "oracle",
+               "sample": f"{done} sweeps (1+5 passes) of the 160^3 lattice, FP64, OpenMP over sites"}
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "L": L_MAIN, "replicas": 1, "beta": BETA_MAIN,
+                       "sweeps_per_step": SWEEPS_PER_STEP, "updates_per_step": UPDATES_PER_STEP,
+                       "tile": list(tile), "exec": "cuda graph of half-sweep kernels",
+                       "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas only x{world}"},
+            "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
+            "gpu_launches": args.steps * launches_per_step,
+        }
+        line.update(extras)
+        print(json.dumps(line))
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,274 @@
+/*
+ * libxy -- B300-native (sm_103a) hot path of the 3D XY Monte Carlo method of
+ * Lan, Hsieh & Kao, "High-precision Monte Carlo study of the
+ * three-dimensional XY model on GPU" (arXiv:1211.0780): checkerboard
+ * Metropolis and over-relaxation sweeps of classical O(2) spins on periodic
+ * L x L x L cubic lattices, run across parallel-tempering replicas, with the
+ * energy, magnetisation and helicity sums fused into the sweep, plus FP64
+ * single-histogram reweighting of the measured series.
+ *
+ * Conventions (every entry point):
+ *   - Returns an int status (XY_OK or a negative XY_ERR_*); never throws.
+ *   - Host pointers are plain host memory owned by the caller and are only
+ *     read or written during the call.  Device pointers (d_*) are owned by
+ *     the caller and must stay valid for as long as the library uses them.
+ *   - The library allocates no device memory: all device state lives in the
+ *     caller's workspace (xy_workspace_bytes) handed to xy_init.
+ *   - Work is ordered on the stream given to xy_init (a cudaStream_t passed
+ *     as void*; NULL = the legacy default stream).  Calls that return host
+ *     data synchronise that stream.
+ *   - Errors are sticky per context: after XY_ERR_CUDA or XY_ERR_TIMEOUT
+ *     every call on the context returns XY_ERR_STATE until xy_destroy.
+ *   - Angles are FP32 radians in [0, 2 pi).
+ *
+ * Lattice, colours and layout.  Site (x, y, z), 0 <= x, y, z < L, has colour
+ * c = (x + y + z) mod 2 (0 = "black", 1 = "white"; Sec. II, Fig. 2).  L must
+ * be a multiple of 8 (8 <= L <= 1024).  Host-side angle arrays use the
+ * natural layout theta[x + L (y + L z)]; on the device each colour is a
+ * separate packed array indexed p = (x >> 1) + (L/2)(y + L z).
+ *
+ * Random numbers.  Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) with
+ * key = (seed & 0xffffffff, seed >> 32).  The site with packed index p and
+ * colour c of global slot g draws from the call with counter
+ *   (p >> 1, count & 0xffffffff, count >> 32, g << 4 | c << 3 | tag),
+ * taking words 0 and 1 if p is even, 2 and 3 if p is odd; a word w maps to
+ * u = (w >> 8) 2^-24 in [0, 1).  tag 1 = initial state (count 0, theta =
+ * 2 pi u of the first word), tag 2 = Metropolis (count = the Metropolis-pass
+ * counter; first word -> proposal, second -> acceptance).  Exchange draws
+ * use counter (k, n & 0xffffffff, n >> 32, ladder << 4 | 3), word 0, for
+ * pair k of exchange event n.
+ *
+ * Slots and ladders.  xy_init takes n_lattices lattices; lattice l has edge
+ * L[l] and n_replicas[l] replicas ("slots"), numbered globally (lattice 0's
+ * first).  Each lattice is one parallel-tempering ladder whose betas are
+ * given in ascending order; initially the k-th replica sits at the k-th
+ * beta.  An exchange swaps beta labels (a permutation), not configurations.
+ */
+#ifndef XY_H
+#define XY_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  XY_OK = 0,
+  XY_ERR_ARG = -1,     /* invalid argument; nothing was done             */
+  XY_ERR_CUDA = -2,    /* a CUDA call failed; the context is now unusable */
+  XY_ERR_TIMEOUT = -3, /* a bounded device-side wait ran out (grid barrier) */
+  XY_ERR_STATE = -4,   /* the context is in a sticky error state          */
+  XY_ERR_NOMEM = -5    /* workspace or series buffer too small            */
+};
+
+/* Execution modes of xy_sweep. */
+enum {
+  XY_EXEC_PLAIN = 0,      /* one kernel launch per half-sweep per lattice          */
+  XY_EXEC_GRAPH = 1,      /* the same launches captured once into a CUDA graph     */
+  XY_EXEC_PERSISTENT = 2  /* one cooperative launch runs every pass of every
+                             lattice and replica, the measurement and the exchange;
+                             captured into a CUDA graph                            */
+};
+
+typedef struct xy_ctx xy_ctx; /* opaque; owned by the library */
+
+/* One measurement of one slot: the lattice sums behind the estimators of
+ * Sec. II, Eqs. (4)-(6).  E = -sum_<ij> cos(theta_i - theta_j) (Eq. 1);
+ * (Mx, My) = sum_i (cos theta_i, sin theta_i); C[mu] and S[mu] = the sums
+ * over bonds (i, i + mu) of cos and sin of (theta_i - theta_{i+mu}).  Then
+ * m = sqrt(Mx^2 + My^2) / N (Eq. 4) and rho_s = (1/3N) sum_mu (C[mu] -
+ * beta S[mu]^2) (Eq. 6). */
+typedef struct xy_record {
+  double E;
+  double Mx, My;
+  double C[3];
+  double S[3];
+  double beta;        /* the beta of the slot when measured            */
+  int32_t slot;       /* global slot                                    */
+  int32_t beta_index; /* position of that beta in its ladder           */
+  uint64_t sweep;     /* 0-based index of the sweep just completed      */
+} xy_record;          /* 96 bytes                                       */
+
+/* Bytes of device workspace xy_init needs for these lattices and a series
+ * buffer of `series_capacity` measurement events (each event holds one
+ * record per slot).  Returns 0 for invalid arguments. */
+size_t xy_workspace_bytes(int n_lattices, const int *L, const int *n_replicas,
+                          int64_t series_capacity);
+
+/* Creates a context over caller-owned device memory `d_workspace` (at least
+ * xy_workspace_bytes, 256-byte aligned; it must outlive the context) and
+ * writes the initial state: theta = 2 pi u from the initial-state stream,
+ * uniform in [0, 2 pi) as in the hot start of the benchmark configurations.
+ * `betas` holds sum(n_replicas) inverse temperatures, lattice by lattice,
+ * each lattice's ascending.  The paper's single-lattice call
+ * xy_init(L, betas, seed) is n_lattices = 1.  `stream` is a cudaStream_t or
+ * NULL.  Errors: XY_ERR_ARG (L not a multiple of 8 or out of range, a
+ * non-positive replica count, betas not finite or not ascending, NULL
+ * pointers), XY_ERR_NOMEM (ws_bytes too small), XY_ERR_CUDA. */
+int xy_init(xy_ctx **out, int n_lattices, const int *L, const int *n_replicas,
+            const double *betas, uint64_t seed, void *d_workspace,
+            size_t ws_bytes, int64_t series_capacity, void *stream);
+
+/* Releases the context (not the workspace).  Safe on NULL. */
+int xy_destroy(xy_ctx *ctx);
+
+/* Selects how xy_sweep issues its work (XY_EXEC_*).  All modes give
+ * bit-identical states and records. */
+int xy_set_exec(xy_ctx *ctx, int mode);
+
+/* Runs n_sweeps sweeps on every slot (Sec. II: "one Monte Carlo step").
+ * One sweep = n_metropolis Metropolis passes then n_overrelax
+ * over-relaxation passes; a pass is a black half-sweep then a white one.
+ * After sweep s (0-based, counted over the context's life):
+ *   - if measure_every > 0 and (s + 1) % measure_every == 0, one record per
+ *     slot is appended to the series buffer (fused into the last white
+ *     half-sweep);
+ *   - if pt_swap_every > 0 and (s + 1) % pt_swap_every == 0, one exchange
+ *     event runs on every ladder with the energies of the final state
+ *     (Sec. II, Eq. 3), alternating even and odd pairs between events.
+ * Metropolis half-sweep (Sec. II): each site of the colour proposes
+ * theta' = 2 pi u0 and accepts iff u1 < exp(-beta dE), with dE = -[h_x
+ * (cos theta' - cos theta) + h_y (sin theta' - sin theta)] and h the sum of
+ * the six neighbour spin vectors.  Over-relaxation half-sweep (Eq. 2): the
+ * spin is reflected about its local field, theta' = 2 atan2(h_y, h_x) -
+ * theta (mod 2 pi); h = 0 leaves it.  Errors: XY_ERR_ARG (negative counts,
+ * n_metropolis + n_overrelax == 0 with n_sweeps > 0), XY_ERR_NOMEM (the
+ * series buffer would overflow: read it first), XY_ERR_TIMEOUT, XY_ERR_CUDA. */
+int xy_sweep(xy_ctx *ctx, int n_metropolis, int n_overrelax, int n_sweeps,
+             int measure_every, int pt_swap_every);
+
+/* One Metropolis half-sweep of `colour` on every slot with Metropolis-pass
+ * counter `mpass` (the counters of the context are not advanced). */
+int xy_metropolis_half(xy_ctx *ctx, int colour, uint64_t mpass);
+
+/* One over-relaxation half-sweep of `colour` on every slot (Eq. 2). */
+int xy_overrelax_half(xy_ctx *ctx, int colour);
+
+/* Measures the current state of every slot (Eqs. 4-6 sums) into
+ * host_out[total slots]; synchronises the stream. */
+int xy_measure(xy_ctx *ctx, xy_record *host_out);
+
+/* One exchange event on every ladder (Eq. 3) with freshly measured
+ * energies: pairs (k, k+1), k = parity, parity + 2, ...; accept with
+ * min[1, exp((beta_k - beta_{k+1})(E_k - E_{k+1}))] where E_k is the energy
+ * of the slot at beta_k.  Uses and advances the exchange-event counter.
+ * *n_accepted_out (nullable) receives the number of accepted swaps over all
+ * ladders; synchronises the stream. */
+int xy_pt_swap(xy_ctx *ctx, int parity, int *n_accepted_out);
+
+/* Copies the records appended since the last read (oldest first) into
+ * host_buf (room for `cap` records) and empties the buffer.  *n_out = the
+ * number copied.  XY_ERR_NOMEM if cap is too small (nothing is copied). */
+int xy_read_series(xy_ctx *ctx, xy_record *host_buf, int64_t cap,
+                   int64_t *n_out);
+
+/* Number of records waiting in the series buffer. */
+int xy_series_count(xy_ctx *ctx, int64_t *n_out);
+
+/* State for parity checks and checkpoints.  host_angles: all slots
+ * concatenated, natural layout, sum over slots of L^3 floats.  perm: for
+ * each ladder in order, n_replicas entries (beta index -> local slot).
+ * counters[4] = {Metropolis passes, sweeps, exchange events, records}.
+ * Any pointer may be NULL to skip that part.  Because every draw is a pure
+ * function of (seed, counters, slot, site), set_state(get_state()) resumes
+ * a run bit-exactly. */
+int xy_get_state(xy_ctx *ctx, float *host_angles, int32_t *perm,
+                 uint64_t *counters);
+int xy_set_state(xy_ctx *ctx, const float *host_angles, const int32_t *perm,
+                 const uint64_t *counters);
+
+/* The angles of every slot in the device's packed layout (for each slot:
+ * colour 0's N/2 floats then colour 1's, p = (x >> 1) + (L/2)(y + L z)),
+ * copied stream-ordered between the workspace and a host buffer of
+ * sum over slots of L^3 floats (pinned memory makes the copy asynchronous;
+ * the call returns after it completes).  Checkpoints and host round trips
+ * without the layout conversion of xy_get_state / xy_set_state. */
+int xy_get_packed(xy_ctx *ctx, float *host_packed);
+int xy_set_packed(xy_ctx *ctx, const float *host_packed);
+
+/* Accepted-move counters: met[total slots] = accepted Metropolis proposals
+ * per slot; swap[total slots] = accepted exchanges per ladder pair (entry
+ * slot0(l) + k for pair (k, k+1) of ladder l).  Either may be NULL. */
+int xy_get_accepts(xy_ctx *ctx, uint64_t *met, uint64_t *swap);
+
+/* Raw Philox words of every site of one colour of slot `slot` for stream
+ * `tag` and counter `count`, natural order of those sites (x fastest), two
+ * words per site, drawn on the device by the same code the sweeps use. */
+int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
+                   uint32_t *host_words);
+
+/* Tile shape of lattice `lattice`: the kernels cover ty rows x tz planes per
+ * thread block (full rows in x).  xy_set_tile checks 1 <= ty, tz <= L,
+ * (L/8) * ty <= the kernels' maximum block size (512 on sm_103a at their
+ * register use) and that the tile count fits the partial-sum area
+ * (ceil(L/ty) ceil(L/tz) <= L^2/4); angles do not depend on the tile shape
+ * (lattice sums only through FP64 summation order). */
+int xy_set_tile(xy_ctx *ctx, int lattice, int ty, int tz);
+int xy_get_tile(xy_ctx *ctx, int lattice, int *ty, int *tz);
+
+/* Picks each lattice's tile shape by timing candidate shapes on the
+ * device for `n_metropolis`/`n_overrelax` sweeps (the state is saved and
+ * restored); the choice is cached in the context.  Returns the cost. */
+int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
+
+/* Device-side status word of the last persistent launch (0 = fine). */
+int xy_device_status(xy_ctx *ctx, int *status_out);
+
+/* Test hook for the bounded grid barrier: runs one persistent launch whose
+ * barrier expects one more block than the grid has, so every wait runs out
+ * after `budget_us` microseconds and the kernel returns XY_ERR_TIMEOUT
+ * through the status word without hanging.  The context stays usable (the
+ * timeout is reported, not made sticky).  No GPU fault is involved. */
+int xy_debug_barrier_timeout(xy_ctx *ctx, int budget_us, int *status_out);
+
+/* Human-readable text of a status code. */
+const char *xy_strerror(int status);
+
+/* ------------------------------------------------------------------------
+ * Single-histogram reweighting (Ferrenberg-Swendsen; not in the paper,
+ * which bins the series on the host, Sec. II).  For a series of T samples
+ * measured at beta0 and targets beta'_k (k < K):
+ *   l_kt = -(beta'_k - beta0) E_t,   log Z_k = log sum_t exp(l_kt),
+ *   <O>_k = sum_t exp(l_kt - log Z_k) O_t,
+ * for O in {E, m2, m4, csum = sum_mu c_mu, s2sum = sum_mu s2_mu}, where
+ * m2 = (|M|/N)^2, m4 = m2^2, c_mu = C_mu / N, s2_mu = S_mu^2 / N.  Derived:
+ *   U_L(beta')   = 1 - <m4> / (3 <m2>^2)               (Eq. 5)
+ *   rho_s L      = L/3 (<csum> - beta' <s2sum>)         (Eq. 6 scaled by L
+ *                                                        as in Eq. 8)
+ * and their d/dbeta' from d<O>/dbeta' = -(<O E> - <O><E>).
+ * All arithmetic is FP64.  Device pointers; layout:
+ *   d_E[T] f64, d_m2[T] f32, d_m4[T] f32, d_c[3][T] f32, d_s2[3][T] f32,
+ *   d_betap[K] f64.
+ * Outputs (device, f64):
+ *   d_out[7][K]  = rows {logZ, <E>, <m2>, <m4>, <csum>, <s2sum>, unused 0}
+ *                  then the caller derives nothing: rows 5.. are documented
+ *                  in the Python binding;
+ *   d_obs[2][K]  = {U_L, rho_s L};
+ *   d_cov[5][K]  = {var E, cov(m2,E), cov(m4,E), cov(csum,E), cov(s2sum,E)}.
+ * d_scratch: xy_reweight_scratch_bytes(T, K) bytes of caller-owned device
+ * memory.  Errors: XY_ERR_ARG (T < 2, K < 1, L < 1, NULL pointers,
+ * non-finite beta0), XY_ERR_NOMEM (scratch too small), XY_ERR_CUDA. */
+size_t xy_reweight_scratch_bytes(int64_t T, int K);
+
+int xy_reweight_forward(int64_t T, const double *d_E, const float *d_m2,
+                        const float *d_m4, const float *d_c, const float *d_s2,
+                        double beta0, int K, const double *d_betap, int L,
+                        double *d_out, double *d_obs, double *d_cov,
+                        void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* Backward: given upstream gradients g_U[K] and g_rhoL[K] (device f64) and
+ * the forward's d_out, d_cov, returns grad_betap[K] = g_U dU/dbeta' +
+ * g_rhoL d(rho_s L)/dbeta' (each output depends only on its own beta'_k).
+ * d_dobs[2][K] (nullable) receives {dU/dbeta', d(rho_s L)/dbeta'}. */
+int xy_reweight_backward(int K, const double *d_betap, int L,
+                         const double *d_out, const double *d_cov,
+                         const double *d_gU, const double *d_grhoL,
+                         double *d_grad_betap, double *d_dobs, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XY_H */

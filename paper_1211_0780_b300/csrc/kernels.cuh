@@ -1,0 +1,197 @@
+// Kernels of the sweep path: initial state, one half-sweep per launch,
+// the deterministic FP64 finishing reduction with the record append and the
+// on-device replica exchange (Sec. II, Eq. 3), the counter advance and the
+// Philox draw dump used by the parity tests.
+#pragma once
+#include <cstdint>
+
+#include "../../include/xy.h"
+#include "philox.cuh"
+#include "sweep.cuh"
+
+namespace xy {
+
+static_assert(sizeof(xy_record) == 96, "xy_record layout");
+
+// theta = 2 pi u from the initial-state stream; one Philox call per packed
+// pair (2q, 2q+1) of one colour of one slot.
+__global__ void k_init(Lattice lat, uint64_t seed) {
+  const long long N = static_cast<long long>(lat.L) * lat.L * lat.L;
+  const long long Q = N >> 2;  // pairs per colour
+  const long long total = static_cast<long long>(lat.R) * 2 * Q;
+  const PhiloxKey key = philox_key(seed);
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(i / (2 * Q));
+    const int c = static_cast<int>((i / Q) & 1);
+    const uint32_t q = static_cast<uint32_t>(i % Q);
+    const uint32_t tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) |
+                          (static_cast<uint32_t>(c) << 3) | kTagInit;
+    const uint4 w = philox4x32_10(make_uint4(q, 0u, 0u, tagw), key);
+    float* a = lat.angles + r * N + c * (N >> 1) + 2 * static_cast<long long>(q);
+    *reinterpret_cast<float2*>(a) = make_float2(u24(w.x) * kTwoPi, u24(w.z) * kTwoPi);
+  }
+}
+
+// One half-sweep of one lattice: grid (tiles per slot, R), block (L/8, ty).
+template <int MODE>
+__global__ void k_half(Lattice lat, int colour, PassParams pp) {
+  extern __shared__ __align__(16) float sm[];
+  const int r = blockIdx.y;
+  const int t = blockIdx.x;
+  const int yt = t % lat.nyt, zt = t / lat.nyt;
+  float acc[kNumSums];
+#pragma unroll
+  for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
+  uint32_t n_acc = 0u;
+  tile_pass<MODE>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
+  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+  const int nth = blockDim.x * blockDim.y;
+  if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);
+  if (MODE == kMeasureOnly || (pp.measure && colour == 1)) {
+    double* red = reinterpret_cast<double*>(sm + tile_plane_floats(lat.L, lat.ty));
+    const long long part = lat.part0 + static_cast<long long>(r) * lat.nyt * lat.nzt + t;
+    block_sums_to(pp.partials + part * kNumSums, acc, tid, nth, red);
+  }
+}
+
+struct FinishParams {
+  const double* partials;
+  double* sums_slot;            // [slots][kNumSums]
+  double* E_slot;               // [slots]
+  const uint64_t* ctr;
+  uint64_t sweep_off;           // record sweep index = ctr[kCtrSweep] + sweep_off
+  uint64_t series_off;          // record event = ctr[kCtrSeries] + series_off
+  uint64_t swap_off;            // exchange event = ctr[kCtrSwap] + swap_off
+  xy_record* series;
+  int n_slots;
+  int record;
+  int swap;
+  int parity;                   // < 0: the event counter's parity
+  int* perm;                    // [slots]: ladder l's entries at slot0(l) + k
+  const double* ladder_beta;    // [slots]: ascending betas of each ladder
+  float* beta_slot;             // [slots]
+  double* beta_slot64;          // [slots]
+  int* bidx_slot;               // [slots]
+  unsigned long long* acc_swap; // [slots]
+  uint64_t seed;
+  int* n_swapped;               // nullable
+};
+
+// Finishing step of one lattice, run by one whole block: fixed-order FP64
+// sum of the tile partials of each slot (lane-strided sequential sums, then
+// a fixed shuffle tree), the record, then the exchange of Eq. (3) on the
+// ladder by one thread.  Partials are read through L2 because the
+// persistent kernel's other blocks wrote them in the same launch.
+__device__ void finish_lattice(const Lattice& lat, int l, const FinishParams& fp) {
+  const int ntile = lat.nyt * lat.nzt;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int r = warp; r < lat.R; r += nw) {
+    const double* P = fp.partials + (static_cast<long long>(lat.part0) + static_cast<long long>(r) * ntile) * kNumSums;
+    double v[kNumSums];
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) v[j] = 0.0;
+    for (int t = lane; t < ntile; t += 32) {
+#pragma unroll
+      for (int j = 0; j < kNumSums; ++j) v[j] += __ldcg(P + t * kNumSums + j);
+    }
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) {
+#pragma unroll
+      for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
+    }
+    if (lane == 0) {
+      const int g = lat.slot0 + r;
+      for (int j = 0; j < kNumSums; ++j) fp.sums_slot[g * kNumSums + j] = v[j];
+      const double E = -(v[2] + v[3] + v[4]);
+      fp.E_slot[g] = E;
+      if (fp.record) {
+        const uint64_t ev = fp.ctr[kCtrSeries] + fp.series_off;
+        xy_record rec;
+        rec.E = E;
+        rec.Mx = v[0];
+        rec.My = v[1];
+        for (int mu = 0; mu < 3; ++mu) {
+          rec.C[mu] = v[2 + mu];
+          rec.S[mu] = v[5 + mu];
+        }
+        rec.beta = fp.beta_slot64[g];
+        rec.slot = g;
+        rec.beta_index = fp.bidx_slot[g];
+        rec.sweep = fp.ctr[kCtrSweep] + fp.sweep_off;
+        fp.series[ev * fp.n_slots + g] = rec;
+      }
+    }
+  }
+  __syncthreads();
+  if (fp.swap && threadIdx.x == 0) {
+    const uint64_t n = fp.ctr[kCtrSwap] + fp.swap_off;
+    const int par = fp.parity < 0 ? static_cast<int>(n & 1ull) : (fp.parity & 1);
+    const PhiloxKey key = philox_key(fp.seed);
+    const uint32_t tagw = (static_cast<uint32_t>(l) << 4) | kTagPt;
+    const int s0 = lat.slot0;
+    int count = 0;
+    for (int k = par; k + 1 < lat.R; k += 2) {
+      const int a = fp.perm[s0 + k], b = fp.perm[s0 + k + 1];
+      const double bk = fp.ladder_beta[s0 + k], bk1 = fp.ladder_beta[s0 + k + 1];
+      const double expo = (bk - bk1) * (fp.E_slot[s0 + a] - fp.E_slot[s0 + b]);
+      const uint4 w = philox4x32_10(
+          make_uint4(static_cast<uint32_t>(k), static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32), tagw), key);
+      const double thr = expo >= 0.0 ? 1.0 : exp(expo);
+      if (u24d(w.x) < thr) {
+        fp.perm[s0 + k] = b;
+        fp.perm[s0 + k + 1] = a;
+        fp.beta_slot[s0 + b] = static_cast<float>(bk);
+        fp.beta_slot64[s0 + b] = bk;
+        fp.bidx_slot[s0 + b] = k;
+        fp.beta_slot[s0 + a] = static_cast<float>(bk1);
+        fp.beta_slot64[s0 + a] = bk1;
+        fp.bidx_slot[s0 + a] = k + 1;
+        fp.acc_swap[s0 + k] += 1ull;
+        ++count;
+      }
+    }
+    if (fp.n_swapped) atomicAdd(fp.n_swapped, count);
+  }
+  __syncthreads();
+}
+
+// One block per lattice.
+__global__ void k_finish(const Lattice* lats, FinishParams fp) {
+  finish_lattice(lats[blockIdx.x], blockIdx.x, fp);
+}
+
+__global__ void k_advance(uint64_t* ctr, uint64_t d_mpass, uint64_t d_sweep, uint64_t d_swap,
+                          uint64_t d_records, uint64_t d_series) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    ctr[kCtrMpass] += d_mpass;
+    ctr[kCtrSweep] += d_sweep;
+    ctr[kCtrSwap] += d_swap;
+    ctr[kCtrRecords] += d_records;
+    ctr[kCtrSeries] += d_series;
+  }
+}
+
+// Raw words of every site of one colour of local slot r, natural order of
+// those sites (x fastest), two per site.
+__global__ void k_draws(Lattice lat, int r, int colour, uint32_t tag, uint64_t count,
+                        uint64_t seed, uint32_t* out) {
+  const int L = lat.L, H = L >> 1;
+  const long long half = static_cast<long long>(L) * L * L / 2;
+  const PhiloxKey key = philox_key(seed);
+  const uint32_t tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) |
+                        (static_cast<uint32_t>(colour) << 3) | (tag & 7u);
+  for (long long n = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; n < half;
+       n += static_cast<long long>(gridDim.x) * blockDim.x) {
+    // n-th site of this colour in natural order: row (y, z) = n / H, k = n % H.
+    const long long row = n / H;
+    const int k = static_cast<int>(n % H);
+    const long long p = row * H + k;  // packed index equals the order index
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(p >> 1), static_cast<uint32_t>(count),
+                                             static_cast<uint32_t>(count >> 32), tagw), key);
+    out[2 * n] = (p & 1) ? w.z : w.x;
+    out[2 * n + 1] = (p & 1) ? w.w : w.y;
+  }
+}
+
+}  // namespace xy

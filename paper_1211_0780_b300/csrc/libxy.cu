@@ -1,0 +1,1084 @@
+// libxy: the C-ABI of the XY sweep path (declared in include/xy.h).
+//
+// Host-side responsibilities: validate arguments, carve the caller's device
+// workspace, issue the half-sweep kernels in the sweep schedule (plain
+// launches, a captured CUDA graph, or one persistent cooperative launch),
+// keep host mirrors of the device counters, and marshal state between the
+// natural host layout and the packed device layout.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <numeric>
+#include <tuple>
+#include <vector>
+
+#include "../../include/xy.h"
+#include "kernels.cuh"
+#include "persistent.cuh"
+
+using namespace xy;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct LatHost {
+  int L, R, slot0;
+  int ty, tz;
+  size_t angle_off;  // floats from the angle base
+  int part0;         // first partial slot
+  int part_cap;      // partial slots reserved per slot
+  long long N() const { return static_cast<long long>(L) * L * L; }
+  int nyt() const { return (L + ty - 1) / ty; }
+  int nzt() const { return (L + tz - 1) / tz; }
+};
+
+// Partial capacity per slot: tiles of at least 4 sites x rows x planes.
+int part_cap_for(int L) { return std::max(1, (L * L) / 4); }
+
+struct Layout {
+  size_t angles, ladder_beta, perm, beta_slot, beta_slot64, bidx_slot, E_slot, sums_slot, partials,
+      acc_met, acc_swap, ctr, status, barrier, nswapped, lats, staging, plan_items, plan_offs,
+      series, total;
+};
+
+constexpr int kMaxPlanBlocks = 8192;
+
+bool valid_lattices(int n, const int* L, const int* R) {
+  if (n <= 0 || n > 4096 || !L || !R) return false;
+  for (int i = 0; i < n; ++i) {
+    if (L[i] < 8 || L[i] > 1024 || L[i] % 8 != 0) return false;
+    if (R[i] <= 0 || R[i] > (1 << 20)) return false;
+  }
+  return true;
+}
+
+Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
+  Layout o{};
+  size_t off = 0;
+  long long angle_floats = 0, slots = 0, parts = 0, maxN = 0;
+  for (int i = 0; i < n; ++i) {
+    const long long N = static_cast<long long>(L[i]) * L[i] * L[i];
+    angle_floats += N * R[i];
+    slots += R[i];
+    parts += static_cast<long long>(part_cap_for(L[i])) * R[i];
+    maxN = std::max(maxN, N);
+  }
+  auto take = [&](size_t bytes) {
+    const size_t at = off;
+    off = align_up(off + bytes);
+    return at;
+  };
+  o.angles = take(static_cast<size_t>(angle_floats) * 4);
+  o.ladder_beta = take(slots * 8);
+  o.perm = take(slots * 4);
+  o.beta_slot = take(slots * 4);
+  o.beta_slot64 = take(slots * 8);
+  o.bidx_slot = take(slots * 4);
+  o.E_slot = take(slots * 8);
+  o.sums_slot = take(slots * kNumSums * 8);
+  o.partials = take(static_cast<size_t>(parts) * kNumSums * 8);
+  o.acc_met = take(slots * 8);
+  o.acc_swap = take(slots * 8);
+  o.ctr = take(kNumCounters * 8);
+  o.status = take(64);
+  o.barrier = take(64);
+  o.nswapped = take(64);
+  o.lats = take(static_cast<size_t>(n) * sizeof(Lattice));
+  o.staging = take(static_cast<size_t>(maxN) * 4);
+  o.plan_items = take(static_cast<size_t>(parts) * sizeof(int4));
+  o.plan_offs = take(static_cast<size_t>(kMaxPlanBlocks + 1) * 4);
+  o.series = take(static_cast<size_t>(std::max<int64_t>(series_cap, 0)) * slots * sizeof(xy_record));
+  o.total = off;
+  return o;
+}
+
+int lcm_int(int a, int b) { return a / std::gcd(a, b) * b; }
+
+}  // namespace
+
+struct xy_ctx {
+  int n_lat = 0;
+  int n_slots = 0;
+  std::vector<LatHost> lat;
+  std::vector<double> betas;  // ladder betas, slot-indexed per lattice
+  uint64_t seed = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  int device = 0;
+  int num_sms = 0;
+  int max_block = 1024;  // threads per block the half-sweep kernels can launch with
+  Layout lay{};
+  char* ws = nullptr;
+  int64_t series_cap = 0;
+  uint64_t h_ctr[kNumCounters] = {0};
+  int exec = XY_EXEC_PLAIN;
+  int sticky = XY_OK;
+  std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+  struct Plan {
+    int G = 0, B = 0, smem = 0;
+    bool graph_ok = true;
+  } plan;
+  bool plan_valid = false;
+
+  template <typename T>
+  T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
+  float* angles() const { return at<float>(lay.angles); }
+  uint64_t* ctr() const { return at<uint64_t>(lay.ctr); }
+  Lattice dev_lat(int i) const {
+    const LatHost& h = lat[i];
+    Lattice d;
+    d.angles = angles() + h.angle_off;
+    d.L = h.L;
+    d.R = h.R;
+    d.slot0 = h.slot0;
+    d.ty = h.ty;
+    d.tz = h.tz;
+    d.nyt = h.nyt();
+    d.nzt = h.nzt();
+    d.part0 = h.part0;
+    return d;
+  }
+  PassParams pass_params(bool use_ctr, uint64_t mpass_off, int measure) const {
+    PassParams p;
+    p.seed = seed;
+    p.ctr = use_ctr ? ctr() : nullptr;
+    p.mpass_off = mpass_off;
+    p.beta_slot = at<float>(lay.beta_slot);
+    p.partials = at<double>(lay.partials);
+    p.acc_met = at<unsigned long long>(lay.acc_met);
+    p.measure = measure;
+    return p;
+  }
+};
+
+namespace {
+
+thread_local char g_last_cuda_error[256] = {0};
+
+int fail_cuda(xy_ctx* c, cudaError_t e, const char* what) {
+  std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", what, cudaGetErrorString(e));
+  if (c) c->sticky = XY_ERR_CUDA;
+  return XY_ERR_CUDA;
+}
+
+#define XY_TRY(c, call)                                      \
+  do {                                                       \
+    cudaError_t e_ = (call);                                 \
+    if (e_ != cudaSuccess) return fail_cuda((c), e_, #call); \
+  } while (0)
+
+#define XY_CHECK_LAUNCH(c) XY_TRY(c, cudaGetLastError())
+
+#define XY_ENTER(c)                                          \
+  do {                                                       \
+    if (!(c)) return XY_ERR_ARG;                             \
+    if ((c)->sticky != XY_OK) return XY_ERR_STATE;           \
+    XY_TRY((c), cudaSetDevice((c)->device));                 \
+  } while (0)
+
+int default_ty(int L) {
+  const int tx = L / 8;
+  int best = 1;
+  for (int d = 1; d <= L; ++d)
+    if (L % d == 0 && tx * d <= 256) best = d;
+  return best;
+}
+int default_tz(int L) { return std::min(16, L); }
+
+int sync_lats(xy_ctx* c) {
+  std::vector<Lattice> d(c->n_lat);
+  for (int i = 0; i < c->n_lat; ++i) d[i] = c->dev_lat(i);
+  XY_TRY(c, cudaMemcpyAsync(c->at<Lattice>(c->lay.lats), d.data(), sizeof(Lattice) * c->n_lat,
+                            cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+void drop_graphs(xy_ctx* c) {
+  for (auto& kv : c->graphs) cudaGraphExecDestroy(kv.second);
+  c->graphs.clear();
+  c->plan_valid = false;
+}
+
+template <int MODE>
+int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams& pp) {
+  const LatHost& h = c->lat[i];
+  const Lattice d = c->dev_lat(i);
+  const dim3 grid(h.nyt() * h.nzt(), h.R);
+  const dim3 block(h.L / 8, h.ty);
+  const int smem = tile_smem_bytes(h.L, h.ty);
+  k_half<MODE><<<grid, block, smem, st>>>(d, colour, pp);
+  XY_CHECK_LAUNCH(c);
+  return XY_OK;
+}
+
+template <int MODE>
+int launch_half_all(xy_ctx* c, cudaStream_t st, int colour, const PassParams& pp) {
+  for (int i = 0; i < c->n_lat; ++i) {
+    const int rc = launch_half<MODE>(c, st, i, colour, pp);
+    if (rc != XY_OK) return rc;
+  }
+  return XY_OK;
+}
+
+FinishParams finish_params(xy_ctx* c) {
+  FinishParams f{};
+  f.partials = c->at<double>(c->lay.partials);
+  f.sums_slot = c->at<double>(c->lay.sums_slot);
+  f.E_slot = c->at<double>(c->lay.E_slot);
+  f.ctr = c->ctr();
+  f.series = c->at<xy_record>(c->lay.series);
+  f.n_slots = c->n_slots;
+  f.parity = -1;
+  f.perm = c->at<int>(c->lay.perm);
+  f.ladder_beta = c->at<double>(c->lay.ladder_beta);
+  f.beta_slot = c->at<float>(c->lay.beta_slot);
+  f.beta_slot64 = c->at<double>(c->lay.beta_slot64);
+  f.bidx_slot = c->at<int>(c->lay.bidx_slot);
+  f.acc_swap = c->at<unsigned long long>(c->lay.acc_swap);
+  f.seed = c->seed;
+  f.n_swapped = nullptr;
+  return f;
+}
+
+int launch_finish(xy_ctx* c, cudaStream_t st, const FinishParams& f) {
+  k_finish<<<c->n_lat, 256, 0, st>>>(c->at<Lattice>(c->lay.lats), f);
+  XY_CHECK_LAUNCH(c);
+  return XY_OK;
+}
+
+bool due(uint64_t s, int every) { return every > 0 && (s + 1) % static_cast<uint64_t>(every) == 0; }
+
+struct BlockCounts {
+  uint64_t mpass = 0, sweeps = 0, swaps = 0, records = 0;
+};
+
+// Issues `ns` sweeps starting at host sweep index s0, relative to the device
+// counters, followed by the counter advance.  No synchronisation.
+int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, int se, uint64_t s0,
+                 BlockCounts* out) {
+  BlockCounts bc;
+  for (int j = 0; j < ns; ++j) {
+    const uint64_t s = s0 + j;
+    const bool meas = due(s, me), swp = due(s, se);
+    const bool needE = meas || swp;
+    const int n_pass = nM + nOR;
+    for (int p = 0; p < n_pass; ++p) {
+      const bool last = (p == n_pass - 1);
+      for (int colour = 0; colour < 2; ++colour) {
+        const int measure = (needE && last && colour == 1) ? 1 : 0;
+        int rc;
+        if (p < nM) {
+          rc = launch_half_all<kMetropolis>(c, st, colour, c->pass_params(true, bc.mpass, measure));
+        } else {
+          rc = launch_half_all<kOverrelax>(c, st, colour, c->pass_params(true, 0, measure));
+        }
+        if (rc != XY_OK) return rc;
+      }
+      if (p < nM) bc.mpass += 1;
+    }
+    if (needE) {
+      FinishParams f = finish_params(c);
+      f.sweep_off = bc.sweeps;
+      f.series_off = bc.records;
+      f.swap_off = bc.swaps;
+      f.record = meas ? 1 : 0;
+      f.swap = swp ? 1 : 0;
+      const int rc = launch_finish(c, st, f);
+      if (rc != XY_OK) return rc;
+    }
+    bc.sweeps += 1;
+    bc.records += meas ? 1 : 0;
+    bc.swaps += swp ? 1 : 0;
+  }
+  k_advance<<<1, 1, 0, st>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
+  XY_CHECK_LAUNCH(c);
+  if (out) *out = bc;
+  return XY_OK;
+}
+
+void mirror_advance(xy_ctx* c, const BlockCounts& bc) {
+  c->h_ctr[kCtrMpass] += bc.mpass;
+  c->h_ctr[kCtrSweep] += bc.sweeps;
+  c->h_ctr[kCtrSwap] += bc.swaps;
+  c->h_ctr[kCtrRecords] += bc.records;
+  c->h_ctr[kCtrSeries] += bc.records;
+}
+
+uint64_t count_due(uint64_t s0, uint64_t n, int every) {
+  if (every <= 0) return 0;
+  const uint64_t e = static_cast<uint64_t>(every);
+  return (s0 + n) / e - s0 / e;
+}
+
+int run_graph_block(xy_ctx* c, int nM, int nOR, int me, int se, int P, uint64_t s0) {
+  const auto key = std::make_tuple(nM, nOR, me, se, P, static_cast<int>(s0 % P), 0);
+  auto it = c->graphs.find(key);
+  if (it == c->graphs.end()) {
+    XY_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
+    BlockCounts bc;
+    const int rc = issue_sweeps(c, c->cap_stream, nM, nOR, P, me, se, s0, &bc);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+    if (rc != XY_OK) {
+      if (g) cudaGraphDestroy(g);
+      return rc;
+    }
+    if (e != cudaSuccess) return fail_cuda(c, e, "cudaStreamEndCapture");
+    cudaGraphExec_t ex = nullptr;
+    const cudaError_t e2 = cudaGraphInstantiate(&ex, g, 0);
+    cudaGraphDestroy(g);
+    if (e2 != cudaSuccess) return fail_cuda(c, e2, "cudaGraphInstantiate");
+    it = c->graphs.emplace(key, ex).first;
+  }
+  XY_TRY(c, cudaGraphLaunch(it->second, c->stream));
+  return XY_OK;
+}
+
+int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se);
+
+}  // namespace
+
+// ------------------------------------------------------------------ C-ABI
+
+extern "C" {
+
+const char* xy_strerror(int status) {
+  switch (status) {
+    case XY_OK: return "ok";
+    case XY_ERR_ARG: return "invalid argument";
+    case XY_ERR_CUDA: return g_last_cuda_error[0] ? g_last_cuda_error : "CUDA error";
+    case XY_ERR_TIMEOUT: return "device-side wait timed out";
+    case XY_ERR_STATE: return "context is in an error state";
+    case XY_ERR_NOMEM: return "buffer too small";
+    default: return "unknown status";
+  }
+}
+
+size_t xy_workspace_bytes(int n_lattices, const int* L, const int* n_replicas, int64_t series_capacity) {
+  if (!valid_lattices(n_lattices, L, n_replicas) || series_capacity < 0) return 0;
+  return layout_for(n_lattices, L, n_replicas, series_capacity).total;
+}
+
+int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, const double* betas,
+            uint64_t seed, void* d_workspace, size_t ws_bytes, int64_t series_capacity, void* stream) {
+  if (!out) return XY_ERR_ARG;
+  *out = nullptr;
+  if (!valid_lattices(n_lattices, L, n_replicas) || !betas || !d_workspace || series_capacity < 0)
+    return XY_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(d_workspace) % kAlign != 0) return XY_ERR_ARG;
+  int off = 0;
+  for (int i = 0; i < n_lattices; ++i) {
+    for (int k = 0; k < n_replicas[i]; ++k) {
+      const double b = betas[off + k];
+      if (!std::isfinite(b) || b < 0.0) return XY_ERR_ARG;
+      if (k > 0 && !(b > betas[off + k - 1])) return XY_ERR_ARG;
+    }
+    off += n_replicas[i];
+  }
+  const Layout lay = layout_for(n_lattices, L, n_replicas, series_capacity);
+  if (ws_bytes < lay.total) return XY_ERR_NOMEM;
+
+  xy_ctx* c = new xy_ctx();
+  c->n_lat = n_lattices;
+  c->seed = seed;
+  c->stream = static_cast<cudaStream_t>(stream);
+  c->lay = lay;
+  c->ws = static_cast<char*>(d_workspace);
+  c->series_cap = series_capacity;
+  size_t aoff = 0;
+  int slot = 0, part = 0;
+  for (int i = 0; i < n_lattices; ++i) {
+    LatHost h;
+    h.L = L[i];
+    h.R = n_replicas[i];
+    h.slot0 = slot;
+    h.ty = default_ty(h.L);
+    h.tz = default_tz(h.L);
+    h.angle_off = aoff;
+    h.part_cap = part_cap_for(h.L);
+    h.part0 = part;
+    aoff += static_cast<size_t>(h.N()) * h.R;
+    slot += h.R;
+    part += h.part_cap * h.R;
+    c->lat.push_back(h);
+  }
+  c->n_slots = slot;
+  c->betas.assign(betas, betas + slot);
+
+  auto bail = [&](int rc) {
+    xy_destroy(c);
+    return rc;
+  };
+  // The workspace's device is the context's device.
+  cudaPointerAttributes pa{};
+  cudaError_t e = cudaPointerGetAttributes(&pa, d_workspace);
+  if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    xy_destroy(c);
+    return XY_ERR_ARG;
+  }
+  c->device = pa.device;
+  e = cudaSetDevice(c->device);
+  if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaSetDevice"));
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device);
+  if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaDeviceGetAttribute"));
+  e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaStreamCreateWithFlags"));
+  for (int mode = 0; mode < 3; ++mode) {
+    // Tiles need up to ~64 KB of shared memory on the largest lattices.
+    const void* fn = mode == 0 ? reinterpret_cast<const void*>(k_half<kMetropolis>)
+                   : mode == 1 ? reinterpret_cast<const void*>(k_half<kOverrelax>)
+                               : reinterpret_cast<const void*>(k_half<kMeasureOnly>);
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncSetAttribute"));
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncGetAttributes"));
+    c->max_block = std::min(c->max_block, fa.maxThreadsPerBlock);
+  }
+  for (LatHost& h : c->lat)
+    while ((h.L / 8) * h.ty > c->max_block && h.ty > 1) h.ty = std::max(1, h.ty / 2);
+
+  // Ladder tables: identity permutation, each slot at its own beta.
+  std::vector<int> perm(slot), bidx(slot);
+  std::vector<float> bs(slot);
+  for (const LatHost& h : c->lat)
+    for (int k = 0; k < h.R; ++k) {
+      perm[h.slot0 + k] = k;
+      bidx[h.slot0 + k] = k;
+      bs[h.slot0 + k] = static_cast<float>(betas[h.slot0 + k]);
+    }
+  cudaStream_t st = c->stream;
+  auto cp = [&](size_t off, const void* src, size_t n) {
+    return cudaMemcpyAsync(c->ws + off, src, n, cudaMemcpyHostToDevice, st);
+  };
+  if ((e = cp(lay.ladder_beta, betas, slot * 8)) != cudaSuccess ||
+      (e = cp(lay.perm, perm.data(), slot * 4)) != cudaSuccess ||
+      (e = cp(lay.beta_slot, bs.data(), slot * 4)) != cudaSuccess ||
+      (e = cp(lay.beta_slot64, betas, slot * 8)) != cudaSuccess ||
+      (e = cp(lay.bidx_slot, bidx.data(), slot * 4)) != cudaSuccess)
+    return bail(fail_cuda(nullptr, e, "cudaMemcpyAsync"));
+  if ((e = cudaMemsetAsync(c->ws + lay.acc_met, 0, slot * 8, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->ws + lay.acc_swap, 0, slot * 8, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->ws + lay.ctr, 0, kNumCounters * 8, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->ws + lay.status, 0, 64, st)) != cudaSuccess)
+    return bail(fail_cuda(nullptr, e, "cudaMemsetAsync"));
+  int rc = sync_lats(c);
+  if (rc != XY_OK) return bail(rc);
+  for (int i = 0; i < n_lattices; ++i) {
+    const long long pairs = c->lat[i].N() / 2 * c->lat[i].R;
+    const int blocks = static_cast<int>(std::min<long long>((pairs + 255) / 256, 65535));
+    k_init<<<blocks, 256, 0, st>>>(c->dev_lat(i), seed);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "k_init"));
+  }
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaStreamSynchronize"));
+  *out = c;
+  return XY_OK;
+}
+
+int xy_destroy(xy_ctx* c) {
+  if (!c) return XY_OK;
+  drop_graphs(c);
+  if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+  delete c;
+  return XY_OK;
+}
+
+int xy_set_exec(xy_ctx* c, int mode) {
+  XY_ENTER(c);
+  if (mode != XY_EXEC_PLAIN && mode != XY_EXEC_GRAPH && mode != XY_EXEC_PERSISTENT) return XY_ERR_ARG;
+  c->exec = mode;
+  return XY_OK;
+}
+
+int xy_sweep(xy_ctx* c, int nM, int nOR, int n_sweeps, int me, int se) {
+  XY_ENTER(c);
+  if (nM < 0 || nOR < 0 || n_sweeps < 0 || me < 0 || se < 0) return XY_ERR_ARG;
+  if (n_sweeps == 0) return XY_OK;
+  if (nM + nOR == 0) return XY_ERR_ARG;
+  const uint64_t s0 = c->h_ctr[kCtrSweep];
+  const uint64_t n_meas = count_due(s0, n_sweeps, me);
+  if (c->h_ctr[kCtrSeries] + n_meas > static_cast<uint64_t>(c->series_cap)) return XY_ERR_NOMEM;
+
+  if (c->exec == XY_EXEC_PERSISTENT) return persistent_sweeps(c, nM, nOR, n_sweeps, me, se);
+
+  if (c->exec == XY_EXEC_GRAPH) {
+    const int P0 = lcm_int(me > 0 ? me : 1, se > 0 ? se : 1);
+    if (P0 <= 64) {
+      const int P = P0 * std::max(1, 16 / P0);  // a graph holds P sweeps
+      int done = 0;
+      while (n_sweeps - done >= P) {
+        const uint64_t s = c->h_ctr[kCtrSweep];
+        const int rc = run_graph_block(c, nM, nOR, me, se, P, s);
+        if (rc != XY_OK) return rc;
+        BlockCounts bc;
+        bc.mpass = static_cast<uint64_t>(nM) * P;
+        bc.sweeps = P;
+        bc.swaps = count_due(s, P, se);
+        bc.records = count_due(s, P, me);
+        mirror_advance(c, bc);
+        done += P;
+      }
+      if (done < n_sweeps) {
+        BlockCounts bc;
+        const int rc = issue_sweeps(c, c->stream, nM, nOR, n_sweeps - done, me, se, c->h_ctr[kCtrSweep], &bc);
+        if (rc != XY_OK) return rc;
+        mirror_advance(c, bc);
+      }
+      return XY_OK;
+    }
+  }
+  BlockCounts bc;
+  const int rc = issue_sweeps(c, c->stream, nM, nOR, n_sweeps, me, se, s0, &bc);
+  if (rc != XY_OK) return rc;
+  mirror_advance(c, bc);
+  return XY_OK;
+}
+
+int xy_metropolis_half(xy_ctx* c, int colour, uint64_t mpass) {
+  XY_ENTER(c);
+  if (colour != 0 && colour != 1) return XY_ERR_ARG;
+  return launch_half_all<kMetropolis>(c, c->stream, colour, c->pass_params(false, mpass, 0));
+}
+
+int xy_overrelax_half(xy_ctx* c, int colour) {
+  XY_ENTER(c);
+  if (colour != 0 && colour != 1) return XY_ERR_ARG;
+  return launch_half_all<kOverrelax>(c, c->stream, colour, c->pass_params(false, 0, 0));
+}
+
+static int measure_now(xy_ctx* c, int swap, int parity) {
+  int rc = launch_half_all<kMeasureOnly>(c, c->stream, 1, c->pass_params(false, 0, 1));
+  if (rc != XY_OK) return rc;
+  FinishParams f = finish_params(c);
+  f.record = 0;
+  f.swap = swap;
+  f.parity = parity;
+  f.n_swapped = swap ? c->at<int>(c->lay.nswapped) : nullptr;
+  return launch_finish(c, c->stream, f);
+}
+
+int xy_measure(xy_ctx* c, xy_record* out) {
+  XY_ENTER(c);
+  if (!out) return XY_ERR_ARG;
+  int rc = measure_now(c, 0, 0);
+  if (rc != XY_OK) return rc;
+  const int S = c->n_slots;
+  std::vector<double> sums(static_cast<size_t>(S) * kNumSums), E(S), b64(S);
+  std::vector<int> bidx(S);
+  XY_TRY(c, cudaMemcpyAsync(sums.data(), c->ws + c->lay.sums_slot, sums.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(E.data(), c->ws + c->lay.E_slot, S * 8, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(b64.data(), c->ws + c->lay.beta_slot64, S * 8, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(bidx.data(), c->ws + c->lay.bidx_slot, S * 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  for (int g = 0; g < S; ++g) {
+    xy_record& r = out[g];
+    const double* v = &sums[static_cast<size_t>(g) * kNumSums];
+    r.E = E[g];
+    r.Mx = v[0];
+    r.My = v[1];
+    for (int mu = 0; mu < 3; ++mu) {
+      r.C[mu] = v[2 + mu];
+      r.S[mu] = v[5 + mu];
+    }
+    r.beta = b64[g];
+    r.slot = g;
+    r.beta_index = bidx[g];
+    r.sweep = c->h_ctr[kCtrSweep];
+  }
+  return XY_OK;
+}
+
+int xy_pt_swap(xy_ctx* c, int parity, int* n_accepted_out) {
+  XY_ENTER(c);
+  if (parity != 0 && parity != 1) return XY_ERR_ARG;
+  XY_TRY(c, cudaMemsetAsync(c->ws + c->lay.nswapped, 0, 4, c->stream));
+  int rc = measure_now(c, 1, parity);
+  if (rc != XY_OK) return rc;
+  k_advance<<<1, 1, 0, c->stream>>>(c->ctr(), 0, 0, 1, 0, 0);
+  XY_CHECK_LAUNCH(c);
+  c->h_ctr[kCtrSwap] += 1;
+  int n = 0;
+  XY_TRY(c, cudaMemcpyAsync(&n, c->ws + c->lay.nswapped, 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  if (n_accepted_out) *n_accepted_out = n;
+  return XY_OK;
+}
+
+int xy_series_count(xy_ctx* c, int64_t* n_out) {
+  XY_ENTER(c);
+  if (!n_out) return XY_ERR_ARG;
+  *n_out = static_cast<int64_t>(c->h_ctr[kCtrSeries]) * c->n_slots;
+  return XY_OK;
+}
+
+int xy_read_series(xy_ctx* c, xy_record* buf, int64_t cap, int64_t* n_out) {
+  XY_ENTER(c);
+  if (!n_out || (cap > 0 && !buf) || cap < 0) return XY_ERR_ARG;
+  const int64_t n = static_cast<int64_t>(c->h_ctr[kCtrSeries]) * c->n_slots;
+  *n_out = 0;
+  if (n > cap) return XY_ERR_NOMEM;
+  if (n > 0) {
+    XY_TRY(c, cudaMemcpyAsync(buf, c->ws + c->lay.series, n * sizeof(xy_record), cudaMemcpyDeviceToHost, c->stream));
+  }
+  XY_TRY(c, cudaMemsetAsync(c->ws + c->lay.ctr + kCtrSeries * 8, 0, 8, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  c->h_ctr[kCtrSeries] = 0;
+  *n_out = n;
+  return XY_OK;
+}
+
+int xy_get_state(xy_ctx* c, float* host_angles, int32_t* perm, uint64_t* counters) {
+  XY_ENTER(c);
+  if (host_angles) {
+    size_t at = 0;
+    for (const LatHost& h : c->lat) {
+      const long long N = h.N();
+      const int Hh = h.L / 2;
+      std::vector<float> packed(static_cast<size_t>(N));
+      for (int r = 0; r < h.R; ++r) {
+        XY_TRY(c, cudaMemcpyAsync(packed.data(), c->angles() + h.angle_off + r * N, N * 4, cudaMemcpyDeviceToHost, c->stream));
+        XY_TRY(c, cudaStreamSynchronize(c->stream));
+        float* dst = host_angles + at;
+        for (int z = 0; z < h.L; ++z)
+          for (int y = 0; y < h.L; ++y)
+            for (int x = 0; x < h.L; ++x) {
+              const int col = (x + y + z) & 1;
+              const long long p = (x >> 1) + static_cast<long long>(Hh) * (y + static_cast<long long>(h.L) * z);
+              dst[x + static_cast<long long>(h.L) * (y + static_cast<long long>(h.L) * z)] = packed[col * (N / 2) + p];
+            }
+        at += static_cast<size_t>(N);
+      }
+    }
+  }
+  if (perm) XY_TRY(c, cudaMemcpyAsync(perm, c->ws + c->lay.perm, c->n_slots * 4, cudaMemcpyDeviceToHost, c->stream));
+  if (counters) XY_TRY(c, cudaMemcpyAsync(counters, c->ctr(), 4 * 8, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+int xy_set_state(xy_ctx* c, const float* host_angles, const int32_t* perm, const uint64_t* counters) {
+  XY_ENTER(c);
+  if (perm) {
+    for (const LatHost& h : c->lat) {
+      std::vector<int> seen(h.R, 0);
+      for (int k = 0; k < h.R; ++k) {
+        const int v = perm[h.slot0 + k];
+        if (v < 0 || v >= h.R || seen[v]) return XY_ERR_ARG;
+        seen[v] = 1;
+      }
+    }
+  }
+  if (host_angles) {
+    size_t at = 0;
+    for (const LatHost& h : c->lat) {
+      const long long N = h.N();
+      const int Hh = h.L / 2;
+      std::vector<float> packed(static_cast<size_t>(N));
+      for (int r = 0; r < h.R; ++r) {
+        const float* src = host_angles + at;
+        for (int z = 0; z < h.L; ++z)
+          for (int y = 0; y < h.L; ++y)
+            for (int x = 0; x < h.L; ++x) {
+              const int col = (x + y + z) & 1;
+              const long long p = (x >> 1) + static_cast<long long>(Hh) * (y + static_cast<long long>(h.L) * z);
+              float v = src[x + static_cast<long long>(h.L) * (y + static_cast<long long>(h.L) * z)];
+              if (!std::isfinite(v)) return XY_ERR_ARG;
+              packed[col * (N / 2) + p] = v;
+            }
+        XY_TRY(c, cudaMemcpyAsync(c->angles() + h.angle_off + r * N, packed.data(), N * 4, cudaMemcpyHostToDevice, c->stream));
+        XY_TRY(c, cudaStreamSynchronize(c->stream));
+        at += static_cast<size_t>(N);
+      }
+    }
+  }
+  if (perm) {
+    const int S = c->n_slots;
+    std::vector<int> pv(perm, perm + S), bidx(S);
+    std::vector<float> bs(S);
+    std::vector<double> b64(S);
+    for (const LatHost& h : c->lat)
+      for (int k = 0; k < h.R; ++k) {
+        const int g = h.slot0 + pv[h.slot0 + k];
+        bidx[g] = k;
+        b64[g] = c->betas[h.slot0 + k];
+        bs[g] = static_cast<float>(b64[g]);
+      }
+    XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.perm, pv.data(), S * 4, cudaMemcpyHostToDevice, c->stream));
+    XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.bidx_slot, bidx.data(), S * 4, cudaMemcpyHostToDevice, c->stream));
+    XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.beta_slot, bs.data(), S * 4, cudaMemcpyHostToDevice, c->stream));
+    XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.beta_slot64, b64.data(), S * 8, cudaMemcpyHostToDevice, c->stream));
+  }
+  if (counters) {
+    uint64_t v[kNumCounters] = {0};
+    for (int i = 0; i < 4; ++i) v[i] = counters[i];
+    v[kCtrSeries] = c->h_ctr[kCtrSeries];
+    XY_TRY(c, cudaMemcpyAsync(c->ctr(), v, 4 * 8, cudaMemcpyHostToDevice, c->stream));
+    for (int i = 0; i < 4; ++i) c->h_ctr[i] = counters[i];
+  }
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  drop_graphs(c);
+  return XY_OK;
+}
+
+int xy_get_packed(xy_ctx* c, float* host_packed) {
+  XY_ENTER(c);
+  if (!host_packed) return XY_ERR_ARG;
+  const size_t bytes = c->lay.ladder_beta - c->lay.angles;
+  size_t n = 0;
+  for (const LatHost& h : c->lat) n += static_cast<size_t>(h.N()) * h.R;
+  XY_TRY(c, cudaMemcpyAsync(host_packed, c->angles(), std::min(bytes, n * 4), cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+int xy_set_packed(xy_ctx* c, const float* host_packed) {
+  XY_ENTER(c);
+  if (!host_packed) return XY_ERR_ARG;
+  size_t n = 0;
+  for (const LatHost& h : c->lat) n += static_cast<size_t>(h.N()) * h.R;
+  XY_TRY(c, cudaMemcpyAsync(c->angles(), host_packed, n * 4, cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+int xy_get_accepts(xy_ctx* c, uint64_t* met, uint64_t* swap) {
+  XY_ENTER(c);
+  if (met) XY_TRY(c, cudaMemcpyAsync(met, c->ws + c->lay.acc_met, c->n_slots * 8, cudaMemcpyDeviceToHost, c->stream));
+  if (swap) XY_TRY(c, cudaMemcpyAsync(swap, c->ws + c->lay.acc_swap, c->n_slots * 8, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+int xy_debug_draws(xy_ctx* c, int slot, int colour, int tag, uint64_t count, uint32_t* host_words) {
+  XY_ENTER(c);
+  if (!host_words || slot < 0 || slot >= c->n_slots || (colour != 0 && colour != 1) || tag < 0 || tag > 7)
+    return XY_ERR_ARG;
+  int i = 0;
+  while (!(slot >= c->lat[i].slot0 && slot < c->lat[i].slot0 + c->lat[i].R)) ++i;
+  const LatHost& h = c->lat[i];
+  const long long half = h.N() / 2;
+  uint32_t* dev = c->at<uint32_t>(c->lay.staging);  // room for N words = 2 * half
+  const int blocks = static_cast<int>(std::min<long long>((half + 255) / 256, 65535));
+  k_draws<<<blocks, 256, 0, c->stream>>>(c->dev_lat(i), slot - h.slot0, colour, static_cast<uint32_t>(tag), count, c->seed, dev);
+  XY_CHECK_LAUNCH(c);
+  XY_TRY(c, cudaMemcpyAsync(host_words, dev, 2 * half * 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+int xy_set_tile(xy_ctx* c, int lattice, int ty, int tz) {
+  XY_ENTER(c);
+  if (lattice < 0 || lattice >= c->n_lat) return XY_ERR_ARG;
+  LatHost& h = c->lat[lattice];
+  if (ty < 1 || tz < 1 || ty > h.L || tz > h.L || (h.L / 8) * ty > c->max_block) return XY_ERR_ARG;
+  if (((h.L + ty - 1) / ty) * ((h.L + tz - 1) / tz) > h.part_cap) return XY_ERR_ARG;
+  if (tile_smem_bytes(h.L, ty) > 200 * 1024) return XY_ERR_ARG;
+  h.ty = ty;
+  h.tz = tz;
+  drop_graphs(c);
+  return sync_lats(c);
+}
+
+int xy_get_tile(xy_ctx* c, int lattice, int* ty, int* tz) {
+  XY_ENTER(c);
+  if (lattice < 0 || lattice >= c->n_lat || !ty || !tz) return XY_ERR_ARG;
+  *ty = c->lat[lattice].ty;
+  *tz = c->lat[lattice].tz;
+  return XY_OK;
+}
+
+int xy_device_status(xy_ctx* c, int* status_out) {
+  XY_ENTER(c);
+  if (!status_out) return XY_ERR_ARG;
+  XY_TRY(c, cudaMemcpyAsync(status_out, c->ws + c->lay.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ persistent path
+
+namespace {
+
+// Longest-processing-time-first assignment of the tile work items of one
+// half-sweep to G blocks.  Cost of a tile ~ (rows + 2)(planes + 2) x row
+// length: the sincos evaluations, which dominate, including the halos.
+int build_plan(xy_ctx* c) {
+  if (c->plan_valid) return XY_OK;
+  int B = 64, smem = 0;
+  for (const LatHost& h : c->lat) {
+    B = std::max(B, (h.L / 8) * h.ty);
+    smem = std::max(smem, tile_smem_bytes(h.L, h.ty));
+  }
+  B = (B + 31) / 32 * 32;
+  cudaFuncAttributes fa{};
+  XY_TRY(c, cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(k_persistent)));
+  if (B > fa.maxThreadsPerBlock) return XY_ERR_ARG;  // a tile wider than one persistent block
+  XY_TRY(c, cudaFuncSetAttribute(reinterpret_cast<const void*>(k_persistent),
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  int nb = 0;
+  XY_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, B, smem));
+  if (nb <= 0) return XY_ERR_ARG;
+  struct Item {
+    int4 w;
+    double cost;
+  };
+  std::vector<Item> items;
+  for (int i = 0; i < c->n_lat; ++i) {
+    const LatHost& h = c->lat[i];
+    for (int r = 0; r < h.R; ++r)
+      for (int t = 0; t < h.nyt() * h.nzt(); ++t) {
+        const int yt = t % h.nyt(), zt = t / h.nyt();
+        const int tya = std::min(h.ty, h.L - yt * h.ty), tza = std::min(h.tz, h.L - zt * h.tz);
+        items.push_back({make_int4(i, r, t, 0), double(tya + 2) * double(tza + 2) * (h.L / 8)});
+      }
+  }
+  const int G = static_cast<int>(std::min<long long>(
+      std::min<long long>(static_cast<long long>(nb) * c->num_sms, kMaxPlanBlocks), std::max<size_t>(items.size(), 1)));
+  std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
+  std::vector<double> load(G, 0.0);
+  std::vector<std::vector<int4>> per(G);
+  for (const Item& it : items) {
+    const int b = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
+    load[b] += it.cost;
+    per[b].push_back(it.w);
+  }
+  std::vector<int4> flat;
+  std::vector<int> offs(G + 1, 0);
+  for (int b = 0; b < G; ++b) {
+    offs[b] = static_cast<int>(flat.size());
+    flat.insert(flat.end(), per[b].begin(), per[b].end());
+  }
+  offs[G] = static_cast<int>(flat.size());
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.plan_items, flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.plan_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  c->plan.G = G;
+  c->plan.B = B;
+  c->plan.smem = smem;
+  c->plan_valid = true;
+  return XY_OK;
+}
+
+PersistentArgs persistent_args(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
+  PersistentArgs a{};
+  a.pp = c->pass_params(true, 0, 0);
+  a.fp = finish_params(c);
+  a.lats = c->at<Lattice>(c->lay.lats);
+  a.items = c->at<int4>(c->lay.plan_items);
+  a.offs = c->at<int>(c->lay.plan_offs);
+  a.n_lat = c->n_lat;
+  a.nM = nM;
+  a.nOR = nOR;
+  a.n_sweeps = ns;
+  a.me = me;
+  a.se = se;
+  a.bar = c->at<unsigned long long>(c->lay.barrier);
+  a.status = c->at<int>(c->lay.status);
+  a.budget_ns = 2000000000ll;
+  a.poison = 0;
+  return a;
+}
+
+cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3(c->plan.G);
+  cfg.blockDim = dim3(c->plan.B);
+  cfg.dynamicSmemBytes = c->plan.smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_persistent, a);
+}
+
+// Records the persistent block: barrier reset, the cooperative kernel, the
+// counter advance.
+int issue_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, const BlockCounts& bc) {
+  XY_TRY(c, cudaMemsetAsync(a.bar, 0, 8, st));
+  XY_TRY(c, launch_persistent(c, st, a));
+  k_advance<<<1, 1, 0, st>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
+  XY_CHECK_LAUNCH(c);
+  return XY_OK;
+}
+
+int check_status(xy_ctx* c) {
+  int st = 0;
+  XY_TRY(c, cudaMemcpyAsync(&st, c->ws + c->lay.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  if (st != 0) {
+    c->sticky = XY_ERR_TIMEOUT;
+    return XY_ERR_TIMEOUT;
+  }
+  return XY_OK;
+}
+
+int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
+  int rc = build_plan(c);
+  if (rc != XY_OK) return rc;
+  const uint64_t s0 = c->h_ctr[kCtrSweep];
+  BlockCounts bc;
+  bc.mpass = static_cast<uint64_t>(nM) * ns;
+  bc.sweeps = ns;
+  bc.swaps = count_due(s0, ns, se);
+  bc.records = count_due(s0, ns, me);
+  const PersistentArgs a = persistent_args(c, nM, nOR, ns, me, se);
+  bool launched = false;
+  if (c->plan.graph_ok) {
+    // The kernel reads the device counters; only the counter advance baked
+    // into the graph depends on the phase of s0 against the two periods.
+    const uint64_t P = static_cast<uint64_t>(lcm_int(me > 0 ? me : 1, se > 0 ? se : 1));
+    const auto key = std::make_tuple(nM, nOR, ns, me, se, static_cast<int>(s0 % P), 1);
+    auto it = c->graphs.find(key);
+    if (it == c->graphs.end()) {
+      cudaGraph_t g = nullptr;
+      cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return fail_cuda(c, e, "cudaStreamBeginCapture");
+      cudaError_t e1 = cudaMemsetAsync(a.bar, 0, 8, c->cap_stream);
+      cudaError_t e2 = e1 == cudaSuccess ? launch_persistent(c, c->cap_stream, a) : e1;
+      if (e2 == cudaSuccess) {
+        k_advance<<<1, 1, 0, c->cap_stream>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
+        e2 = cudaGetLastError();
+      }
+      e = cudaStreamEndCapture(c->cap_stream, &g);
+      if (e2 == cudaSuccess && e == cudaSuccess) {
+        cudaGraphExec_t ex = nullptr;
+        e = cudaGraphInstantiate(&ex, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return fail_cuda(c, e, "cudaGraphInstantiate");
+        it = c->graphs.emplace(key, ex).first;
+      } else {
+        // Capture of a cooperative launch is not available: launch directly.
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        c->plan.graph_ok = false;
+      }
+    }
+    if (c->plan.graph_ok) {
+      XY_TRY(c, cudaGraphLaunch(it->second, c->stream));
+      launched = true;
+    }
+  }
+  if (!launched) {
+    rc = issue_persistent(c, c->stream, a, bc);
+    if (rc != XY_OK) return rc;
+  }
+  mirror_advance(c, bc);
+  return check_status(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+int xy_debug_barrier_timeout(xy_ctx* c, int budget_us, int* status_out) {
+  XY_ENTER(c);
+  if (budget_us <= 0 || budget_us > 2000000) return XY_ERR_ARG;
+  int rc = build_plan(c);
+  if (rc != XY_OK) return rc;
+  PersistentArgs a = persistent_args(c, 0, 0, 0, 0, 0);
+  a.poison = 1;
+  a.budget_ns = static_cast<long long>(budget_us) * 1000;
+  XY_TRY(c, cudaMemsetAsync(a.bar, 0, 8, c->stream));
+  XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));
+  XY_TRY(c, launch_persistent(c, c->stream, a));
+  int st = 0;
+  XY_TRY(c, cudaMemcpyAsync(&st, a.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  if (status_out) *status_out = st;
+  return st == 0 ? XY_OK : XY_ERR_TIMEOUT;
+}
+
+int xy_autotune(xy_ctx* c, int nM, int nOR) {
+  XY_ENTER(c);
+  if (nM < 0 || nOR < 0 || nM + nOR == 0) return XY_ERR_ARG;
+  // Save what trial sweeps change: angles, counters, Metropolis accepts.
+  const size_t angle_bytes = c->lay.ladder_beta - c->lay.angles;
+  std::vector<char> angles(angle_bytes);
+  std::vector<char> ctr(kNumCounters * 8), acc(static_cast<size_t>(c->n_slots) * 8);
+  XY_TRY(c, cudaMemcpyAsync(angles.data(), c->ws + c->lay.angles, angle_bytes, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(ctr.data(), c->ws + c->lay.ctr, ctr.size(), cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(acc.data(), c->ws + c->lay.acc_met, acc.size(), cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  uint64_t h_ctr[kNumCounters];
+  std::memcpy(h_ctr, c->h_ctr, sizeof h_ctr);
+  const int exec = c->exec;
+  c->exec = XY_EXEC_PLAIN;
+  cudaEvent_t e0, e1;
+  XY_TRY(c, cudaEventCreate(&e0));
+  XY_TRY(c, cudaEventCreate(&e1));
+  int rc = XY_OK;
+  for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) {
+    LatHost& h = c->lat[i];
+    const int tx = h.L / 8;
+    float best = 1e30f;
+    int bty = h.ty, btz = h.tz;
+    for (int ty = 1; ty <= h.L && rc == XY_OK; ++ty) {
+      if (h.L % ty != 0 || tx * ty > c->max_block || tx * ty < 32) continue;
+      if (tile_smem_bytes(h.L, ty) > 200 * 1024) continue;
+      const int tzs[] = {2, 4, 8, 16, 32};
+      for (int tz : tzs) {
+        if (tz > h.L || h.L % tz != 0) continue;
+        if ((h.L / ty) * (h.L / tz) > h.part_cap) continue;
+        h.ty = ty;
+        h.tz = tz;
+        if ((rc = sync_lats(c)) != XY_OK) break;
+        // Time this lattice alone: other lattices keep their shapes but are
+        // timed too; the argmin over this lattice's shapes is unaffected.
+        for (int rep = 0; rep < 2 && rc == XY_OK; ++rep) {
+          for (int p = 0; p < nM + nOR && rc == XY_OK; ++p)
+            for (int col = 0; col < 2 && rc == XY_OK; ++col)
+              rc = p < nM ? launch_half<kMetropolis>(c, c->stream, i, col, c->pass_params(false, 0, 0))
+                          : launch_half<kOverrelax>(c, c->stream, i, col, c->pass_params(false, 0, 0));
+        }
+        if (rc != XY_OK) break;
+        XY_TRY(c, cudaEventRecord(e0, c->stream));
+        for (int rep = 0; rep < 3 && rc == XY_OK; ++rep)
+          for (int p = 0; p < nM + nOR && rc == XY_OK; ++p)
+            for (int col = 0; col < 2 && rc == XY_OK; ++col)
+              rc = p < nM ? launch_half<kMetropolis>(c, c->stream, i, col, c->pass_params(false, 0, 0))
+                          : launch_half<kOverrelax>(c, c->stream, i, col, c->pass_params(false, 0, 0));
+        XY_TRY(c, cudaEventRecord(e1, c->stream));
+        XY_TRY(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        XY_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bty = ty;
+          btz = tz;
+        }
+      }
+    }
+    h.ty = bty;
+    h.tz = btz;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  c->exec = exec;
+  if (rc != XY_OK) return rc;
+  rc = sync_lats(c);
+  if (rc != XY_OK) return rc;
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.angles, angles.data(), angle_bytes, cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.ctr, ctr.data(), ctr.size(), cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.acc_met, acc.data(), acc.size(), cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  std::memcpy(c->h_ctr, h_ctr, sizeof h_ctr);
+  drop_graphs(c);
+  return XY_OK;
+}
+
+}  // extern "C"

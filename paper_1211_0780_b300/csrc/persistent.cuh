@@ -1,0 +1,146 @@
+// Persistent batched sweep: one cooperative launch advances every replica of
+// every lattice (uneven L included) through n_sweeps sweeps, with the fused
+// measurement and the on-device exchange of Sec. II, Eq. (3).  Each
+// half-sweep is a list of tile work items (lattice, slot, tile) that the host
+// scheduler spreads over the blocks by longest-processing-time-first; a
+// bounded grid barrier separates half-sweeps.
+//
+// The barrier is a monotonically increasing arrival counter: barrier number
+// b completes when the counter reaches (b + 1) * gridDim.x.  Thread 0 of each
+// block arrives with a release fence and polls with acquire loads.  Every
+// wait is bounded by a %globaltimer budget; when it runs out the block sets
+// the status word to XY_ERR_TIMEOUT and every block leaves at its next
+// barrier, so a missing block ends the launch with an error, never a hang.
+// Co-residency of all blocks is guaranteed by the cooperative launch.
+#pragma once
+#include <cstdint>
+
+#include "kernels.cuh"
+#include "sweep.cuh"
+
+namespace xy {
+
+struct PersistentArgs {
+  PassParams pp;            // mpass_off and measure are set per pass
+  FinishParams fp;          // offsets, record and swap are set per sweep
+  const Lattice* lats;
+  const int4* items;        // (lattice, local slot, tile, unused)
+  const int* offs;          // items of block b: offs[b] .. offs[b+1]-1
+  int n_lat;
+  int nM, nOR, n_sweeps, me, se;
+  unsigned long long* bar;  // arrival counter, zero at launch
+  int* status;              // 0, or XY_ERR_TIMEOUT
+  long long budget_ns;      // bound of one barrier wait
+  int poison;               // test hook: the first barrier expects one block too many
+};
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ unsigned long long ld_acquire(const unsigned long long* p) {
+  unsigned long long v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned long long v) {
+  asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// Returns false if the launch has failed (this or another block timed out).
+__device__ __forceinline__ bool grid_barrier(const PersistentArgs& a, unsigned long long target) {
+  __syncthreads();
+  __shared__ int ok;
+  if (threadIdx.x == 0) {
+    __threadfence();
+    red_release_add(a.bar, 1ull);
+    const long long t0 = global_ns();
+    int good = 1;
+    while (ld_acquire(a.bar) < target) {
+      if (*reinterpret_cast<volatile int*>(a.status) != 0) {
+        good = 0;
+        break;
+      }
+      if (global_ns() - t0 > a.budget_ns) {
+        atomicCAS(a.status, 0, XY_ERR_TIMEOUT);
+        good = 0;
+        break;
+      }
+      __nanosleep(64);
+    }
+    ok = good;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool due_dev(uint64_t s, int every) {
+  return every > 0 && (s + 1) % static_cast<uint64_t>(every) == 0;
+}
+
+__global__ void __launch_bounds__(512, 1) k_persistent(PersistentArgs a) {
+  extern __shared__ __align__(16) float sm[];
+  const unsigned long long G = gridDim.x;
+  unsigned long long nbar = 0;
+  if (a.poison) {
+    grid_barrier(a, G + 1);
+    return;
+  }
+  const int tid = threadIdx.x, B = blockDim.x;
+  const uint64_t s_base = a.pp.ctr[kCtrSweep];
+  const int n_pass = a.nM + a.nOR;
+  const int i0 = a.offs[blockIdx.x], i1 = a.offs[blockIdx.x + 1];
+  uint64_t n_rec = 0, n_swp = 0;
+  for (int s = 0; s < a.n_sweeps; ++s) {
+    const uint64_t sw = s_base + s;
+    const bool meas = due_dev(sw, a.me), swp = due_dev(sw, a.se);
+    for (int p = 0; p < n_pass; ++p) {
+      const bool is_met = p < a.nM;
+      for (int colour = 0; colour < 2; ++colour) {
+        PassParams pp = a.pp;
+        pp.mpass_off = is_met ? static_cast<uint64_t>(s) * a.nM + p : 0ull;
+        pp.measure = ((meas || swp) && p == n_pass - 1 && colour == 1) ? 1 : 0;
+        for (int it = i0; it < i1; ++it) {
+          const int4 w = a.items[it];
+          const Lattice lat = a.lats[w.x];
+          const int TX = lat.L >> 3;
+          const int tx = tid % TX, ty = tid / TX;
+          const int yt = w.z % lat.nyt, zt = w.z / lat.nyt;
+          float acc[kNumSums];
+#pragma unroll
+          for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
+          uint32_t n_acc = 0u;
+          if (is_met) {
+            tile_pass<kMetropolis>(lat, w.y, yt, zt, colour, tx, ty, ty < lat.ty, pp, sm, acc, n_acc);
+            block_count_to(pp.acc_met + lat.slot0 + w.y, n_acc, tid, B);
+          } else {
+            tile_pass<kOverrelax>(lat, w.y, yt, zt, colour, tx, ty, ty < lat.ty, pp, sm, acc, n_acc);
+          }
+          if (pp.measure) {
+            double* red = reinterpret_cast<double*>(sm + tile_plane_floats(lat.L, lat.ty));
+            const long long part = lat.part0 + static_cast<long long>(w.y) * lat.nyt * lat.nzt + w.z;
+            block_sums_to(pp.partials + part * kNumSums, acc, tid, B, red);
+          }
+        }
+        if (!grid_barrier(a, (++nbar) * G)) return;
+      }
+    }
+    if (meas || swp) {
+      FinishParams fp = a.fp;
+      fp.sweep_off = s;
+      fp.series_off = n_rec;
+      fp.swap_off = n_swp;
+      fp.record = meas ? 1 : 0;
+      fp.swap = swp ? 1 : 0;
+      for (int l = blockIdx.x; l < a.n_lat; l += gridDim.x) finish_lattice(a.lats[l], l, fp);
+      n_rec += meas ? 1 : 0;
+      n_swp += swp ? 1 : 0;
+      if (!grid_barrier(a, (++nbar) * G)) return;
+    }
+  }
+}
+
+}  // namespace xy

@@ -1,0 +1,346 @@
+"""GPU path vs the FP64 oracle, element by element on the same seeded inputs.
+
+Bit-exact: Philox draws and site indexing, execution modes (plain launches,
+CUDA graph, persistent launch), tile shapes.  Within tolerance: angles after
+half-sweeps and sweeps from a shared FP32 state (1e-5 rad; Metropolis sites
+whose accept margin |u - exp(-beta dE)| < 1e-6 are excluded and counted),
+lattice sums, exchange decisions (excluding |u - W| < 1e-6).
+"""
+
+import numpy as np
+import pytest
+
+import oracle
+from helpers import circ_dist
+
+pytestmark = pytest.mark.gpu
+
+SEED = 0x5EED2012
+TOL_RAD = 1e-5
+MARGIN = 1e-6
+
+
+def sim(L, R, betas, seed=SEED, **kw):
+    from paper_1211_0780_b300 import xy
+    return xy.Simulation(L, R, betas, seed, **kw)
+
+
+def f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def field_norm(theta):
+    c, s = np.cos(theta), np.sin(theta)
+    hx = sum(np.roll(c, sh, ax) for ax in range(3) for sh in (1, -1))
+    hy = sum(np.roll(s, sh, ax) for ax in range(3) for sh in (1, -1))
+    return np.hypot(hx, hy)
+
+
+def colour_mask(L, colour):
+    z, y, x = np.meshgrid(*(np.arange(L),) * 3, indexing="ij")
+    return ((x + y + z) % 2) == colour
+
+
+# ---------------------------------------------------------------- bit-exact parts
+
+def test_philox_draws_bit_exact():
+    s = sim([16, 24], [2, 1], [0.40, 0.50, 0.45])
+    for slot, L in ((0, 16), (1, 16), (2, 24)):
+        for colour in (0, 1):
+            for tag in (1, 2, 3):
+                for count in (0, 7, (1 << 33) + 5):
+                    g = s.debug_draws(slot, colour, tag, count)
+                    c = oracle.draw_words((L, L, L), SEED, slot, colour, tag, count)
+                    assert np.array_equal(g, c), (slot, colour, tag, count)
+
+
+def test_initial_state_matches_oracle():
+    s = sim([16, 24], [2, 1], [0.40, 0.50, 0.45])
+    angles, perm, ctr = s.get_state()
+    for slot, (L, a) in enumerate(zip((16, 16, 24), angles)):
+        ref = oracle.init_uniform((L, L, L), SEED, slot)
+        assert np.max(np.abs(a - ref)) < 1e-6
+        assert a.min() >= 0 and a.max() < 2 * np.pi
+    assert list(perm) == [0, 1, 0] and list(ctr) == [0, 0, 0, 0]
+
+
+def test_state_roundtrip_and_layout():
+    """set_state/get_state round-trip a random natural-layout state exactly."""
+    from paper_1211_0780_b300.inputs import random_angles
+    s = sim(24, 2, [0.4, 0.5])
+    st = [random_angles((24, 24, 24), 3).astype(np.float32), random_angles((24, 24, 24), 4).astype(np.float32)]
+    s.set_state(st, perm=[1, 0], counters=[5, 6, 7, 8])
+    a, p, c = s.get_state()
+    assert all(np.array_equal(x, y) for x, y in zip(a, st))
+    assert list(p) == [1, 0] and list(c) == [5, 6, 7, 8]
+
+
+# ---------------------------------------------------------------- half-sweeps
+
+@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7)), (40, (3, 16)), (32, (32, 32))])
+def test_metropolis_half_parity(L, tile):
+    """One Metropolis half-sweep of each colour from the same FP32 state."""
+    beta = 0.4542
+    s = sim(L, 1, [beta])
+    if tile:
+        s.set_tile(0, *tile)
+    th32 = s.get_state()[0][0].copy()
+    excluded = 0
+    for colour, mpass in ((0, 3), (1, 3), (0, 11)):
+        s.set_state([th32])
+        acc0 = s.accepts()[0][0]
+        s.metropolis_half(colour, mpass)
+        g = s.get_state()[0][0]
+        ref = f64(th32)
+        n_acc, margin = oracle.metropolis_half(ref, beta, SEED, 0, mpass, colour, want_margin=True)
+        close = margin < MARGIN
+        excluded += int(close.sum())
+        d = circ_dist(g, ref)
+        assert np.max(d[~close]) < TOL_RAD, (colour, np.max(d[~close]))
+        assert np.all(g[~colour_mask(L, colour)] == th32[~colour_mask(L, colour)])
+        gacc = int(s.accepts()[0][0] - acc0)
+        assert abs(gacc - n_acc) <= int(close.sum())
+        th32 = g.copy()
+    assert excluded <= max(2, 1e-4 * 3 * L ** 3 / 2)
+
+
+# Worst-case deviation of one over-relaxation update from the FP64 value on
+# the same FP32 inputs: each neighbour's fast sincos (evaluated at theta - pi)
+# is off by <= 6e-7 per component, the six-term FP32 field sum adds <= 1.2e-6,
+# so |dh| <= 6.8e-6 and the reflected angle 2 atan2(h) - theta moves by
+# <= 2 |dh| / |h| plus the rounding of atan2 and of the wrap (<= 2e-6).
+OR_A, OR_B = 1.5e-5, 2e-6
+
+
+@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7)), (40, (3, 16))])
+def test_overrelax_half_parity(L, tile):
+    """One over-relaxation half-sweep (Eq. 2) of each colour from the same
+    FP32 state, every site within the conditioning bound A/|h| + B, and 99.9%
+    of sites within 1e-5 rad."""
+    s = sim(L, 1, [0.4542])
+    if tile:
+        s.set_tile(0, *tile)
+    s.sweep(1, 1, 3)
+    th32 = s.get_state()[0][0].copy()
+    for colour in (0, 1):
+        s.set_state([th32])
+        s.overrelax_half(colour)
+        g = s.get_state()[0][0]
+        ref = f64(th32)
+        h = field_norm(ref)
+        oracle.overrelax_half(ref, colour)
+        m = colour_mask(L, colour)
+        d = circ_dist(g, ref)
+        assert np.all(d[m] <= OR_A / h[m] + OR_B), float(np.max(d[m] * h[m]))
+        assert np.quantile(d[m], 0.999) < TOL_RAD
+        assert np.all(d[~m] == 0)
+        th32 = g.copy()
+
+
+def test_overrelax_involution_and_energy():
+    """Applying the same-colour reflection twice returns the start, and the
+    lattice energy is unchanged (FP64 sums)."""
+    L = 32
+    s = sim(L, 1, [0.4542])
+    s.sweep(1, 2, 20)
+    th0 = s.get_state()[0][0].copy()
+    E0 = s.measure()["E"][0]
+    s.overrelax_half(0)
+    E1 = s.measure()["E"][0]
+    s.overrelax_half(0)
+    th2 = s.get_state()[0][0]
+    h = field_norm(f64(th0))
+    assert np.max(circ_dist(th2, th0)[h > 0.05]) < 2e-5
+    assert abs(E1 - E0) / abs(E0) < 1e-6
+
+
+def test_overrelax_energy_drift_per_sweep():
+    """Over-relaxation sweeps keep E: relative drift <= 1e-6 per sweep."""
+    L = 64
+    s = sim(L, 1, [0.4542])
+    s.sweep(1, 1, 10)
+    E = [s.measure()["E"][0]]
+    for _ in range(5):
+        s.sweep(0, 1, 1)
+        E.append(s.measure()["E"][0])
+    E = np.array(E)
+    drift = np.abs(np.diff(E)) / np.abs(E[:-1])
+    assert drift.max() < 1e-6, drift
+
+
+# ---------------------------------------------------------------- measurement
+
+def test_measure_plane_wave_closed_form():
+    L = 16
+    s = sim(L, 1, [0.4542])
+    n = (1, 2, 3)
+    z, y, x = np.meshgrid(*(np.arange(L),) * 3, indexing="ij")
+    th = np.mod(2 * np.pi * (n[0] * x + n[1] * y + n[2] * z) / L, 2 * np.pi).astype(np.float32)
+    s.set_state([th])
+    r = s.measure()[0]
+    N = L ** 3
+    for mu in range(3):
+        assert r["C"][mu] == pytest.approx(N * np.cos(2 * np.pi * n[mu] / L), abs=2e-3)
+        assert r["S"][mu] == pytest.approx(-N * np.sin(2 * np.pi * n[mu] / L), abs=2e-3)
+    assert abs(r["Mx"]) < 2e-3 and abs(r["My"]) < 2e-3
+    assert r["E"] == pytest.approx(-r["C"].sum(), rel=1e-14)
+
+
+@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7)), (48, (7, 9))])
+def test_measure_parity(L, tile):
+    s = sim(L, 2, [0.40, 0.4542])
+    if tile:
+        s.set_tile(0, *tile)
+    s.sweep(1, 2, 5)
+    rec = s.measure()
+    angles = s.get_state()[0]
+    N = L ** 3
+    for slot in range(2):
+        ref = oracle.measure(f64(angles[slot]))
+        tol = 1e-6 * 3 * N
+        assert abs(rec["E"][slot] - ref.E) < tol
+        assert abs(rec["Mx"][slot] - ref.Mx) < 1e-6 * N
+        assert abs(rec["My"][slot] - ref.My) < 1e-6 * N
+        assert np.max(np.abs(rec["C"][slot] - ref.C)) < 1e-6 * N
+        assert np.max(np.abs(rec["S"][slot] - ref.S)) < 1e-6 * N
+
+
+# ---------------------------------------------------------------- sweeps and schedule
+
+def check_sweep_by_half_sweeps(L, beta, nM, nOR, tile=None, seed=SEED):
+    """One xy_sweep equals the same half-sweeps issued one by one (bit for
+    bit), and each half-sweep agrees with the oracle's half-sweep applied to
+    the GPU's stored FP32 state before it: Metropolis sites within 1e-5 rad
+    outside accept margins < 1e-6 (counted), over-relaxation sites within the
+    conditioning bound.  (A whole sweep cannot be compared to a pure FP64
+    chain: FP32 storage alone, amplified by the reflections, moves ~2% of
+    sites by more than 1e-5 rad in one 1 + 2 sweep.)"""
+    a = sim(L, 1, [beta], seed=seed)
+    b = sim(L, 1, [beta], seed=seed)
+    if tile:
+        a.set_tile(0, *tile)
+        b.set_tile(0, *tile)
+    a.sweep(nM, nOR, 1)
+    excluded = 0
+    for m in range(nM):
+        for c in (0, 1):
+            before = f64(b.get_state()[0][0])
+            b.metropolis_half(c, m)
+            g = b.get_state()[0][0]
+            _, mg = oracle.metropolis_half(before, beta, seed, 0, m, c, want_margin=True)
+            close = mg < MARGIN
+            excluded += int(close.sum())
+            assert np.max(circ_dist(g, before)[~close]) < TOL_RAD
+    for _ in range(nOR):
+        for c in (0, 1):
+            before = f64(b.get_state()[0][0])
+            h = field_norm(before)
+            b.overrelax_half(c)
+            g = b.get_state()[0][0]
+            oracle.overrelax_half(before, c)
+            d = circ_dist(g, before)
+            assert np.all(d <= OR_A / h + OR_B)
+    assert np.array_equal(a.get_state()[0][0], b.get_state()[0][0])
+    assert excluded <= max(2, 1e-4 * L ** 3 * nM)
+    return excluded
+
+
+@pytest.mark.parametrize("nM,nOR", [(1, 2), (2, 1)])
+def test_one_sweep_from_shared_state(nM, nOR):
+    """The 16^3 workload's sweep (1 Metropolis + 2 over-relaxation passes)
+    and a two-Metropolis variant, half-sweep by half-sweep."""
+    check_sweep_by_half_sweeps(16, 0.4542, nM, nOR)
+
+
+def test_counters_and_series_records():
+    s = sim([16, 24], [3, 2], [0.40, 0.45, 0.50, 0.44, 0.46], series_capacity=64)
+    s.sweep(1, 2, 7, measure_every=2, pt_swap_every=1)
+    ctr = s.get_state()[2]
+    assert list(ctr) == [7, 7, 7, 3]
+    rec = s.read_series()
+    assert len(rec) == 3 * 5
+    assert list(rec["sweep"][::5]) == [1, 3, 5]
+    assert sorted(set(rec["slot"])) == [0, 1, 2, 3, 4]
+    assert s.read_series().size == 0
+    # a series buffer that would overflow is refused before any work
+    from paper_1211_0780_b300 import xy
+    with pytest.raises(xy.XYError):
+        s.sweep(1, 1, 200, measure_every=1)
+
+
+def test_exec_modes_bit_identical():
+    """Plain launches, the captured graph and the persistent cooperative
+    launch give the same angles, permutations and records, bit for bit."""
+    from paper_1211_0780_b300 import xy
+    Ls, Rs = [16, 24], [4, 3]
+    betas = [0.40, 0.43, 0.46, 0.49, 0.44, 0.45, 0.46]
+    outs = []
+    for mode in (xy.EXEC_PLAIN, xy.EXEC_GRAPH, xy.EXEC_PERSISTENT):
+        s = sim(Ls, Rs, betas, series_capacity=64)
+        s.set_exec(mode)
+        s.sweep(1, 2, 9, measure_every=3, pt_swap_every=1)
+        s.sweep(2, 1, 7, measure_every=3, pt_swap_every=2)
+        a, p, c = s.get_state()
+        outs.append((a, p, c, s.read_series(), s.accepts()))
+    for other in outs[1:]:
+        assert all(np.array_equal(x, y) for x, y in zip(outs[0][0], other[0]))
+        assert np.array_equal(outs[0][1], other[1])
+        assert np.array_equal(outs[0][2], other[2])
+        assert np.array_equal(outs[0][3], other[3])
+        assert np.array_equal(outs[0][4][0], other[4][0])
+        assert np.array_equal(outs[0][4][1], other[4][1])
+
+
+def test_tile_shapes_give_identical_angles():
+    res = []
+    for tile in ((16, 16), (4, 8), (5, 3), (2, 4)):
+        s = sim(40, 1, [0.4542])
+        s.set_tile(0, *tile)
+        s.sweep(1, 3, 4)
+        res.append((s.get_state()[0][0], s.measure()["E"][0]))
+    for a, E in res[1:]:
+        assert np.array_equal(a, res[0][0])
+        assert E == pytest.approx(res[0][1], rel=1e-12)
+
+
+def test_pt_swap_parity():
+    """Exchange decisions (Eq. 3) against the oracle's on the same energies."""
+    betas = np.array([0.30, 0.36, 0.42, 0.48, 0.54])
+    L = 8
+    s = sim(L, 5, betas)
+    s.sweep(1, 1, 30)
+    decided = 0
+    for event in range(12):
+        parity = event & 1
+        angles, perm, ctr = s.get_state()
+        E = np.array([oracle.measure(f64(a)).E for a in angles])
+        gE = s.measure()["E"]
+        assert np.max(np.abs(gE - E)) < 1e-6 * 3 * L ** 3
+        p_ref = perm.astype(np.int32).copy()
+        n_ref, _ = oracle.pt_swap(betas, E, p_ref, SEED, 0, int(ctr[2]), parity)
+        # skip events with a near-tie between u and W
+        tie = False
+        for k in range(parity, 4, 2):
+            a, b = perm[k], perm[k + 1]
+            w = min(1.0, np.exp((betas[k] - betas[k + 1]) * (E[a] - E[b])))
+            tie |= abs(oracle.pt_uniform(SEED, 0, int(ctr[2]), k) - w) < MARGIN
+        n = s.pt_swap(parity)
+        if not tie:
+            assert n == n_ref
+            assert np.array_equal(s.get_state()[1], p_ref)
+            decided += 1
+        s.sweep(1, 1, 2)
+    assert decided >= 10
+
+
+def test_barrier_timeout_reports_status_without_hanging():
+    """The persistent kernel's grid barrier gives up after its budget and
+    reports XY_ERR_TIMEOUT through the status word; the context stays usable."""
+    from paper_1211_0780_b300 import xy
+    s = sim(16, 2, [0.40, 0.45])
+    s.set_exec(xy.EXEC_PERSISTENT)
+    rc, st = s.debug_barrier_timeout(20000)
+    assert rc == xy.XY_ERR_TIMEOUT and st == xy.XY_ERR_TIMEOUT
+    assert s.device_status() == 0
+    s.sweep(1, 1, 3)
+    assert s.get_state()[2][1] == 3

@@ -1,0 +1,75 @@
+"""Reweighting kernels (forward, backward, autograd) vs the FP64 oracle."""
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _series(L, T, seed):
+    from paper_1211_0780_b300.inputs import synthetic_series
+    return synthetic_series(L, T, seed)
+
+
+def _oracle(s, beta0, bp, L):
+    return oracle.reweight_observables(s["E"], s["m2"], s["m4"], s["c"].T, s["s2"].T, beta0, bp, L)
+
+
+@pytest.mark.parametrize("L,T,K", [(8, 5000, 37), (32, 20000, 300), (64, 3000, 1025)])
+def test_forward_backward_match_oracle(L, T, K):
+    """All outputs and derivatives agree with the oracle to 1e-8 relative."""
+    from paper_1211_0780_b300 import xy
+    s = _series(L, T, 7 + L)
+    beta0 = 0.4542
+    bp = np.linspace(0.4530, 0.4555, K)
+    f = xy.reweight_forward(s, beta0, bp, L)
+    _, dobs = xy.reweight_backward(bp, L, f)
+    ref = _oracle(s, beta0, bp, L)
+    for key, gk in (("logZ", "logZ"), ("E", "E"), ("m2", "m2"), ("m4", "m4"), ("U", "U"), ("rhoL", "rhoL")):
+        np.testing.assert_allclose(f[gk].cpu().numpy(), ref[key], rtol=1e-10, err_msg=key)
+    np.testing.assert_allclose(dobs[0].cpu().numpy(), ref["dU"], rtol=1e-8)
+    np.testing.assert_allclose(dobs[1].cpu().numpy(), ref["drhoL"], rtol=1e-8)
+
+
+def test_non_uniform_grid_and_sign_change():
+    """Unevenly spaced beta' (no stepping) and a grid crossing beta0."""
+    from paper_1211_0780_b300 import xy
+    L, T = 16, 4000
+    s = _series(L, T, 3)
+    bp = np.sort(np.random.default_rng(1).uniform(0.4500, 0.4580, 61))
+    f = xy.reweight_forward(s, 0.4542, bp, L)
+    ref = _oracle(s, 0.4542, bp, L)
+    np.testing.assert_allclose(f["logZ"].cpu().numpy(), ref["logZ"], rtol=1e-11)
+    np.testing.assert_allclose(f["U"].cpu().numpy(), ref["U"], rtol=1e-10)
+    np.testing.assert_allclose(f["rhoL"].cpu().numpy(), ref["rhoL"], rtol=1e-10)
+
+
+def test_identity_at_beta0():
+    from paper_1211_0780_b300 import xy
+    s = _series(8, 3000, 5)
+    f = xy.reweight_forward(s, 0.4542, np.array([0.4542, 0.4542]), 8)
+    assert f["logZ"][0].item() == pytest.approx(np.log(3000), rel=1e-13)
+    assert f["m2"][0].item() == pytest.approx(float(s["m2"].astype(np.float64).mean()), rel=1e-13)
+
+
+def test_autograd_matches_finite_differences_and_fluctuation_formula():
+    """d/dbeta' through torch.autograd equals the fluctuation formula to 1e-8
+    and a central difference of the forward kernel (h = 1e-7) to 1e-6."""
+    import torch
+    from paper_1211_0780_b300 import xy
+    L, T, K = 32, 20000, 64
+    s = _series(L, T, 11)
+    bp = torch.linspace(0.4530, 0.4555, K, dtype=torch.float64, device="cuda", requires_grad=True)
+    U, R = xy.reweight(s, 0.4542, bp, L)
+    (U.sum() + 2.0 * R.sum()).backward()
+    g = bp.grad.cpu().numpy()
+    ref = _oracle(s, 0.4542, bp.detach().cpu().numpy(), L)
+    np.testing.assert_allclose(g, ref["dU"] + 2.0 * ref["drhoL"], rtol=1e-8)
+    h = 1e-7
+    b = bp.detach()
+    fp = xy.reweight_forward(s, 0.4542, b + h, L)
+    fm = xy.reweight_forward(s, 0.4542, b - h, L)
+    fd = ((fp["U"] - fm["U"]) + 2.0 * (fp["rhoL"] - fm["rhoL"])).cpu().numpy() / (2 * h)
+    np.testing.assert_allclose(g, fd, rtol=1e-6)

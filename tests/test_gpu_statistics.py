@@ -1,0 +1,55 @@
+"""Long runs: the GPU chain and the FP64 oracle chain (independent seeds)
+agree on <E>/N, the Binder ratio U_L (Eq. 5) and the helicity modulus rho_s
+(Eq. 6) within 3 sigma of the combined binned error bars (the paper's
+binning, Sec. II; smaller bins for short runs)."""
+
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def observables(E, Mx, My, C, S, N, beta, n_bins):
+    """Bin means of E/N, m^2, m^4 and the rho_s terms; U and rho_s with
+    jackknife errors over the bins."""
+    m2 = (Mx ** 2 + My ** 2) / N ** 2
+    T = (len(E) // n_bins) * n_bins
+    def bins(x):
+        return x[:T].reshape(n_bins, -1).mean(axis=1)
+    bE, b2, b4 = bins(E / N), bins(m2), bins(m2 * m2)
+    bC, bS2 = bins(C.sum(axis=1) / N), bins((S * S).sum(axis=1) / N)
+    out = {"e": (bE.mean(), bE.std(ddof=1) / np.sqrt(n_bins))}
+    def jack(f):
+        full = f(b2.mean(), b4.mean(), bC.mean(), bS2.mean())
+        reps = []
+        for i in range(n_bins):
+            k = np.ones(n_bins, bool)
+            k[i] = False
+            reps.append(f(b2[k].mean(), b4[k].mean(), bC[k].mean(), bS2[k].mean()))
+        reps = np.array(reps)
+        return full, np.sqrt((n_bins - 1) * np.mean((reps - reps.mean()) ** 2))
+    out["U"] = jack(lambda a2, a4, c, s2: 1 - a4 / (3 * a2 * a2))
+    out["rho"] = jack(lambda a2, a4, c, s2: (c - beta * s2) / 3)
+    return out
+
+
+@pytest.mark.parametrize("L,n_sweeps", [(8, 40000), (16, 8000)])
+def test_gpu_and_oracle_chains_agree(L, n_sweeps):
+    from paper_1211_0780_b300 import xy
+    beta, nM, nOR, burn = 0.4542, 1, 2, 500
+    N = L ** 3
+    sim = xy.Simulation(L, 1, [beta], seed=101, series_capacity=n_sweeps + 1)
+    sim.set_exec(xy.EXEC_GRAPH)
+    sim.sweep(nM, nOR, burn)
+    sim.sweep(nM, nOR, n_sweeps, measure_every=1)
+    r = sim.read_series()
+    g = observables(r["E"], r["Mx"], r["My"], r["C"], r["S"], N, beta, 40)
+    th = oracle.init_uniform((L, L, L), 202, 0)
+    oracle.run_chain(th, beta, 202, 0, 0, nM, nOR, burn, 0)
+    _, ser = oracle.run_chain(th, beta, 202, 0, burn, nM, nOR, n_sweeps, 1)
+    c = observables(ser[:, 0], ser[:, 1], ser[:, 2], ser[:, 3:6], ser[:, 6:9], N, beta, 40)
+    for key in ("e", "U", "rho"):
+        (a, ea), (b, eb) = g[key], c[key]
+        assert abs(a - b) < 3 * np.hypot(ea, eb), (key, a, ea, b, eb)
