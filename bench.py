@@ -189,17 +189,20 @@ def run_reference(args):
 # ---------------------------------------------------------------- GPU arm
 
 def time_kernel(fn, stream, n, warm=5):
+    """Average device time of one launch: n back-to-back launches between one
+    pair of CUDA events on the launching stream (the host enqueues faster
+    than the kernels run, so launch latency is hidden)."""
     import torch
     for _ in range(warm):
         fn()
-    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
-    for a, b in evs:
-        a.record(stream)
+    a.record(stream)
+    for _ in range(n):
         fn()
-        b.record(stream)
+    b.record(stream)
     torch.cuda.synchronize()
-    return sum(a.elapsed_time(b) for a, b in evs) / n  # ms
+    return a.elapsed_time(b) / n  # ms
 
 
 def bench_pt(steps: int, warmup: int):
@@ -264,7 +267,12 @@ def run_gpu(args):
     dev = torch.cuda.current_device()
     st = torch.cuda.current_stream()
     sim = xy.Simulation(L_MAIN, 1, [BETA_MAIN], SEED + rank, series_capacity=args.steps + args.warmup + 4)
-    tile = sim.autotune(NM_MAIN, NOR_MAIN)[0]
+    if args.tile:
+        ty, tz = (int(v) for v in args.tile.split(","))
+        sim.set_tile(0, ty, tz)
+        tile = (ty, tz)
+    else:
+        tile = sim.autotune(NM_MAIN, NOR_MAIN)[0]
     sim.set_exec(xy.EXEC_GRAPH)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -297,8 +305,12 @@ def run_gpu(args):
     launches_per_step = SWEEPS_PER_STEP * (NM_MAIN + NOR_MAIN) * 2 + 2  # half-sweeps + finish + advance
 
     # --- per-kernel durations (CUDA events on the launching stream) ----------
-    ms_or = time_kernel(lambda: sim.overrelax_half(1), st, 60)
-    ms_met = time_kernel(lambda: sim.metropolis_half(0, 1 << 40), st, 60)
+    # Graph-captured runs of one pass type: 6 sweeps of 0 + 5 passes = 60
+    # over-relaxation half-sweeps; 30 sweeps of 1 + 0 = 60 Metropolis ones
+    # (plus one counter-advance kernel each).  Average per half-sweep,
+    # including the kernel-to-kernel gaps of the graph.
+    ms_or = time_kernel(lambda: sim.sweep(0, 5, 6), st, 5) / 60
+    ms_met = time_kernel(lambda: sim.sweep(1, 0, 30), st, 5) / 60
     half = L_MAIN ** 3 // 2
     hbm, src = measured_peaks()
     ach = BYTES_PER_UPDATE * half / (ms_or * 1e-3) / 1e9
@@ -369,6 +381,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--tile", default="", help="ty,tz of the 160^3 tile (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -199,6 +199,13 @@ int xy_get_accepts(xy_ctx *ctx, uint64_t *met, uint64_t *swap);
 int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
                    uint32_t *host_words);
 
+/* Evaluates the device's reflection-angle function 2 atan2(y, x) (the one
+ * the over-relaxation kernel uses) at n points: d_out[i] = 2 atan2(d_y[i],
+ * d_x[i]), device arrays owned by the caller, ordered on `stream`; for
+ * accuracy tests.  (x, y) = (0, 0) is not a valid input. */
+int xy_debug_two_atan2(int n, const float *d_x, const float *d_y, float *d_out,
+                       void *stream);
+
 /* Tile shape of lattice `lattice`: the kernels cover ty rows x tz planes per
  * thread block (full rows in x).  xy_set_tile checks 1 <= ty, tz <= L,
  * (L/8) * ty <= the kernels' maximum block size (512 on sm_103a at their

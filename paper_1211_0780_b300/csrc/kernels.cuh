@@ -34,9 +34,12 @@ __global__ void k_init(Lattice lat, uint64_t seed) {
 }
 
 // One half-sweep of one lattice: grid (tiles per slot, R), block (L/8, ty).
-template <int MODE>
+// MEAS: the variant that fuses the lattice sums (white passes of measured
+// sweeps and the measurement-only pass).
+template <int MODE, bool MEAS>
 __global__ void k_half(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
+  chain_wait_and_release();
   const int r = blockIdx.y;
   const int t = blockIdx.x;
   const int yt = t % lat.nyt, zt = t / lat.nyt;
@@ -44,11 +47,11 @@ __global__ void k_half(Lattice lat, int colour, PassParams pp) {
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
-  tile_pass<MODE>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
+  tile_pass<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
   const int tid = threadIdx.y * blockDim.x + threadIdx.x;
   const int nth = blockDim.x * blockDim.y;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);
-  if (MODE == kMeasureOnly || (pp.measure && colour == 1)) {
+  if (MEAS) {
     double* red = reinterpret_cast<double*>(sm + tile_plane_floats(lat.L, lat.ty));
     const long long part = lat.part0 + static_cast<long long>(r) * lat.nyt * lat.nzt + t;
     block_sums_to(pp.partials + part * kNumSums, acc, tid, nth, red);
@@ -158,11 +161,18 @@ __device__ void finish_lattice(const Lattice& lat, int l, const FinishParams& fp
 
 // One block per lattice.
 __global__ void k_finish(const Lattice* lats, FinishParams fp) {
+  chain_wait_and_release();
   finish_lattice(lats[blockIdx.x], blockIdx.x, fp);
+}
+
+__global__ void k_two_atan2(int n, const float* x, const float* y, float* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = two_atan2(y[i], x[i]);
 }
 
 __global__ void k_advance(uint64_t* ctr, uint64_t d_mpass, uint64_t d_sweep, uint64_t d_swap,
                           uint64_t d_records, uint64_t d_series) {
+  chain_wait_and_release();
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     ctr[kCtrMpass] += d_mpass;
     ctr[kCtrSweep] += d_sweep;

@@ -146,7 +146,7 @@ struct xy_ctx {
   }
   PassParams pass_params(bool use_ctr, uint64_t mpass_off, int measure) const {
     PassParams p;
-    p.seed = seed;
+    p.rk = philox_round_keys(seed);
     p.ctr = use_ctr ? ctr() : nullptr;
     p.mpass_off = mpass_off;
     p.beta_slot = at<float>(lay.beta_slot);
@@ -206,6 +206,25 @@ void drop_graphs(xy_ctx* c) {
   c->plan_valid = false;
 }
 
+// Launches a kernel of the half-sweep chain with programmatic stream
+// serialization, so it is launched while its predecessor still runs and
+// starts its work (after griddepcontrol.wait) as soon as that one is done.
+template <typename... KArgs, typename... Args>
+cudaError_t launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                           Args... args) {
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 template <int MODE>
 int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams& pp) {
   const LatHost& h = c->lat[i];
@@ -213,8 +232,15 @@ int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams&
   const dim3 grid(h.nyt() * h.nzt(), h.R);
   const dim3 block(h.L / 8, h.ty);
   const int smem = tile_smem_bytes(h.L, h.ty);
-  k_half<MODE><<<grid, block, smem, st>>>(d, colour, pp);
-  XY_CHECK_LAUNCH(c);
+  constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
+  cudaError_t e;
+  if (MODE == kMeasureOnly)
+    e = launch_chained(k_half<kMeasureOnly, true>, grid, block, smem, st, d, colour, pp);
+  else if (pp.measure && colour == 1)
+    e = launch_chained(k_half<M, true>, grid, block, smem, st, d, colour, pp);
+  else
+    e = launch_chained(k_half<M, false>, grid, block, smem, st, d, colour, pp);
+  XY_TRY(c, e);
   return XY_OK;
 }
 
@@ -248,8 +274,8 @@ FinishParams finish_params(xy_ctx* c) {
 }
 
 int launch_finish(xy_ctx* c, cudaStream_t st, const FinishParams& f) {
-  k_finish<<<c->n_lat, 256, 0, st>>>(c->at<Lattice>(c->lay.lats), f);
-  XY_CHECK_LAUNCH(c);
+  XY_TRY(c, launch_chained(k_finish, dim3(c->n_lat), dim3(256), 0, st,
+                           static_cast<const Lattice*>(c->at<Lattice>(c->lay.lats)), f));
   return XY_OK;
 }
 
@@ -297,8 +323,8 @@ int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, in
     bc.records += meas ? 1 : 0;
     bc.swaps += swp ? 1 : 0;
   }
-  k_advance<<<1, 1, 0, st>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
-  XY_CHECK_LAUNCH(c);
+  XY_TRY(c, launch_chained(k_advance, dim3(1), dim3(1), 0, st, c->ctr(), bc.mpass, bc.sweeps, bc.swaps,
+                           bc.records, bc.records));
   if (out) *out = bc;
   return XY_OK;
 }
@@ -431,11 +457,12 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
   if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaDeviceGetAttribute"));
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaStreamCreateWithFlags"));
-  for (int mode = 0; mode < 3; ++mode) {
+  const void* half_kernels[5] = {
+      reinterpret_cast<const void*>(k_half<kMetropolis, false>), reinterpret_cast<const void*>(k_half<kMetropolis, true>),
+      reinterpret_cast<const void*>(k_half<kOverrelax, false>), reinterpret_cast<const void*>(k_half<kOverrelax, true>),
+      reinterpret_cast<const void*>(k_half<kMeasureOnly, true>)};
+  for (const void* fn : half_kernels) {
     // Tiles need up to ~64 KB of shared memory on the largest lattices.
-    const void* fn = mode == 0 ? reinterpret_cast<const void*>(k_half<kMetropolis>)
-                   : mode == 1 ? reinterpret_cast<const void*>(k_half<kOverrelax>)
-                               : reinterpret_cast<const void*>(k_half<kMeasureOnly>);
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncSetAttribute"));
     cudaFuncAttributes fa{};
@@ -513,8 +540,9 @@ int xy_sweep(xy_ctx* c, int nM, int nOR, int n_sweeps, int me, int se) {
 
   if (c->exec == XY_EXEC_GRAPH) {
     const int P0 = lcm_int(me > 0 ? me : 1, se > 0 ? se : 1);
-    if (P0 <= 64) {
-      const int P = P0 * std::max(1, 16 / P0);  // a graph holds P sweeps
+    if (P0 <= 64 && n_sweeps >= P0) {
+      // a graph holds P sweeps: whole periods, up to ~16 sweeps
+      const int P = P0 * std::max(1, std::min(16 / P0, n_sweeps / P0));
       int done = 0;
       while (n_sweeps - done >= P) {
         const uint64_t s = c->h_ctr[kCtrSweep];
@@ -773,6 +801,14 @@ int xy_debug_draws(xy_ctx* c, int slot, int colour, int tag, uint64_t count, uin
   XY_CHECK_LAUNCH(c);
   XY_TRY(c, cudaMemcpyAsync(host_words, dev, 2 * half * 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+int xy_debug_two_atan2(int n, const float* d_x, const float* d_y, float* d_out, void* stream) {
+  if (n <= 0 || !d_x || !d_y || !d_out) return XY_ERR_ARG;
+  k_two_atan2<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(n, d_x, d_y, d_out);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return fail_cuda(nullptr, e, "k_two_atan2");
   return XY_OK;
 }
 

@@ -113,11 +113,18 @@ __global__ void __launch_bounds__(512, 1) k_persistent(PersistentArgs a) {
 #pragma unroll
           for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
           uint32_t n_acc = 0u;
+          const bool inb = ty < lat.ty;
           if (is_met) {
-            tile_pass<kMetropolis>(lat, w.y, yt, zt, colour, tx, ty, ty < lat.ty, pp, sm, acc, n_acc);
+            if (pp.measure)
+              tile_pass<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
+            else
+              tile_pass<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
             block_count_to(pp.acc_met + lat.slot0 + w.y, n_acc, tid, B);
           } else {
-            tile_pass<kOverrelax>(lat, w.y, yt, zt, colour, tx, ty, ty < lat.ty, pp, sm, acc, n_acc);
+            if (pp.measure)
+              tile_pass<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
+            else
+              tile_pass<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
           }
           if (pp.measure) {
             double* red = reinterpret_cast<double*>(sm + tile_plane_floats(lat.L, lat.ty));

@@ -31,6 +31,37 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 c, PhiloxKey key) {
   return c;
 }
 
+// The ten round keys of a seed, computed once on the host and passed as a
+// kernel parameter: the XOR with the round key then reads its operand from
+// the constant bank instead of recomputing the key schedule per call.
+struct PhiloxRoundKeys {
+  uint32_t k0[10];
+  uint32_t k1[10];
+};
+
+__host__ __device__ inline PhiloxRoundKeys philox_round_keys(uint64_t seed) {
+  PhiloxRoundKeys rk;
+  uint32_t a = static_cast<uint32_t>(seed), b = static_cast<uint32_t>(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k0[r] = a;
+    rk.k1[r] = b;
+    a += 0x9E3779B9u;
+    b += 0xBB67AE85u;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const PhiloxRoundKeys& rk) {
+#pragma unroll
+  for (int round = 0; round < 10; ++round) {
+    const unsigned long long a = static_cast<unsigned long long>(c.x) * 0xD2511F53ull;
+    const unsigned long long b = static_cast<unsigned long long>(c.z) * 0xCD9E8D57ull;
+    c = make_uint4(static_cast<uint32_t>(b >> 32) ^ c.y ^ rk.k0[round], static_cast<uint32_t>(b),
+                   static_cast<uint32_t>(a >> 32) ^ c.w ^ rk.k1[round], static_cast<uint32_t>(a));
+  }
+  return c;
+}
+
 // 24-bit uniform in [0, 1); exact in FP32 (and FP64).
 __device__ __forceinline__ float u24(uint32_t w) {
   return static_cast<float>(w >> 8) * 5.9604644775390625e-8f;  // 2^-24

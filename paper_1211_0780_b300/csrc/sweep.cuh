@@ -19,11 +19,13 @@
 // through three shared-memory buffers (one barrier per plane) for the y
 // neighbours and the x halo element.  The thread rows at the tile's y edges
 // also evaluate the halo rows y0-1 and y0+ty.  Cost per update:
-// (ty+2)(tz+2)/(ty tz) sincos evaluations instead of six.
+// (ty+2)(tz+2)/(ty tz) sincos evaluations instead of six.  The plane loop is
+// unrolled three times so the register planes and the buffer indices rotate
+// without copies.
 //
 // Accuracy.  Angles live in [0, 2 pi); the fast sincos is evaluated at
 // theta - pi, inside [-pi, pi) where its absolute error is ~2^-21.4, and
-// negated.
+// negated.  The reflection angle uses the polynomial two_atan2 below.
 #pragma once
 #include <cstdint>
 
@@ -33,6 +35,7 @@ namespace xy {
 
 constexpr float kPi = 3.14159265358979323846f;
 constexpr float kTwoPi = 6.28318530717958647692f;
+constexpr float kTwoPiOver2p24 = 6.28318530717958647692f / 16777216.0f;  // exact scaling
 constexpr uint32_t kTagInit = 1u, kTagMet = 2u, kTagPt = 3u;
 constexpr int kNumSums = 8;                       // Mx, My, Cx, Cy, Cz, Sx, Sy, Sz
 constexpr int kReduceBytes = kNumSums * 32 * 8;   // per-warp FP64 partials
@@ -63,7 +66,7 @@ struct Lattice {
 };
 
 struct PassParams {
-  uint64_t seed;
+  PhiloxRoundKeys rk;           // round keys of the seed
   const uint64_t* ctr;          // device counters (may be null: mpass_off absolute)
   uint64_t mpass_off;           // pass counter = ctr[kCtrMpass] + mpass_off
   const float* beta_slot;       // FP32 beta of every global slot
@@ -79,11 +82,44 @@ __host__ __device__ inline int tile_smem_bytes(int L, int ty) {
   return tile_plane_floats(L, ty) * 4 + kReduceBytes;
 }
 
+// Programmatic dependent launch: a kernel of the half-sweep chain waits for
+// its predecessor's results (griddepcontrol.wait returns once the previous
+// grid has completed and its memory is visible; it is a no-op for launches
+// without the attribute), then lets its own successor be launched early.
+__device__ __forceinline__ void chain_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __device__ __forceinline__ void spin(float th, float& c, float& s) {
   float sn, cs;
   __sincosf(th - kPi, &sn, &cs);
   c = -cs;
   s = -sn;
+}
+
+// 2 atan2(y, x) in [-2 pi, 2 pi] for (x, y) != (0, 0): octant reduction to
+// r = min(|x|,|y|) / max(|x|,|y|) in [0, 1], then 2 atan(r) = r P(r^2) with a
+// degree-7 polynomial in r^2 fitted to 2 atan(r) / r on [0, 1] (weighted
+// least squares iterated towards the minimax error; |error| of atan <=
+// 3.8e-8 in exact arithmetic, <= 1.5e-7 with FP32 Horner), then the octant
+// and quadrant reflections.  Tested against atan2f over the plane.
+__device__ __forceinline__ float two_atan2(float y, float x) {
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float r = __fdividef(fminf(ax, ay), fmaxf(ax, ay));
+  const float s = r * r;
+  float p = -8.109124919e-03f;
+  p = fmaf(p, s, 4.372588046e-02f);
+  p = fmaf(p, s, -1.118246012e-01f);
+  p = fmaf(p, s, 1.928439072e-01f);
+  p = fmaf(p, s, -2.781725752e-01f);
+  p = fmaf(p, s, 3.989313098e-01f);
+  p = fmaf(p, s, -6.665972154e-01f);
+  p = fmaf(p, s, 1.999998671e+00f);
+  float q = p * r;                       // 2 atan(r), in [0, pi/2]
+  q = (ay > ax) ? (kPi - q) : q;         // first quadrant: 2 phi
+  q = (x < 0.f) ? (kTwoPi - q) : q;      // second quadrant: 2 (pi - phi')
+  return copysignf(q, y);                // lower half plane: -2 phi'
 }
 
 struct Spins4 {
@@ -118,80 +154,125 @@ __device__ __forceinline__ float comp(const float4& v, int e) {
   return e == 0 ? v.x : (e == 1 ? v.y : (e == 2 ? v.z : v.w));
 }
 
+template <int N>
+struct IC {
+  static constexpr int value = N;
+};
+
+// Per-thread accumulators of the fused lattice sums (present only in the
+// measuring variants).
+template <bool MEAS>
+struct SumAcc {
+  __device__ __forceinline__ void add_plane(const float*) {}
+  __device__ __forceinline__ void export_to(float*) const {}
+};
+template <>
+struct SumAcc<true> {
+  float acc[kNumSums];
+  float err[kNumSums];
+  __device__ __forceinline__ SumAcc() {
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) acc[j] = err[j] = 0.f;
+  }
+  // Compensated (Kahan) accumulation of one plane's terms, so the per-thread
+  // FP32 sums stay within a few roundings of the terms whatever the depth.
+  __device__ __forceinline__ void add_plane(const float* step) {
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) {
+      const float yv = step[j] - err[j];
+      const float t = acc[j] + yv;
+      err[j] = (t - acc[j]) - yv;
+      acc[j] = t;
+    }
+  }
+  __device__ __forceinline__ void export_to(float* out) const {
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) out[j] = acc[j];
+  }
+};
+
 // One tile of one half-sweep of colour `colour` on local slot r.
 // (tx, ty): thread coordinates, tx in [0, L/8); in_block = the thread maps
 // onto the tile at all (the persistent kernel's flat blocks have spares).
 // Every thread of the block must call this (it contains barriers).
-// acc[] receives this thread's FP32 lattice-sum partials when measuring;
+// acc_out[] receives this thread's FP32 lattice-sum partials (MEAS);
 // n_acc its accepted Metropolis proposals.
-template <int MODE>
+template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int zt, int colour,
                                           int tx, int ty, bool in_block, const PassParams& pp,
-                                          float* sm, float acc[kNumSums], uint32_t& n_acc) {
+                                          float* sm, float* acc_out, uint32_t& n_acc) {
+  static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
   const int L = lat.L;
   const int H = L >> 1;
-  const long long N = static_cast<long long>(L) * L * L;
+  const uint32_t PS = static_cast<uint32_t>(H) * static_cast<uint32_t>(L);  // plane stride
+  const uint32_t half = PS * static_cast<uint32_t>(L);                       // N / 2
   const int y0 = yt * lat.ty, z0 = zt * lat.tz;
   const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
   const bool act = in_block && ty < TYa;
   const int y = y0 + ty;
-  float* own = lat.angles + r * N + colour * (N >> 1);
-  const float* oth = lat.angles + r * N + (colour ^ 1) * (N >> 1);
+  float* const slot = lat.angles + static_cast<size_t>(r) * (2 * static_cast<size_t>(half));
+  float* const own = slot + colour * half;
+  const float* const oth = slot + (colour ^ 1) * half;
   const int rows = lat.ty + 2;
   const int ym = (y0 == 0 ? L : y0) - 1;          // halo row y0 - 1 (periodic)
   const int yp = (y0 + TYa == L) ? 0 : y0 + TYa;  // halo row y0 + TYa
   const bool top = act && ty == 0;
   const bool bot = act && ty == TYa - 1;
-  const bool meas = (MODE == kMeasureOnly) || (pp.measure && colour == 1);
-  auto idx = [&](int yy, int zz) -> long long {
-    return static_cast<long long>(H) * (yy + static_cast<long long>(L) * zz) + 4 * tx;
-  };
+  const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
+  const uint32_t offym = static_cast<uint32_t>(H * ym + 4 * tx);
+  const uint32_t offyp = static_cast<uint32_t>(H * yp + 4 * tx);
   auto row_ptr = [&](int b, int rr) -> float* { return sm + (b * rows + rr) * 2 * H; };
+  // x-halo element of this thread's row: k = 4 tx - 1 (s = 0) or 4 tx + 4 (s = 1)
+  const int kh0 = (tx == 0) ? H - 1 : 4 * tx - 1;
+  const int kh1 = (4 * tx + 4 == H) ? 0 : 4 * tx + 4;
 
   float beta = 0.f;
-  PhiloxKey key{0u, 0u};
-  uint32_t tagw = 0u;
-  uint64_t mp = 0ull;
+  uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
   if (MODE == kMetropolis) {
     beta = __ldcg(pp.beta_slot + lat.slot0 + r);
-    key = philox_key(pp.seed);
     tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) |
            kTagMet;
-    mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    mlo = static_cast<uint32_t>(mp);
+    mhi = static_cast<uint32_t>(mp >> 32);
   }
+  SumAcc<MEAS> sums;
 
-  Spins4 zm{}, zc{}, zn{};  // other colour, own column: planes z-1, z, z+1
+  Spins4 pa{}, pb{}, pc{};  // rotating register planes (other colour, own column)
   float4 nx_oth = make_float4(0.f, 0.f, 0.f, 0.f), nx_own = nx_oth, nx_h0 = nx_oth, nx_h1 = nx_oth;
   if (act) {
-    const int zb = (z0 == 0 ? L : z0) - 1;
-    const int z1 = (z0 + 1 == L) ? 0 : z0 + 1;
-    zm = spins4(ld4(oth + idx(y, zb)));
-    zc = spins4(ld4(oth + idx(y, z0)));
-    put_row(row_ptr(0, ty + 1), H, tx, zc);
-    if (top) put_row(row_ptr(0, 0), H, tx, spins4(ld4(oth + idx(ym, z0))));
-    if (bot) put_row(row_ptr(0, TYa + 1), H, tx, spins4(ld4(oth + idx(yp, z0))));
-    nx_oth = ld4(oth + idx(y, z1));
-    nx_own = ld4(own + idx(y, z0));
+    const uint32_t zb = static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS;
+    const uint32_t zz = static_cast<uint32_t>(z0) * PS;
+    const uint32_t z1 = static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS;
+    pa = spins4(ld4(oth + offy + zb));
+    pb = spins4(ld4(oth + offy + zz));
+    put_row(row_ptr(0, ty + 1), H, tx, pb);
+    if (top) put_row(row_ptr(0, 0), H, tx, spins4(ld4(oth + offym + zz)));
+    if (bot) put_row(row_ptr(0, TYa + 1), H, tx, spins4(ld4(oth + offyp + zz)));
+    nx_oth = ld4(oth + offy + z1);
+    nx_own = ld4(own + offy + zz);
     if (TZa > 1) {
-      if (top) nx_h0 = ld4(oth + idx(ym, z1));
-      if (bot) nx_h1 = ld4(oth + idx(yp, z1));
+      if (top) nx_h0 = ld4(oth + offym + z1);
+      if (bot) nx_h1 = ld4(oth + offyp + z1);
     }
   }
   __syncthreads();
 
-  int b0 = 0, b1 = 1;
-  for (int i = 0; i < TZa; ++i) {
+  // One plane: zm, zc = planes z-1, z (registers); zn receives plane z+1.
+  auto step = [&](auto bc, Spins4& zm, Spins4& zc, Spins4& zn, int i) {
+    constexpr int b0 = decltype(bc)::value;
+    constexpr int b1 = b0 == 2 ? 0 : b0 + 1;
     const int z = z0 + i;
     if (act) {
       const float4 t_oth = nx_oth, t_own = nx_own, t_h0 = nx_h0, t_h1 = nx_h1;
       if (i + 1 < TZa) {  // prefetch the next plane's operands
-        const int z1 = z + 1;
-        const int z2 = (z1 + 1 == L) ? 0 : z1 + 1;
-        nx_oth = ld4(oth + idx(y, z2));
-        nx_own = ld4(own + idx(y, z1));
+        const uint32_t pz1 = static_cast<uint32_t>(z + 1) * PS;
+        const uint32_t pz2 = static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS;
+        nx_oth = ld4(oth + offy + pz2);
+        nx_own = ld4(own + offy + pz1);
         if (i + 2 < TZa) {
-          if (top) nx_h0 = ld4(oth + idx(ym, z2));
-          if (bot) nx_h1 = ld4(oth + idx(yp, z2));
+          if (top) nx_h0 = ld4(oth + offym + pz2);
+          if (bot) nx_h1 = ld4(oth + offyp + pz2);
         }
       }
       zn = spins4(t_oth);
@@ -208,7 +289,7 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
       const float4 ypc = reinterpret_cast<const float4*>(rp)[tx];
       const float4 yps = reinterpret_cast<const float4*>(rp + H)[tx];
       const int s = (y + z + colour) & 1;
-      const int kh = s ? ((4 * tx + 4 == H) ? 0 : 4 * tx + 4) : (tx == 0 ? H - 1 : 4 * tx - 1);
+      const int kh = s ? kh1 : kh0;
       const float hc = r0[kh], hs = r0[H + kh];
       // X[e] = the -x neighbour of site e, X[e+1] its +x neighbour.
       float Xc[5], Xs[5];
@@ -220,15 +301,18 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
         Xc[e] = s ? a_c : b_c;
         Xs[e] = s ? a_s : b_s;
       }
+      const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
       const float th[4] = {t_own.x, t_own.y, t_own.z, t_own.w};
       float tn[4], nc[4], ns[4];
       uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
       if (MODE == kMetropolis) {
-        const uint32_t q0 = static_cast<uint32_t>(idx(y, z) >> 1);
-        const uint32_t mlo = static_cast<uint32_t>(mp), mhi = static_cast<uint32_t>(mp >> 32);
-        w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), key);
-        w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), key);
+        const uint32_t q0 = offz >> 1;
+        w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+        w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
       }
+      float stepv[kNumSums];
+#pragma unroll
+      for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float hx = (Xc[e] + Xc[e + 1]) + (comp(ymc, e) + comp(ypc, e)) + (zm.c[e] + zn.c[e]);
@@ -237,13 +321,14 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
           const uint4& w = (e < 2) ? w0 : w1;
           const uint32_t wprop = (e & 1) ? w.z : w.x;
           const uint32_t wacc = (e & 1) ? w.w : w.y;
-          const float tp = u24(wprop) * kTwoPi;
+          const float tp = static_cast<float>(wprop >> 8) * kTwoPiOver2p24;  // = u0 * 2 pi
           float cp, sp, co, so;
           spin(tp, cp, sp);
           spin(th[e], co, so);
           // -beta dE with dE = -[h_x (cos t' - cos t) + h_y (sin t' - sin t)]
           const float x = beta * (hx * (cp - co) + hy * (sp - so));
-          const bool accept = u24(wacc) < __expf(x);
+          // u1 < exp(x)  <=>  (w >> 8) < exp(x) 2^24 (exact scaling)
+          const bool accept = static_cast<float>(wacc >> 8) < __expf(x) * 16777216.0f;
           n_acc += accept ? 1u : 0u;
           tn[e] = accept ? tp : th[e];
           nc[e] = accept ? cp : co;
@@ -251,42 +336,48 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
         } else if (MODE == kOverrelax) {
           float t = th[e];
           if (hx != 0.f || hy != 0.f) {
-            t = fmaf(2.f, atan2f(hy, hx), -th[e]);  // reflection about the field
+            t = two_atan2(hy, hx) - th[e];  // reflection about the field
             if (t < 0.f) t += kTwoPi;
             if (t < 0.f) t += kTwoPi;
             if (t >= kTwoPi) t -= kTwoPi;
           }
           tn[e] = t;
-          if (meas) spin(t, nc[e], ns[e]);
+          if (MEAS) spin(t, nc[e], ns[e]);
         } else {
           tn[e] = th[e];
           spin(th[e], nc[e], ns[e]);
         }
-        if (meas) {
+        if (MEAS) {
           // Bonds (w, w+mu) and (w-mu, w) of the white site w: every bond has
           // exactly one white end, so each is counted once.
           const float c = nc[e], sn = ns[e];
           const float pxc = Xc[e + 1], qxc = Xc[e], pxs = Xs[e + 1], qxs = Xs[e];
           const float pyc = comp(ypc, e), qyc = comp(ymc, e), pys = comp(yps, e), qys = comp(yms, e);
           const float pzc = zn.c[e], qzc = zm.c[e], pzs = zn.s[e], qzs = zm.s[e];
-          acc[0] += c + zc.c[e];  // white site + the black site of this column
-          acc[1] += sn + zc.s[e];
-          acc[2] += c * (pxc + qxc) + sn * (pxs + qxs);
-          acc[3] += c * (pyc + qyc) + sn * (pys + qys);
-          acc[4] += c * (pzc + qzc) + sn * (pzs + qzs);
-          acc[5] += sn * (pxc - qxc) - c * (pxs - qxs);
-          acc[6] += sn * (pyc - qyc) - c * (pys - qys);
-          acc[7] += sn * (pzc - qzc) - c * (pzs - qzs);
+          stepv[0] += c + zc.c[e];  // white site + the black site of this column
+          stepv[1] += sn + zc.s[e];
+          stepv[2] += c * (pxc + qxc) + sn * (pxs + qxs);
+          stepv[3] += c * (pyc + qyc) + sn * (pys + qys);
+          stepv[4] += c * (pzc + qzc) + sn * (pzs + qzs);
+          stepv[5] += sn * (pxc - qxc) - c * (pxs - qxs);
+          stepv[6] += sn * (pyc - qyc) - c * (pys - qys);
+          stepv[7] += sn * (pzc - qzc) - c * (pzs - qzs);
         }
       }
-      if (MODE != kMeasureOnly) st4(own + idx(y, z), make_float4(tn[0], tn[1], tn[2], tn[3]));
+      if (MEAS) sums.add_plane(stepv);
+      if (MODE != kMeasureOnly) st4(own + offz, make_float4(tn[0], tn[1], tn[2], tn[3]));
     }
-    zm = zc;
-    zc = zn;
-    b0 = b0 == 2 ? 0 : b0 + 1;
-    b1 = b1 == 2 ? 0 : b1 + 1;
     __syncthreads();
+  };
+
+  for (int i = 0; i < TZa; i += 3) {
+    step(IC<0>{}, pa, pb, pc, i);
+    if (i + 1 >= TZa) break;
+    step(IC<1>{}, pb, pc, pa, i + 1);
+    if (i + 2 >= TZa) break;
+    step(IC<2>{}, pc, pa, pb, i + 2);
   }
+  if (MEAS) sums.export_to(acc_out);
 }
 
 // Fixed-order block reduction of the FP32 partials into FP64 (a deterministic

@@ -1,0 +1,47 @@
+"""A small, fixed launch sequence of one half-sweep kernel, for profilers.
+
+python -m paper_1211_0780_b300.profile_case --L 160 --ty 10 --tz 16 --mode or --launches 5
+
+Creates one lattice (seeded hot start), runs a few warm-up sweeps, then
+issues `--launches` half-sweeps of the chosen kernel (or = over-relaxation,
+met = Metropolis, meas = measurement-only) and synchronises.  No autotuning,
+so the launch list is short and deterministic.
+"""
+
+import argparse
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, default=160)
+    ap.add_argument("--R", type=int, default=1)
+    ap.add_argument("--ty", type=int, default=0)
+    ap.add_argument("--tz", type=int, default=0)
+    ap.add_argument("--mode", default="or", choices=["or", "met", "meas", "sweep"])
+    ap.add_argument("--launches", type=int, default=5)
+    ap.add_argument("--warm-sweeps", type=int, default=2)
+    args = ap.parse_args()
+    import torch
+    from paper_1211_0780_b300 import xy
+    betas = np.linspace(0.4542, 0.4560, args.R) if args.R > 1 else [0.4542]
+    sim = xy.Simulation(args.L, args.R, betas, 0x5EED2012)
+    if args.ty and args.tz:
+        sim.set_tile(0, args.ty, args.tz)
+    sim.sweep(1, 1, args.warm_sweeps)
+    for i in range(args.launches):
+        if args.mode == "or":
+            sim.overrelax_half(i & 1)
+        elif args.mode == "met":
+            sim.metropolis_half(i & 1, 1000 + i)
+        elif args.mode == "meas":
+            sim.measure()
+        else:
+            sim.sweep(1, 5, 1)
+    torch.cuda.synchronize()
+    print("tile", sim.get_tile(0), "done")
+
+
+if __name__ == "__main__":
+    main()

@@ -70,6 +70,7 @@ _SIGNATURES = {
     "xy_get_packed": (_I, [_P, _P]),
     "xy_set_packed": (_I, [_P, _P]),
     "xy_debug_draws": (_I, [_P, _I, _I, _I, _U64, _P]),
+    "xy_debug_two_atan2": (_I, [_I, _P, _P, _P, _P]),
     "xy_set_tile": (_I, [_P, _I, _I, _I]),
     "xy_get_tile": (_I, [_P, _I, _P, _P]),
     "xy_autotune": (_I, [_P, _I, _I]),
@@ -290,6 +291,17 @@ class Simulation:
         return int(rc), int(s.value)
 
 
+def debug_two_atan2(x, y) -> np.ndarray:
+    """The device's 2 atan2(y, x) at the given points (accuracy tests)."""
+    torch = _require_cuda()
+    xd = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
+    yd = torch.as_tensor(np.ascontiguousarray(y, dtype=np.float32), device="cuda")
+    out = torch.empty_like(xd)
+    _check(lib().xy_debug_two_atan2(xd.numel(), xd.data_ptr(), yd.data_ptr(), out.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream), "xy_debug_two_atan2")
+    return out.cpu().numpy()
+
+
 # ---------------------------------------------------------------------------
 # Single-histogram reweighting (FP64), forward and backward kernels
 # ---------------------------------------------------------------------------
@@ -351,8 +363,12 @@ def reweight_backward(betap, L: int, fwd, gU=None, grhoL=None):
     K = bp.numel()
     dobs = torch.empty((2, K), dtype=torch.float64, device="cuda")
     grad = torch.empty(K, dtype=torch.float64, device="cuda") if (gU is not None or grhoL is not None) else None
-    gUp = gU.contiguous().data_ptr() if gU is not None else None
-    gRp = grhoL.contiguous().data_ptr() if grhoL is not None else None
+    # Keep the contiguous copies alive until the kernel has been enqueued on
+    # this stream (the caching allocator then orders any reuse after it).
+    gUc = gU.to(torch.float64).contiguous() if gU is not None else None
+    gRc = grhoL.to(torch.float64).contiguous() if grhoL is not None else None
+    gUp = gUc.data_ptr() if gUc is not None else None
+    gRp = gRc.data_ptr() if gRc is not None else None
     st = torch.cuda.current_stream().cuda_stream
     _check(lib().xy_reweight_backward(K, bp.data_ptr(), int(L), fwd["_out"].data_ptr(),
                                       fwd["_cov"].data_ptr(), gUp, gRp,

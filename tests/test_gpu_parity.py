@@ -18,6 +18,10 @@ pytestmark = pytest.mark.gpu
 SEED = 0x5EED2012
 TOL_RAD = 1e-5
 MARGIN = 1e-6
+# Error of one term of the fused lattice sums: a bond term cos(a - b) =
+# ca cb + sa sb from fast sincos values (<= 6e-7 each) is off by <= 2e-6, a
+# site term by <= 1e-6; FP64 accumulation adds nothing at these sizes.
+BOND_TOL, SITE_TOL = 2e-6, 1e-6
 
 
 def sim(L, R, betas, seed=SEED, **kw):
@@ -73,6 +77,26 @@ def test_state_roundtrip_and_layout():
     a, p, c = s.get_state()
     assert all(np.array_equal(x, y) for x, y in zip(a, st))
     assert list(p) == [1, 0] and list(c) == [5, 6, 7, 8]
+
+
+def test_two_atan2_error_bound():
+    """The reflection angle 2 atan2(y, x) of the over-relaxation kernel is
+    within 8e-7 rad of the FP64 value over the plane (all octants, signed
+    zeros, magnitudes 1e-3..6, the range of the local field): twice the
+    polynomial (1.5e-7) and division (1.2e-7) errors plus the final FP32
+    rounding near 2 pi (2.4e-7)."""
+    from paper_1211_0780_b300 import xy
+    rng = np.random.default_rng(5)
+    r = 10 ** rng.uniform(-3, np.log10(6.0), 200000)
+    a = rng.uniform(-np.pi, np.pi, 200000)
+    x = np.concatenate([r * np.cos(a), [1, -1, 0, 0, 2, -2, 3, -3]]).astype(np.float32)
+    y = np.concatenate([r * np.sin(a), [0, 0, 1, -1, 2, 2, -3, -3]]).astype(np.float32)
+    y[-8] = -0.0
+    g = xy.debug_two_atan2(x, y).astype(np.float64)
+    ref = 2 * np.arctan2(y.astype(np.float64), x.astype(np.float64))
+    d = np.abs(np.mod(g - ref + np.pi, 2 * np.pi) - np.pi)
+    assert d.max() < 8e-7, d.max()
+    assert np.all(np.abs(g) <= 2 * np.pi + 1e-6)
 
 
 # ---------------------------------------------------------------- half-sweeps
@@ -179,10 +203,13 @@ def test_measure_plane_wave_closed_form():
     s.set_state([th])
     r = s.measure()[0]
     N = L ** 3
+    # Every bond has the same angle difference here, so the per-term error of
+    # the fast sincos products (<= 2e-6 per bond, <= 1e-6 per site) adds
+    # coherently: the bounds scale with N.
     for mu in range(3):
-        assert r["C"][mu] == pytest.approx(N * np.cos(2 * np.pi * n[mu] / L), abs=2e-3)
-        assert r["S"][mu] == pytest.approx(-N * np.sin(2 * np.pi * n[mu] / L), abs=2e-3)
-    assert abs(r["Mx"]) < 2e-3 and abs(r["My"]) < 2e-3
+        assert r["C"][mu] == pytest.approx(N * np.cos(2 * np.pi * n[mu] / L), abs=BOND_TOL * N)
+        assert r["S"][mu] == pytest.approx(-N * np.sin(2 * np.pi * n[mu] / L), abs=BOND_TOL * N)
+    assert abs(r["Mx"]) < SITE_TOL * N and abs(r["My"]) < SITE_TOL * N
     assert r["E"] == pytest.approx(-r["C"].sum(), rel=1e-14)
 
 
@@ -197,12 +224,11 @@ def test_measure_parity(L, tile):
     N = L ** 3
     for slot in range(2):
         ref = oracle.measure(f64(angles[slot]))
-        tol = 1e-6 * 3 * N
-        assert abs(rec["E"][slot] - ref.E) < tol
-        assert abs(rec["Mx"][slot] - ref.Mx) < 1e-6 * N
-        assert abs(rec["My"][slot] - ref.My) < 1e-6 * N
-        assert np.max(np.abs(rec["C"][slot] - ref.C)) < 1e-6 * N
-        assert np.max(np.abs(rec["S"][slot] - ref.S)) < 1e-6 * N
+        assert abs(rec["E"][slot] - ref.E) < BOND_TOL * 3 * N
+        assert abs(rec["Mx"][slot] - ref.Mx) < SITE_TOL * N
+        assert abs(rec["My"][slot] - ref.My) < SITE_TOL * N
+        assert np.max(np.abs(rec["C"][slot] - ref.C)) < BOND_TOL * N
+        assert np.max(np.abs(rec["S"][slot] - ref.S)) < BOND_TOL * N
 
 
 # ---------------------------------------------------------------- sweeps and schedule
@@ -300,7 +326,8 @@ def test_tile_shapes_give_identical_angles():
         res.append((s.get_state()[0][0], s.measure()["E"][0]))
     for a, E in res[1:]:
         assert np.array_equal(a, res[0][0])
-        assert E == pytest.approx(res[0][1], rel=1e-12)
+        # FP32 per-thread partials (compensated) group differently per tile
+        assert E == pytest.approx(res[0][1], rel=1e-8)
 
 
 def test_pt_swap_parity():
@@ -315,7 +342,7 @@ def test_pt_swap_parity():
         angles, perm, ctr = s.get_state()
         E = np.array([oracle.measure(f64(a)).E for a in angles])
         gE = s.measure()["E"]
-        assert np.max(np.abs(gE - E)) < 1e-6 * 3 * L ** 3
+        assert np.max(np.abs(gE - E)) < BOND_TOL * 3 * L ** 3
         p_ref = perm.astype(np.int32).copy()
         n_ref, _ = oracle.pt_swap(betas, E, p_ref, SEED, 0, int(ctr[2]), parity)
         # skip events with a near-tie between u and W

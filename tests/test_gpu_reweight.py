@@ -29,8 +29,10 @@ def test_forward_backward_match_oracle(L, T, K):
     ref = _oracle(s, beta0, bp, L)
     for key, gk in (("logZ", "logZ"), ("E", "E"), ("m2", "m2"), ("m4", "m4"), ("U", "U"), ("rhoL", "rhoL")):
         np.testing.assert_allclose(f[gk].cpu().numpy(), ref[key], rtol=1e-10, err_msg=key)
-    np.testing.assert_allclose(dobs[0].cpu().numpy(), ref["dU"], rtol=1e-8)
-    np.testing.assert_allclose(dobs[1].cpu().numpy(), ref["drhoL"], rtol=1e-8)
+    # Relative to each curve's scale: dU/dbeta' crosses zero inside the grid.
+    for row, key in ((0, "dU"), (1, "drhoL")):
+        np.testing.assert_allclose(dobs[row].cpu().numpy(), ref[key], rtol=1e-8,
+                                   atol=1e-8 * np.max(np.abs(ref[key])))
 
 
 def test_non_uniform_grid_and_sign_change():
@@ -66,10 +68,11 @@ def test_autograd_matches_finite_differences_and_fluctuation_formula():
     (U.sum() + 2.0 * R.sum()).backward()
     g = bp.grad.cpu().numpy()
     ref = _oracle(s, 0.4542, bp.detach().cpu().numpy(), L)
-    np.testing.assert_allclose(g, ref["dU"] + 2.0 * ref["drhoL"], rtol=1e-8)
+    want = ref["dU"] + 2.0 * ref["drhoL"]
+    np.testing.assert_allclose(g, want, rtol=1e-8, atol=1e-8 * np.max(np.abs(want)))
     h = 1e-7
     b = bp.detach()
     fp = xy.reweight_forward(s, 0.4542, b + h, L)
     fm = xy.reweight_forward(s, 0.4542, b - h, L)
     fd = ((fp["U"] - fm["U"]) + 2.0 * (fp["rhoL"] - fm["rhoL"])).cpu().numpy() / (2 * h)
-    np.testing.assert_allclose(g, fd, rtol=1e-6)
+    np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-6 * np.max(np.abs(fd)))
