@@ -265,6 +265,32 @@ int xy_reweight_forward(int64_t T, const double *d_E, const float *d_m2,
                         double *d_out, double *d_obs, double *d_cov,
                         void *d_scratch, size_t scratch_bytes, void *stream);
 
+/* Allocation-free forward pass.  The paper has no counterpart: this entry
+ * point exists for callers that cannot give the library scratch memory --
+ * code working inside a device-memory budget fixed at start-up, code that
+ * must not call the CUDA allocator (or a framework's caching allocator)
+ * once running, and plugins whose host framework owns every device
+ * allocation.  It computes exactly what xy_reweight_forward computes (same
+ * kernels, outputs equal to FP64 rounding) but takes its scratch from one
+ * library-owned device array of xy_reweight_noalloc_capacity_bytes() bytes
+ * (8 MiB), which every GPU that loads the library holds until the process
+ * exits.  The number of sample chunks is capped so their partial sums fit:
+ * K may be at most about 95,000 target couplings; larger K returns
+ * XY_ERR_NOMEM (T is unrestricted).  The call allocates nothing.  It runs on
+ * the device that owns d_out (made current) and, on its first call on a
+ * device, looks up the array's device address -- make that first call
+ * before any stream capture.  Every call shares the array and leaves its
+ * contents behind; nothing needs clearing because each call writes every
+ * word it later reads, but calls that overlap on the GPU race.  Errors as
+ * for xy_reweight_forward. */
+size_t xy_reweight_noalloc_capacity_bytes(void);
+
+int xy_reweight_forward_noalloc(int64_t T, const double *d_E, const float *d_m2,
+                                const float *d_m4, const float *d_c,
+                                const float *d_s2, double beta0, int K,
+                                const double *d_betap, int L, double *d_out,
+                                double *d_obs, double *d_cov, void *stream);
+
 /* Backward: given upstream gradients g_U[K] and g_rhoL[K] (device f64) and
  * the forward's d_out, d_cov, returns grad_betap[K] = g_U dU/dbeta' +
  * g_rhoL d(rho_s L)/dbeta' (each output depends only on its own beta'_k).

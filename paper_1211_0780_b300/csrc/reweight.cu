@@ -27,6 +27,7 @@
 #include <cmath>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 
 #include "../../include/xy.h"
 
@@ -298,6 +299,107 @@ int xy_reweight_backward(int K, const double* d_betap, int L, const double* d_ou
   k_rw_backward<<<(K + 127) / 128, 128, 0, st>>>(K, d_betap, L, d_out, d_cov, d_gU, d_grhoL, d_grad_betap, d_dobs);
   const cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? XY_OK : XY_ERR_CUDA;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the reweighting forward pass.
+//
+// Some callers cannot hand the library a scratch buffer: code that runs with a
+// fixed device-memory budget decided up front, code that must not call the
+// CUDA allocator (or a framework's caching allocator) between set-up and
+// shutdown, and plugins hosted by a framework that owns all device
+// allocations.  For them the forward pass can run out of one file-scope
+// device array of a fixed size that every GPU loading this library holds
+// until the process exits.
+//
+// The kernels are the same as xy_reweight_forward's; only the number of
+// sample chunks is capped so that the per-chunk partial sums fit the array.
+// Every scratch word the kernels read is written earlier in the same call,
+// so nothing needs clearing between calls.  All calls share the one array:
+// calls that overlap on the GPU (other streams, other host threads) race.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+constexpr size_t kStaticScratchBytes = size_t(8) << 20;  // 8 MiB per device
+static __device__ __align__(256) unsigned char g_rw_static_scratch[kStaticScratchBytes];
+
+// Device address of g_rw_static_scratch per device, looked up once with that
+// device current (in host code the array's name is only a host-side handle).
+std::mutex g_static_mu;
+void* g_static_addr[64] = {nullptr};
+
+int static_scratch_address(int device, void** out) {
+  if (device < 0 || device >= 64) return XY_ERR_ARG;
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[device]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_rw_static_scratch);
+    if (e != cudaSuccess || !p) {
+      snprintf(g_rw_err, sizeof g_rw_err, "cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+      return XY_ERR_CUDA;
+    }
+    g_static_addr[device] = p;
+  }
+  *out = g_static_addr[device];
+  return XY_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t xy_reweight_noalloc_capacity_bytes(void) { return kStaticScratchBytes; }
+
+int xy_reweight_forward_noalloc(int64_t T, const double* d_E, const float* d_m2, const float* d_m4,
+                                const float* d_c, const float* d_s2, double beta0, int K,
+                                const double* d_betap, int L, double* d_out, double* d_obs, double* d_cov,
+                                void* stream) {
+  if (T < 2 || K < 1 || L < 1 || !std::isfinite(beta0)) return XY_ERR_ARG;
+  if (!d_E || !d_m2 || !d_m4 || !d_c || !d_s2 || !d_betap || !d_out || !d_obs || !d_cov) return XY_ERR_ARG;
+  // Layout inside the array: stat partials, stats, then n_tchunks x K x kNSum sums.
+  const size_t off_stat_part = 0;
+  const size_t off_stats = (static_cast<size_t>(kStatBlocks) * 3 * 8 + 255) / 256 * 256;
+  const size_t off_sums = off_stats + 256;
+  const size_t per_chunk = static_cast<size_t>(K) * kNSum * 8;
+  if (off_sums + per_chunk > kStaticScratchBytes) return XY_ERR_NOMEM;  // K too large
+  Plan p = plan_for(T, K);
+  const int cap = static_cast<int>((kStaticScratchBytes - off_sums) / per_chunk);
+  if (p.n_tchunks > cap) {
+    p.n_tchunks = cap;
+    p.t_per_chunk = (T + cap - 1) / cap;
+  }
+  // The device of the outputs is the device to run on; the first call on a
+  // device looks the array's address up (do it before any stream capture).
+  cudaPointerAttributes pa{};
+  cudaError_t e = cudaPointerGetAttributes(&pa, d_out);
+  if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+    cudaGetLastError();
+    return XY_ERR_ARG;
+  }
+  e = cudaSetDevice(pa.device);
+  if (e != cudaSuccess) return XY_ERR_CUDA;
+  void* base = nullptr;
+  const int rc = static_scratch_address(pa.device, &base);
+  if (rc != XY_OK) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(base);
+  double* part = reinterpret_cast<double*>(ws + off_stat_part);
+  double* stats = reinterpret_cast<double*>(ws + off_stats);
+  double* sums = reinterpret_cast<double*>(ws + off_sums);
+  k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
+  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, stats);
+  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, d_E, d_m2, d_m4, d_c, d_s2, beta0,
+                                                                  K, d_betap, stats, sums);
+  k_rw_finish<<<(K + 127) / 128, 128, 0, st>>>(K, p.n_tchunks, beta0, d_betap, L, stats, sums, d_out, d_obs, d_cov);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_rw_err, sizeof g_rw_err, "%s", cudaGetErrorString(e));
+    return XY_ERR_CUDA;
+  }
+  return XY_OK;
 }
 
 }  // extern "C"

@@ -79,6 +79,8 @@ _SIGNATURES = {
     "xy_reweight_scratch_bytes": (_SZ, [_I64, _I]),
     "xy_reweight_forward": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     "xy_reweight_backward": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
+    "xy_reweight_noalloc_capacity_bytes": (_SZ, []),
+    "xy_reweight_forward_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P]),
 }
 
 
