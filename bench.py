@@ -217,8 +217,8 @@ def bench_pt(steps: int, warmup: int):
     upd = sweeps * 4 * R * L ** 3
     st = torch.cuda.current_stream()
     s = xy.Simulation(L, R, betas, SEED, series_capacity=4 * sweeps * (steps + warmup + 2))
-    s.autotune(1, 3)
     s.set_exec(xy.EXEC_PERSISTENT)
+    s.autotune(1, 3)
     for _ in range(warmup):
         s.sweep(1, 3, sweeps, measure_every=1, pt_swap_every=1)
         s.read_series()
@@ -254,6 +254,83 @@ def bench_pt(steps: int, warmup: int):
             "unit": UNIT, "tile": list(tiles), "ms_per_10_sweeps_persistent": ms_p}
 
 
+RAGGED_L = (16, 24, 32, 48, 64, 96, 128)
+
+
+def bench_ragged(steps: int, warmup: int):
+    """L in {16, 24, 32, 48, 64, 96, 128} x 16 replicas each (beta in
+    [0.452, 0.456]), 1 Metropolis + 3 over-relaxation passes, exchange every
+    sweep and lattice sums every 10 sweeps, all lattices in one persistent
+    cooperative launch per call (218 MB of angles: HBM-resident)."""
+    import torch
+    from paper_1211_0780_b300 import xy
+    R, sweeps = 16, 10
+    betas = np.concatenate([np.linspace(0.452, 0.456, R) for _ in RAGGED_L])
+    upd = sweeps * 4 * R * sum(L ** 3 for L in RAGGED_L)
+    st = torch.cuda.current_stream()
+    s = xy.Simulation(list(RAGGED_L), [R] * len(RAGGED_L), betas, SEED,
+                      series_capacity=(steps + warmup + 2) * sweeps)
+    s.set_exec(xy.EXEC_PERSISTENT)
+    tiles = s.autotune(1, 3)
+    out = {"workload": "L in {16,24,32,48,64,96,128} x 16 replicas, 1+3 passes, exchange every sweep, "
+                       "sums every 10 sweeps", "unit": UNIT, "tiles": [list(t) for t in tiles]}
+    for mode, name in ((xy.EXEC_PERSISTENT, "persistent"), (xy.EXEC_GRAPH, "graph")):
+        try:
+            s.set_exec(mode)
+            for _ in range(warmup):
+                s.sweep(1, 3, sweeps, measure_every=10, pt_swap_every=1)
+            s.read_series()
+            ms = time_kernel(lambda: s.sweep(1, 3, sweeps, measure_every=10, pt_swap_every=1), st, steps, warm=0)
+            s.read_series()
+            out[name] = upd / (ms * 1e6)
+        except Exception as exc:
+            out[name] = {"error": repr(exc)}
+    return out
+
+
+def bench_reweight(reps: int):
+    """Forward + backward reweighting of T = 10^6 samples to K = 4096 beta'
+    in [0.4530, 0.4555], one synthetic series per L in {32, 64, 128, 160}."""
+    import torch
+    from paper_1211_0780_b300 import xy
+    from paper_1211_0780_b300.inputs import synthetic_series
+    T, K = 10 ** 6, 4096
+    st = torch.cuda.current_stream()
+    bp = torch.linspace(0.4530, 0.4555, K, dtype=torch.float64, device="cuda")
+    total_ms, per_L = 0.0, {}
+    for L in (32, 64, 128, 160):
+        s = synthetic_series(L, T, 100 + L)
+        tens = dict(zip(("E", "m2", "m4", "c", "s2"), xy._series_tensors(s)))
+        scratch = torch.empty(xy.lib().xy_reweight_scratch_bytes(T, K), dtype=torch.uint8, device="cuda")
+        gU = torch.ones(K, dtype=torch.float64, device="cuda")
+
+        def one():
+            f = xy.reweight_forward(tens, 0.4542, bp, L, scratch=scratch)
+            xy.reweight_backward(bp, L, f, gU, gU)
+
+        ms = time_kernel(one, st, reps, warm=1)
+        per_L[str(L)] = ms
+        total_ms += ms
+    pairs = 4 * K * T
+    # 13 FP64 instructions per (beta', sample) pair: the weight step, w*e and
+    # the 11 accumulations (2 adds + 9 fused multiply-adds)
+    fp64_ops = 13.0 * pairs
+    return {"workload": "4 series (L=32,64,128,160) x T=1e6 samples x K=4096 beta', forward+backward, FP64",
+            "pairs_per_ns": pairs / (total_ms * 1e6), "ms_total": total_ms, "ms_per_L": per_L,
+            "fp64_instr_per_s": fp64_ops / (total_ms * 1e-3)}
+
+
+def measured_units():
+    from paper_1211_0780_b300 import xy
+    out = {}
+    for k in xy.PEAK_KINDS:
+        try:
+            out[k] = xy.peak_probe(k)
+        except Exception as exc:  # report, do not hide
+            out[k] = repr(exc)
+    return out
+
+
 def run_gpu(args):
     import torch
     from paper_1211_0780_b300 import xy
@@ -268,9 +345,9 @@ def run_gpu(args):
     st = torch.cuda.current_stream()
     sim = xy.Simulation(L_MAIN, 1, [BETA_MAIN], SEED + rank, series_capacity=args.steps + args.warmup + 4)
     if args.tile:
-        ty, tz = (int(v) for v in args.tile.split(","))
-        sim.set_tile(0, ty, tz)
-        tile = (ty, tz)
+        parts = [int(v) for v in args.tile.split(",")]
+        sim.set_tile(0, *parts)
+        tile = sim.get_tile(0)
     else:
         tile = sim.autotune(NM_MAIN, NOR_MAIN)[0]
     sim.set_exec(xy.EXEC_GRAPH)
@@ -306,11 +383,11 @@ def run_gpu(args):
 
     # --- per-kernel durations (CUDA events on the launching stream) ----------
     # Graph-captured runs of one pass type: 6 sweeps of 0 + 5 passes = 60
-    # over-relaxation half-sweeps; 30 sweeps of 1 + 0 = 60 Metropolis ones
+    # over-relaxation half-sweeps; 32 sweeps of 1 + 0 = 64 Metropolis ones
     # (plus one counter-advance kernel each).  Average per half-sweep,
     # including the kernel-to-kernel gaps of the graph.
     ms_or = time_kernel(lambda: sim.sweep(0, 5, 6), st, 5) / 60
-    ms_met = time_kernel(lambda: sim.sweep(1, 0, 30), st, 5) / 60
+    ms_met = time_kernel(lambda: sim.sweep(1, 0, 32), st, 5) / 64
     half = L_MAIN ** 3 // 2
     hbm, src = measured_peaks()
     ach = BYTES_PER_UPDATE * half / (ms_or * 1e-3) / 1e9
@@ -342,10 +419,21 @@ def run_gpu(args):
 
     extras = {}
     if not args.no_extras and rank == 0:
-        try:
-            extras["batched_pt"] = bench_pt(max(3, args.steps // 2), 2)
-        except Exception as exc:  # report, do not hide
-            extras["batched_pt"] = {"error": repr(exc)}
+        for key, fn in (("batched_pt", lambda: bench_pt(max(3, args.steps // 2), 2)),
+                        ("ragged", lambda: bench_ragged(max(3, args.steps // 4), 2)),
+                        ("reweight", lambda: bench_reweight(3)),
+                        ("units", measured_units)):
+            try:
+                extras[key] = fn()
+            except Exception as exc:  # report, do not hide
+                extras[key] = {"error": repr(exc)}
+        if isinstance(extras.get("reweight"), dict) and isinstance(extras.get("units"), dict):
+            peak = extras["units"].get("fp64_fma")
+            if isinstance(peak, float):
+                extras["reweight"]["roofline"] = {
+                    "bound": "alu", "unit": "FP64 instr/s", "achieved": extras["reweight"]["fp64_instr_per_s"],
+                    "peak": peak, "frac": extras["reweight"]["fp64_instr_per_s"] / peak,
+                    "peak_source": "xy_peak_probe FP64 FMA (measured here)"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, done = oracle_rate(args.cpu_seconds)
@@ -381,7 +469,7 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--tile", default="", help="ty,tz of the 160^3 tile (skips the autotuner)")
+    ap.add_argument("--tile", default="", help="ty,tz[,kind] of the 160^3 tile (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -199,25 +199,32 @@ int xy_get_accepts(xy_ctx *ctx, uint64_t *met, uint64_t *swap);
 int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
                    uint32_t *host_words);
 
-/* Evaluates the device's reflection-angle function 2 atan2(y, x) (the one
- * the over-relaxation kernel uses) at n points: d_out[i] = 2 atan2(d_y[i],
- * d_x[i]), device arrays owned by the caller, ordered on `stream`; for
- * accuracy tests.  (x, y) = (0, 0) is not a valid input. */
+/* Evaluates the device's reflection-angle function (the one the
+ * over-relaxation kernel uses) at n points: d_out[i] = 2 atan2(d_y[i],
+ * d_x[i]) taken into [0, 2 pi], device arrays owned by the caller, ordered
+ * on `stream`; for accuracy tests.  (x, y) = (0, 0) is not a valid input. */
 int xy_debug_two_atan2(int n, const float *d_x, const float *d_y, float *d_out,
                        void *stream);
 
-/* Tile shape of lattice `lattice`: the kernels cover ty rows x tz planes per
- * thread block (full rows in x).  xy_set_tile checks 1 <= ty, tz <= L,
- * (L/8) * ty <= the kernels' maximum block size (512 on sm_103a at their
- * register use) and that the tile count fits the partial-sum area
- * (ceil(L/ty) ceil(L/tz) <= L^2/4); angles do not depend on the tile shape
- * (lattice sums only through FP64 summation order). */
-int xy_set_tile(xy_ctx *ctx, int lattice, int ty, int tz);
-int xy_get_tile(xy_ctx *ctx, int lattice, int *ty, int *tz);
+/* Tile of lattice `lattice`.  kind 0 (march): a thread block of (L/8) x ty
+ * threads covers full rows in x and ty rows in y and marches over tz planes
+ * in z, evaluating each other-colour cos/sin about once.  kind 1 (block): a
+ * thread block of (L/8) x ty x tz threads covers ty rows x tz planes at
+ * once after one cooperative evaluation of the tile's other-colour rows and
+ * face halos.  xy_set_tile checks 1 <= ty, tz <= L, the block size against
+ * the kernels' limit (512 threads at their register use on sm_103a), tz <=
+ * 64 for kind 1, and that the tile count fits the partial-sum area
+ * (ceil(L/ty) ceil(L/tz) <= L^2/4).  Angles do not depend on the tile (the
+ * lattice sums only through FP64 summation order). */
+int xy_set_tile(xy_ctx *ctx, int lattice, int kind, int ty, int tz);
+int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
 
-/* Picks each lattice's tile shape by timing candidate shapes on the
- * device for `n_metropolis`/`n_overrelax` sweeps (the state is saved and
- * restored); the choice is cached in the context.  Returns the cost. */
+/* Picks each lattice's tile (kind and shape) by timing the candidates on
+ * the device for sweeps of `n_metropolis` + `n_overrelax` passes (the angles,
+ * counters and accept counts are saved and restored); the choice stays in
+ * the context.  In XY_EXEC_PERSISTENT mode only block tiles of at most 256
+ * threads are candidates: a persistent launch needs one tile kind for all
+ * lattices (xy_sweep returns XY_ERR_ARG otherwise). */
 int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
 
 /* Device-side status word of the last persistent launch (0 = fine). */
@@ -229,6 +236,16 @@ int xy_device_status(xy_ctx *ctx, int *status_out);
  * through the status word without hanging.  The context stays usable (the
  * timeout is reported, not made sticky).  No GPU fault is involved. */
 int xy_debug_barrier_timeout(xy_ctx *ctx, int budget_us, int *status_out);
+
+/* Throughput probe of one hardware unit, for roofline denominators:
+ * kind 0 = special-function unit sin+cos (2 ops per pair), 1 = ex2,
+ * 2 = FP32 FMA, 3 = FP64 FMA, 4 = 32x32->64 integer multiply (the Philox
+ * round's operation), 5 = L2 read bytes (a 32 MiB L2-resident buffer).
+ * Writes operations (or bytes) per second to *ops_per_s.  d_scratch: device
+ * memory owned by the caller, >= 64 MiB for kind 5 and >= 4 bytes
+ * otherwise.  Runs on the current device and `stream`; synchronises it. */
+int xy_peak_probe(int kind, void *d_scratch, size_t scratch_bytes,
+                  double *ops_per_s, void *stream);
 
 /* Human-readable text of a status code. */
 const char *xy_strerror(int status);

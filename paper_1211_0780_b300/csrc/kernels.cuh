@@ -33,11 +33,12 @@ __global__ void k_init(Lattice lat, uint64_t seed) {
   }
 }
 
-// One half-sweep of one lattice: grid (tiles per slot, R), block (L/8, ty).
-// MEAS: the variant that fuses the lattice sums (white passes of measured
-// sweeps and the measurement-only pass).
-template <int MODE, bool MEAS>
-__global__ void k_half(Lattice lat, int colour, PassParams pp) {
+// One half-sweep of one lattice: grid (tiles per slot, R); block (L/8, ty) for
+// the march kind, (L/8, ty, tz) for the block kind.  MEAS: the variant that
+// fuses the lattice sums (white passes of measured sweeps and the
+// measurement-only pass).
+template <int MODE, bool MEAS, int KIND>
+__global__ void __launch_bounds__(512) k_half(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   chain_wait_and_release();
   const int r = blockIdx.y;
@@ -47,12 +48,15 @@ __global__ void k_half(Lattice lat, int colour, PassParams pp) {
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
-  tile_pass<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
-  const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-  const int nth = blockDim.x * blockDim.y;
+  if (KIND == kTileBlock)
+    tile_block<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, threadIdx.z, true, pp, sm, acc, n_acc);
+  else
+    tile_pass<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nth = blockDim.x * blockDim.y * blockDim.z;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);
   if (MEAS) {
-    double* red = reinterpret_cast<double*>(sm + tile_plane_floats(lat.L, lat.ty));
+    double* red = reinterpret_cast<double*>(sm + tile_floats(KIND, lat.L, lat.ty, lat.tz));
     const long long part = lat.part0 + static_cast<long long>(r) * lat.nyt * lat.nzt + t;
     block_sums_to(pp.partials + part * kNumSums, acc, tid, nth, red);
   }

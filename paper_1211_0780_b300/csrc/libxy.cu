@@ -29,6 +29,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct LatHost {
   int L, R, slot0;
+  int kind;  // kTileMarch or kTileBlock
   int ty, tz;
   size_t angle_off;  // floats from the angle base
   int part0;         // first partial slot
@@ -36,6 +37,8 @@ struct LatHost {
   long long N() const { return static_cast<long long>(L) * L * L; }
   int nyt() const { return (L + ty - 1) / ty; }
   int nzt() const { return (L + tz - 1) / tz; }
+  int threads() const { return (L / 8) * ty * (kind == kTileBlock ? tz : 1); }
+  int smem() const { return tile_bytes(kind, L, ty, tz); }
 };
 
 // Partial capacity per slot: tiles of at least 4 sites x rows x planes.
@@ -121,7 +124,7 @@ struct xy_ctx {
   int sticky = XY_OK;
   std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
   struct Plan {
-    int G = 0, B = 0, smem = 0;
+    int G = 0, B = 0, smem = 0, kind = 0;
     bool graph_ok = true;
   } plan;
   bool plan_valid = false;
@@ -141,6 +144,7 @@ struct xy_ctx {
     d.tz = h.tz;
     d.nyt = h.nyt();
     d.nzt = h.nzt();
+    d.kind = h.kind;
     d.part0 = h.part0;
     return d;
   }
@@ -182,14 +186,16 @@ int fail_cuda(xy_ctx* c, cudaError_t e, const char* what) {
     XY_TRY((c), cudaSetDevice((c)->device));                 \
   } while (0)
 
-int default_ty(int L) {
-  const int tx = L / 8;
-  int best = 1;
-  for (int d = 1; d <= L; ++d)
-    if (L % d == 0 && tx * d <= 256) best = d;
-  return best;
+// Default tile: the block kind with up to 8 x 8 rows and at most 256 threads.
+void default_tile(LatHost& h) {
+  h.kind = kTileBlock;
+  h.ty = std::min(h.L, 8);
+  h.tz = std::min(h.L, 8);
+  while (h.threads() > 256 && (h.ty > 1 || h.tz > 1)) {
+    if (h.tz >= h.ty) h.tz = std::max(1, h.tz / 2);
+    else h.ty = std::max(1, h.ty / 2);
+  }
 }
-int default_tz(int L) { return std::min(16, L); }
 
 int sync_lats(xy_ctx* c) {
   std::vector<Lattice> d(c->n_lat);
@@ -225,21 +231,24 @@ cudaError_t launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+template <int MODE, int KIND>
+cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st, int colour,
+                             const PassParams& pp) {
+  const dim3 grid(h.nyt() * h.nzt(), h.R);
+  const dim3 block = KIND == kTileBlock ? dim3(h.L / 8, h.ty, h.tz) : dim3(h.L / 8, h.ty);
+  const int smem = h.smem();
+  constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
+  if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);
+  if (pp.measure && colour == 1) return launch_chained(k_half<M, true, KIND>, grid, block, smem, st, d, colour, pp);
+  return launch_chained(k_half<M, false, KIND>, grid, block, smem, st, d, colour, pp);
+}
+
 template <int MODE>
 int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams& pp) {
   const LatHost& h = c->lat[i];
   const Lattice d = c->dev_lat(i);
-  const dim3 grid(h.nyt() * h.nzt(), h.R);
-  const dim3 block(h.L / 8, h.ty);
-  const int smem = tile_smem_bytes(h.L, h.ty);
-  constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
-  cudaError_t e;
-  if (MODE == kMeasureOnly)
-    e = launch_chained(k_half<kMeasureOnly, true>, grid, block, smem, st, d, colour, pp);
-  else if (pp.measure && colour == 1)
-    e = launch_chained(k_half<M, true>, grid, block, smem, st, d, colour, pp);
-  else
-    e = launch_chained(k_half<M, false>, grid, block, smem, st, d, colour, pp);
+  const cudaError_t e = h.kind == kTileBlock ? launch_half_kind<MODE, kTileBlock>(h, d, st, colour, pp)
+                                             : launch_half_kind<MODE, kTileMarch>(h, d, st, colour, pp);
   XY_TRY(c, e);
   return XY_OK;
 }
@@ -425,8 +434,7 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
     h.L = L[i];
     h.R = n_replicas[i];
     h.slot0 = slot;
-    h.ty = default_ty(h.L);
-    h.tz = default_tz(h.L);
+    default_tile(h);
     h.angle_off = aoff;
     h.part_cap = part_cap_for(h.L);
     h.part0 = part;
@@ -457,10 +465,17 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
   if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaDeviceGetAttribute"));
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaStreamCreateWithFlags"));
-  const void* half_kernels[5] = {
-      reinterpret_cast<const void*>(k_half<kMetropolis, false>), reinterpret_cast<const void*>(k_half<kMetropolis, true>),
-      reinterpret_cast<const void*>(k_half<kOverrelax, false>), reinterpret_cast<const void*>(k_half<kOverrelax, true>),
-      reinterpret_cast<const void*>(k_half<kMeasureOnly, true>)};
+  const void* half_kernels[10] = {
+      reinterpret_cast<const void*>(k_half<kMetropolis, false, kTileMarch>),
+      reinterpret_cast<const void*>(k_half<kMetropolis, true, kTileMarch>),
+      reinterpret_cast<const void*>(k_half<kOverrelax, false, kTileMarch>),
+      reinterpret_cast<const void*>(k_half<kOverrelax, true, kTileMarch>),
+      reinterpret_cast<const void*>(k_half<kMeasureOnly, true, kTileMarch>),
+      reinterpret_cast<const void*>(k_half<kMetropolis, false, kTileBlock>),
+      reinterpret_cast<const void*>(k_half<kMetropolis, true, kTileBlock>),
+      reinterpret_cast<const void*>(k_half<kOverrelax, false, kTileBlock>),
+      reinterpret_cast<const void*>(k_half<kOverrelax, true, kTileBlock>),
+      reinterpret_cast<const void*>(k_half<kMeasureOnly, true, kTileBlock>)};
   for (const void* fn : half_kernels) {
     // Tiles need up to ~64 KB of shared memory on the largest lattices.
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -471,7 +486,10 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
     c->max_block = std::min(c->max_block, fa.maxThreadsPerBlock);
   }
   for (LatHost& h : c->lat)
-    while ((h.L / 8) * h.ty > c->max_block && h.ty > 1) h.ty = std::max(1, h.ty / 2);
+    while (h.threads() > c->max_block && (h.ty > 1 || h.tz > 1)) {
+      if (h.tz >= h.ty) h.tz = std::max(1, h.tz / 2);
+      else h.ty = std::max(1, h.ty / 2);
+    }
 
   // Ladder tables: identity permutation, each slot at its own beta.
   std::vector<int> perm(slot), bidx(slot);
@@ -812,22 +830,27 @@ int xy_debug_two_atan2(int n, const float* d_x, const float* d_y, float* d_out, 
   return XY_OK;
 }
 
-int xy_set_tile(xy_ctx* c, int lattice, int ty, int tz) {
+int xy_set_tile(xy_ctx* c, int lattice, int kind, int ty, int tz) {
   XY_ENTER(c);
   if (lattice < 0 || lattice >= c->n_lat) return XY_ERR_ARG;
-  LatHost& h = c->lat[lattice];
-  if (ty < 1 || tz < 1 || ty > h.L || tz > h.L || (h.L / 8) * ty > c->max_block) return XY_ERR_ARG;
-  if (((h.L + ty - 1) / ty) * ((h.L + tz - 1) / tz) > h.part_cap) return XY_ERR_ARG;
-  if (tile_smem_bytes(h.L, ty) > 200 * 1024) return XY_ERR_ARG;
+  if (kind != kTileMarch && kind != kTileBlock) return XY_ERR_ARG;
+  LatHost h = c->lat[lattice];
+  h.kind = kind;
   h.ty = ty;
   h.tz = tz;
+  if (ty < 1 || tz < 1 || ty > h.L || tz > h.L || h.threads() > c->max_block) return XY_ERR_ARG;
+  if (kind == kTileBlock && tz > 64) return XY_ERR_ARG;  // block z extent
+  if (h.nyt() * h.nzt() > h.part_cap) return XY_ERR_ARG;
+  if (h.smem() > 200 * 1024) return XY_ERR_ARG;
+  c->lat[lattice] = h;
   drop_graphs(c);
   return sync_lats(c);
 }
 
-int xy_get_tile(xy_ctx* c, int lattice, int* ty, int* tz) {
+int xy_get_tile(xy_ctx* c, int lattice, int* kind, int* ty, int* tz) {
   XY_ENTER(c);
-  if (lattice < 0 || lattice >= c->n_lat || !ty || !tz) return XY_ERR_ARG;
+  if (lattice < 0 || lattice >= c->n_lat || !kind || !ty || !tz) return XY_ERR_ARG;
+  *kind = c->lat[lattice].kind;
   *ty = c->lat[lattice].ty;
   *tz = c->lat[lattice].tz;
   return XY_OK;
@@ -853,18 +876,21 @@ namespace {
 int build_plan(xy_ctx* c) {
   if (c->plan_valid) return XY_OK;
   int B = 64, smem = 0;
+  const int kind = c->lat[0].kind;
   for (const LatHost& h : c->lat) {
-    B = std::max(B, (h.L / 8) * h.ty);
-    smem = std::max(smem, tile_smem_bytes(h.L, h.ty));
+    if (h.kind != kind) return XY_ERR_ARG;  // one tile kind per persistent launch
+    B = std::max(B, h.threads());
+    smem = std::max(smem, h.smem());
   }
   B = (B + 31) / 32 * 32;
+  const void* fn = kind == kTileBlock ? reinterpret_cast<const void*>(k_persistent<kTileBlock>)
+                                      : reinterpret_cast<const void*>(k_persistent<kTileMarch>);
   cudaFuncAttributes fa{};
-  XY_TRY(c, cudaFuncGetAttributes(&fa, reinterpret_cast<const void*>(k_persistent)));
+  XY_TRY(c, cudaFuncGetAttributes(&fa, fn));
   if (B > fa.maxThreadsPerBlock) return XY_ERR_ARG;  // a tile wider than one persistent block
-  XY_TRY(c, cudaFuncSetAttribute(reinterpret_cast<const void*>(k_persistent),
-                                 cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  XY_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
   int nb = 0;
-  XY_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_persistent, B, smem));
+  XY_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, B, smem));
   if (nb <= 0) return XY_ERR_ARG;
   struct Item {
     int4 w;
@@ -903,6 +929,7 @@ int build_plan(xy_ctx* c) {
   c->plan.G = G;
   c->plan.B = B;
   c->plan.smem = smem;
+  c->plan.kind = kind;
   c->plan_valid = true;
   return XY_OK;
 }
@@ -938,7 +965,8 @@ cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return cudaLaunchKernelEx(&cfg, k_persistent, a);
+  return c->plan.kind == kTileBlock ? cudaLaunchKernelEx(&cfg, k_persistent<kTileBlock>, a)
+                                    : cudaLaunchKernelEx(&cfg, k_persistent<kTileMarch>, a);
 }
 
 // Records the persistent block: barrier reset, the cooperative kernel, the
@@ -1060,47 +1088,49 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
   int rc = XY_OK;
   for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) {
     LatHost& h = c->lat[i];
-    const int tx = h.L / 8;
     float best = 1e30f;
-    int bty = h.ty, btz = h.tz;
-    for (int ty = 1; ty <= h.L && rc == XY_OK; ++ty) {
-      if (h.L % ty != 0 || tx * ty > c->max_block || tx * ty < 32) continue;
-      if (tile_smem_bytes(h.L, ty) > 200 * 1024) continue;
-      const int tzs[] = {2, 4, 8, 16, 32};
-      for (int tz : tzs) {
-        if (tz > h.L || h.L % tz != 0) continue;
-        if ((h.L / ty) * (h.L / tz) > h.part_cap) continue;
-        h.ty = ty;
-        h.tz = tz;
-        if ((rc = sync_lats(c)) != XY_OK) break;
-        // Time this lattice alone: other lattices keep their shapes but are
-        // timed too; the argmin over this lattice's shapes is unaffected.
-        for (int rep = 0; rep < 2 && rc == XY_OK; ++rep) {
-          for (int p = 0; p < nM + nOR && rc == XY_OK; ++p)
-            for (int col = 0; col < 2 && rc == XY_OK; ++col)
-              rc = p < nM ? launch_half<kMetropolis>(c, c->stream, i, col, c->pass_params(false, 0, 0))
-                          : launch_half<kOverrelax>(c, c->stream, i, col, c->pass_params(false, 0, 0));
-        }
-        if (rc != XY_OK) break;
-        XY_TRY(c, cudaEventRecord(e0, c->stream));
-        for (int rep = 0; rep < 3 && rc == XY_OK; ++rep)
-          for (int p = 0; p < nM + nOR && rc == XY_OK; ++p)
-            for (int col = 0; col < 2 && rc == XY_OK; ++col)
-              rc = p < nM ? launch_half<kMetropolis>(c, c->stream, i, col, c->pass_params(false, 0, 0))
-                          : launch_half<kOverrelax>(c, c->stream, i, col, c->pass_params(false, 0, 0));
-        XY_TRY(c, cudaEventRecord(e1, c->stream));
-        XY_TRY(c, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        XY_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          bty = ty;
-          btz = tz;
+    LatHost best_h = h;
+    const int zs[] = {1, 2, 4, 8, 16, 32};
+    const bool persistent = exec == XY_EXEC_PERSISTENT;
+    for (int kind = persistent ? kTileBlock : 0; kind < 2 && rc == XY_OK; ++kind) {
+      for (int ty = 1; ty <= h.L && rc == XY_OK; ++ty) {
+        if (h.L % ty != 0) continue;
+        for (int tz : zs) {
+          if (tz > h.L || h.L % tz != 0) continue;
+          LatHost cand = h;
+          cand.kind = kind;
+          cand.ty = ty;
+          cand.tz = tz;
+          if (kind == kTileMarch && tz < 2) continue;
+          if (cand.threads() > c->max_block || cand.threads() < 32) continue;
+          if (persistent && cand.threads() > kPersistentBlockThreads) continue;
+          if (cand.nyt() * cand.nzt() > h.part_cap || cand.smem() > 200 * 1024) continue;
+          h = cand;
+          if ((rc = sync_lats(c)) != XY_OK) break;
+          auto run = [&](int reps) {
+            int r2 = XY_OK;
+            for (int rep = 0; rep < reps && r2 == XY_OK; ++rep)
+              for (int p = 0; p < nM + nOR && r2 == XY_OK; ++p)
+                for (int col = 0; col < 2 && r2 == XY_OK; ++col)
+                  r2 = p < nM ? launch_half<kMetropolis>(c, c->stream, i, col, c->pass_params(false, 0, 0))
+                              : launch_half<kOverrelax>(c, c->stream, i, col, c->pass_params(false, 0, 0));
+            return r2;
+          };
+          if ((rc = run(1)) != XY_OK) break;
+          XY_TRY(c, cudaEventRecord(e0, c->stream));
+          if ((rc = run(3)) != XY_OK) break;
+          XY_TRY(c, cudaEventRecord(e1, c->stream));
+          XY_TRY(c, cudaEventSynchronize(e1));
+          float ms = 0.f;
+          XY_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            best_h = h;
+          }
         }
       }
     }
-    h.ty = bty;
-    h.tz = btz;
+    h = best_h;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

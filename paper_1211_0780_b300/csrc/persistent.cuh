@@ -81,7 +81,14 @@ __device__ __forceinline__ bool due_dev(uint64_t s, int every) {
   return every > 0 && (s + 1) % static_cast<uint64_t>(every) == 0;
 }
 
-__global__ void __launch_bounds__(512, 1) k_persistent(PersistentArgs a) {
+// Every lattice of a persistent launch uses tile kind KIND: the march kind
+// allows blocks of up to 512 threads; the block kind up to 256 threads with
+// at least three blocks resident per SM (its registers stay below 85).
+constexpr int kPersistentBlockThreads = 256;
+
+template <int KIND>
+__global__ void __launch_bounds__(KIND == kTileBlock ? kPersistentBlockThreads : 512, KIND == kTileBlock ? 3 : 1)
+    k_persistent(PersistentArgs a) {
   extern __shared__ __align__(16) float sm[];
   const unsigned long long G = gridDim.x;
   unsigned long long nbar = 0;
@@ -107,27 +114,44 @@ __global__ void __launch_bounds__(512, 1) k_persistent(PersistentArgs a) {
           const int4 w = a.items[it];
           const Lattice lat = a.lats[w.x];
           const int TX = lat.L >> 3;
-          const int tx = tid % TX, ty = tid / TX;
+          const int tx = tid % TX, rest = tid / TX;
           const int yt = w.z % lat.nyt, zt = w.z / lat.nyt;
           float acc[kNumSums];
 #pragma unroll
           for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
           uint32_t n_acc = 0u;
-          const bool inb = ty < lat.ty;
-          if (is_met) {
-            if (pp.measure)
-              tile_pass<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
-            else
-              tile_pass<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
-            block_count_to(pp.acc_met + lat.slot0 + w.y, n_acc, tid, B);
+          if (KIND == kTileBlock) {
+            const int ty = rest % lat.ty, tz = rest / lat.ty;
+            const bool inb = tz < lat.tz;
+            if (is_met) {
+              if (pp.measure)
+                tile_block<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
+              else
+                tile_block<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
+            } else {
+              if (pp.measure)
+                tile_block<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
+              else
+                tile_block<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
+            }
           } else {
-            if (pp.measure)
-              tile_pass<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
-            else
-              tile_pass<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
+            const int ty = rest;
+            const bool inb = ty < lat.ty;
+            if (is_met) {
+              if (pp.measure)
+                tile_pass<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
+              else
+                tile_pass<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
+            } else {
+              if (pp.measure)
+                tile_pass<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
+              else
+                tile_pass<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
+            }
           }
+          if (is_met) block_count_to(pp.acc_met + lat.slot0 + w.y, n_acc, tid, B);
           if (pp.measure) {
-            double* red = reinterpret_cast<double*>(sm + tile_plane_floats(lat.L, lat.ty));
+            double* red = reinterpret_cast<double*>(sm + tile_floats(lat.kind, lat.L, lat.ty, lat.tz));
             const long long part = lat.part0 + static_cast<long long>(w.y) * lat.nyt * lat.nzt + w.z;
             block_sums_to(pp.partials + part * kNumSums, acc, tid, B, red);
           }

@@ -42,6 +42,13 @@ constexpr int kReduceBytes = kNumSums * 32 * 8;   // per-warp FP64 partials
 
 enum Mode : int { kMetropolis = 0, kOverrelax = 1, kMeasureOnly = 2 };
 
+// Tile kinds.  kTileMarch: a block of (L/8) x ty threads marches over tz
+// planes (each other-colour site's cos/sin evaluated ~once, but the planes
+// are processed in sequence).  kTileBlock: a block of (L/8) x ty x tz threads
+// updates its whole tile at once after one cooperative evaluation of the
+// tile's other-colour rows and face halos (more evaluations, no sequence).
+enum TileKind : int { kTileMarch = 0, kTileBlock = 1 };
+
 // Device-resident counters (graph replays read them instead of baking
 // values into kernel arguments).
 enum Counter : int {
@@ -61,6 +68,7 @@ struct Lattice {
   int slot0;      // global index of local slot 0
   int ty, tz;     // tile: ty rows x tz planes, full rows in x
   int nyt, nzt;   // tiles per slot along y and z
+  int kind;       // kTileMarch or kTileBlock
   int part0;      // first tile partial of this lattice; slot r tile t at
                   // part0 + r*nyt*nzt + t, t = yt + nyt*zt
 };
@@ -81,6 +89,14 @@ __host__ __device__ inline int tile_plane_floats(int L, int ty) { return 3 * (ty
 __host__ __device__ inline int tile_smem_bytes(int L, int ty) {
   return tile_plane_floats(L, ty) * 4 + kReduceBytes;
 }
+// kTileBlock: (ty+2) x (tz+2) rows of L/2 (cos, sin) pairs.
+__host__ __device__ inline int block_tile_floats(int L, int ty, int tz) { return (ty + 2) * (tz + 2) * L; }
+__host__ __device__ inline int tile_floats(int kind, int L, int ty, int tz) {
+  return kind == kTileBlock ? block_tile_floats(L, ty, tz) : tile_plane_floats(L, ty);
+}
+__host__ __device__ inline int tile_bytes(int kind, int L, int ty, int tz) {
+  return tile_floats(kind, L, ty, tz) * 4 + kReduceBytes;
+}
 
 // Programmatic dependent launch: a kernel of the half-sweep chain waits for
 // its predecessor's results (griddepcontrol.wait returns once the previous
@@ -98,15 +114,21 @@ __device__ __forceinline__ void spin(float th, float& c, float& s) {
   s = -sn;
 }
 
-// 2 atan2(y, x) in [-2 pi, 2 pi] for (x, y) != (0, 0): octant reduction to
-// r = min(|x|,|y|) / max(|x|,|y|) in [0, 1], then 2 atan(r) = r P(r^2) with a
-// degree-7 polynomial in r^2 fitted to 2 atan(r) / r on [0, 1] (weighted
-// least squares iterated towards the minimax error; |error| of atan <=
-// 3.8e-8 in exact arithmetic, <= 1.5e-7 with FP32 Horner), then the octant
-// and quadrant reflections.  Tested against atan2f over the plane.
+// 2 atan2(y, x) taken into [0, 2 pi] (the doubled field angle the
+// reflection needs), for (x, y) != (0, 0).  Octant reduction: r = min(|x|,|y|)
+// / max(|x|,|y|) in [0, 1] and q = 2 atan(r) = r P(r^2), with a degree-7
+// polynomial in r^2 fitted to 2 atan(r) / r on [0, 1] (weighted least squares
+// iterated towards the minimax error; |error| of atan <= 3.8e-8 in exact
+// arithmetic, <= 1.5e-7 with FP32 Horner).  The three reflections of the
+// octant reduction (|y| > |x|: pi - q; x < 0: 2 pi - ...; y < 0: 2 pi - ...)
+// compose to base + (-1)^k q, where k counts the reflections applied and
+// base = pi if |y| > |x|, else 2 pi if x and y have opposite signs, else 0.
+// Tested against FP64 atan2.
 __device__ __forceinline__ float two_atan2(float y, float x) {
   const float ax = fabsf(x), ay = fabsf(y);
-  const float r = __fdividef(fminf(ax, ay), fmaxf(ax, ay));
+  float rc;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(fmaxf(ax, ay)));
+  const float r = fminf(ax, ay) * rc;
   const float s = r * r;
   float p = -8.109124919e-03f;
   p = fmaf(p, s, 4.372588046e-02f);
@@ -116,10 +138,24 @@ __device__ __forceinline__ float two_atan2(float y, float x) {
   p = fmaf(p, s, 3.989313098e-01f);
   p = fmaf(p, s, -6.665972154e-01f);
   p = fmaf(p, s, 1.999998671e+00f);
-  float q = p * r;                       // 2 atan(r), in [0, pi/2]
-  q = (ay > ax) ? (kPi - q) : q;         // first quadrant: 2 phi
-  q = (x < 0.f) ? (kTwoPi - q) : q;      // second quadrant: 2 (pi - phi')
-  return copysignf(q, y);                // lower half plane: -2 phi'
+  const bool swap = ay > ax;
+  const uint32_t xb = __float_as_uint(x), yb = __float_as_uint(y);
+  // sign of (-1)^k: one bit each for swap, x < 0, y < 0 (signed zeros count
+  // as their sign, which only moves the result between 0 and 2 pi)
+  const uint32_t flip = (xb ^ yb ^ (swap ? 0x80000000u : 0u)) & 0x80000000u;
+  const float sq = __uint_as_float(__float_as_uint(p * r) ^ flip);
+  const float base = swap ? kPi : (((xb ^ yb) & 0x80000000u) ? kTwoPi : 0.f);
+  return base + sq;
+}
+
+// The reflection of Eq. (2) as an angle: theta' = 2 phi - theta mod 2 pi,
+// phi = arg h, branch free.  h = 0 leaves theta (Sec. II reading: no field,
+// no reflection).  Result in [0, 2 pi).
+__device__ __forceinline__ float reflect(float hx, float hy, float th) {
+  float t = two_atan2(hy, hx) - th;      // in (-2 pi, 2 pi]
+  t = (t < 0.f) ? t + kTwoPi : t;
+  t = (t >= kTwoPi) ? t - kTwoPi : t;
+  return (hx == 0.f && hy == 0.f) ? th : t;
 }
 
 struct Spins4 {
@@ -334,13 +370,7 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
           nc[e] = accept ? cp : co;
           ns[e] = accept ? sp : so;
         } else if (MODE == kOverrelax) {
-          float t = th[e];
-          if (hx != 0.f || hy != 0.f) {
-            t = two_atan2(hy, hx) - th[e];  // reflection about the field
-            if (t < 0.f) t += kTwoPi;
-            if (t < 0.f) t += kTwoPi;
-            if (t >= kTwoPi) t -= kTwoPi;
-          }
+          const float t = reflect(hx, hy, th[e]);  // reflection about the field
           tn[e] = t;
           if (MEAS) spin(t, nc[e], ns[e]);
         } else {
@@ -378,6 +408,160 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
     step(IC<2>{}, pc, pa, pb, i + 2);
   }
   if (MEAS) sums.export_to(acc_out);
+}
+
+// One tile of one half-sweep, kTileBlock: thread (tx, ty, tz) owns the float4
+// at row y0+ty of plane z0+tz.  Prologue: every thread evaluates the
+// other-colour cos/sin of its own row; threads on the tile's faces also
+// evaluate the face-halo rows (y0-1, y0+TYa at each plane; z0-1, z0+TZa at
+// each row).  One barrier, then each thread reads its six neighbours from
+// shared memory.  The per-site arithmetic (field in the same association
+// order, Metropolis, reflection, lattice sums) is the march kind's, so both
+// kinds give bit-identical angles.
+template <int MODE, bool MEAS>
+__device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, int zt, int colour,
+                                           int tx, int ty, int tz, bool in_block, const PassParams& pp,
+                                           float* sm, float* acc_out, uint32_t& n_acc) {
+  static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
+  const int L = lat.L;
+  const int H = L >> 1;
+  const uint32_t PS = static_cast<uint32_t>(H) * static_cast<uint32_t>(L);
+  const uint32_t half = PS * static_cast<uint32_t>(L);
+  const int y0 = yt * lat.ty, z0 = zt * lat.tz;
+  const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
+  const bool act = in_block && ty < TYa && tz < TZa;
+  const int y = y0 + ty, z = z0 + tz;
+  float* const slot = lat.angles + static_cast<size_t>(r) * (2 * static_cast<size_t>(half));
+  float* const own = slot + colour * half;
+  const float* const oth = slot + (colour ^ 1) * half;
+  const int stride_z = lat.ty + 2;  // rows per plane in shared memory
+  auto row_ptr = [&](int dy, int dz) -> float* { return sm + (dz * stride_z + dy) * 2 * H; };
+  const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
+  const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
+  const int kh0 = (tx == 0) ? H - 1 : 4 * tx - 1;
+  const int kh1 = (4 * tx + 4 == H) ? 0 : 4 * tx + 4;
+
+  float beta = 0.f;
+  uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
+  if (MODE == kMetropolis) {
+    beta = __ldcg(pp.beta_slot + lat.slot0 + r);
+    tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) |
+           kTagMet;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    mlo = static_cast<uint32_t>(mp);
+    mhi = static_cast<uint32_t>(mp >> 32);
+  }
+
+  float4 t_own = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (act) {
+    t_own = ld4(own + offz);
+    const bool zlo = tz == 0, zhi = tz == TZa - 1, ylo = ty == 0, yhi = ty == TYa - 1;
+    const uint32_t pzm = static_cast<uint32_t>(z == 0 ? L - 1 : z - 1) * PS;
+    const uint32_t pzp = static_cast<uint32_t>(z + 1 == L ? 0 : z + 1) * PS;
+    const uint32_t oym = static_cast<uint32_t>(H * (y == 0 ? L - 1 : y - 1) + 4 * tx);
+    const uint32_t oyp = static_cast<uint32_t>(H * (y + 1 == L ? 0 : y + 1) + 4 * tx);
+    const float4 a0 = ld4(oth + offz);
+    float4 a1 = a0, a2 = a0, a3 = a0, a4 = a0;
+    if (zlo) a1 = ld4(oth + offy + pzm);
+    if (zhi) a2 = ld4(oth + offy + pzp);
+    if (ylo) a3 = ld4(oth + oym + static_cast<uint32_t>(z) * PS);
+    if (yhi) a4 = ld4(oth + oyp + static_cast<uint32_t>(z) * PS);
+    put_row(row_ptr(ty + 1, tz + 1), H, tx, spins4(a0));
+    if (zlo) put_row(row_ptr(ty + 1, 0), H, tx, spins4(a1));
+    if (zhi) put_row(row_ptr(ty + 1, TZa + 1), H, tx, spins4(a2));
+    if (ylo) put_row(row_ptr(0, tz + 1), H, tx, spins4(a3));
+    if (yhi) put_row(row_ptr(TYa + 1, tz + 1), H, tx, spins4(a4));
+  }
+  __syncthreads();
+  if (act) {
+    const float* r0 = row_ptr(ty + 1, tz + 1);
+    const float* rm = row_ptr(ty, tz + 1);
+    const float* rp = row_ptr(ty + 2, tz + 1);
+    const float* rzm = row_ptr(ty + 1, tz);
+    const float* rzp = row_ptr(ty + 1, tz + 2);
+    const float4 zcc = reinterpret_cast<const float4*>(r0)[tx];
+    const float4 zcs = reinterpret_cast<const float4*>(r0 + H)[tx];
+    const float4 ymc = reinterpret_cast<const float4*>(rm)[tx];
+    const float4 yms = reinterpret_cast<const float4*>(rm + H)[tx];
+    const float4 ypc = reinterpret_cast<const float4*>(rp)[tx];
+    const float4 yps = reinterpret_cast<const float4*>(rp + H)[tx];
+    const float4 zmc = reinterpret_cast<const float4*>(rzm)[tx];
+    const float4 zms = reinterpret_cast<const float4*>(rzm + H)[tx];
+    const float4 zpc = reinterpret_cast<const float4*>(rzp)[tx];
+    const float4 zps = reinterpret_cast<const float4*>(rzp + H)[tx];
+    const int s = (y + z + colour) & 1;
+    const int kh = s ? kh1 : kh0;
+    const float hc = r0[kh], hs = r0[H + kh];
+    float Xc[5], Xs[5];
+#pragma unroll
+    for (int e = 0; e < 5; ++e) {
+      const float a_c = (e < 4) ? comp(zcc, e < 4 ? e : 0) : hc;
+      const float a_s = (e < 4) ? comp(zcs, e < 4 ? e : 0) : hs;
+      const float b_c = (e == 0) ? hc : comp(zcc, e == 0 ? 0 : e - 1);
+      const float b_s = (e == 0) ? hs : comp(zcs, e == 0 ? 0 : e - 1);
+      Xc[e] = s ? a_c : b_c;
+      Xs[e] = s ? a_s : b_s;
+    }
+    const float th[4] = {t_own.x, t_own.y, t_own.z, t_own.w};
+    float tn[4], nc[4], ns[4];
+    uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+    if (MODE == kMetropolis) {
+      const uint32_t q0 = offz >> 1;
+      w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+      w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+    }
+    float stepv[kNumSums];
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const float hx = (Xc[e] + Xc[e + 1]) + (comp(ymc, e) + comp(ypc, e)) + (comp(zmc, e) + comp(zpc, e));
+      const float hy = (Xs[e] + Xs[e + 1]) + (comp(yms, e) + comp(yps, e)) + (comp(zms, e) + comp(zps, e));
+      if (MODE == kMetropolis) {
+        const uint4& w = (e < 2) ? w0 : w1;
+        const uint32_t wprop = (e & 1) ? w.z : w.x;
+        const uint32_t wacc = (e & 1) ? w.w : w.y;
+        const float tp = static_cast<float>(wprop >> 8) * kTwoPiOver2p24;
+        float cp, sp, co, so;
+        spin(tp, cp, sp);
+        spin(th[e], co, so);
+        const float x = beta * (hx * (cp - co) + hy * (sp - so));
+        const bool accept = static_cast<float>(wacc >> 8) < __expf(x) * 16777216.0f;
+        n_acc += accept ? 1u : 0u;
+        tn[e] = accept ? tp : th[e];
+        nc[e] = accept ? cp : co;
+        ns[e] = accept ? sp : so;
+      } else if (MODE == kOverrelax) {
+        const float t = reflect(hx, hy, th[e]);
+        tn[e] = t;
+        if (MEAS) spin(t, nc[e], ns[e]);
+      } else {
+        tn[e] = th[e];
+        spin(th[e], nc[e], ns[e]);
+      }
+      if (MEAS) {
+        const float c = nc[e], sn = ns[e];
+        const float pxc = Xc[e + 1], qxc = Xc[e], pxs = Xs[e + 1], qxs = Xs[e];
+        const float pyc = comp(ypc, e), qyc = comp(ymc, e), pys = comp(yps, e), qys = comp(yms, e);
+        const float pzc = comp(zpc, e), qzc = comp(zmc, e), pzs = comp(zps, e), qzs = comp(zms, e);
+        stepv[0] += c + comp(zcc, e);
+        stepv[1] += sn + comp(zcs, e);
+        stepv[2] += c * (pxc + qxc) + sn * (pxs + qxs);
+        stepv[3] += c * (pyc + qyc) + sn * (pys + qys);
+        stepv[4] += c * (pzc + qzc) + sn * (pzs + qzs);
+        stepv[5] += sn * (pxc - qxc) - c * (pxs - qxs);
+        stepv[6] += sn * (pyc - qyc) - c * (pys - qys);
+        stepv[7] += sn * (pzc - qzc) - c * (pzs - qzs);
+      }
+    }
+    if (MEAS) {
+#pragma unroll
+      for (int j = 0; j < kNumSums; ++j) acc_out[j] = stepv[j];
+    }
+    if (MODE != kMeasureOnly) st4(own + offz, make_float4(tn[0], tn[1], tn[2], tn[3]));
+  }
+  // The shared rows may be overwritten by the caller's next tile.
+  __syncthreads();
 }
 
 // Fixed-order block reduction of the FP32 partials into FP64 (a deterministic

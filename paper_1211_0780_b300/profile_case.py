@@ -1,6 +1,6 @@
 """A small, fixed launch sequence of one half-sweep kernel, for profilers.
 
-python -m paper_1211_0780_b300.profile_case --L 160 --ty 10 --tz 16 --mode or --launches 5
+python -m paper_1211_0780_b300.profile_case --L 160 --ty 8 --tz 2 --kind 1 --mode or --launches 5
 
 Creates one lattice (seeded hot start), runs a few warm-up sweeps, then
 issues `--launches` half-sweeps of the chosen kernel (or = over-relaxation,
@@ -19,6 +19,7 @@ def main():
     ap.add_argument("--R", type=int, default=1)
     ap.add_argument("--ty", type=int, default=0)
     ap.add_argument("--tz", type=int, default=0)
+    ap.add_argument("--kind", type=int, default=1, help="0 = march tile, 1 = block tile")
     ap.add_argument("--mode", default="or", choices=["or", "met", "meas", "sweep"])
     ap.add_argument("--launches", type=int, default=5)
     ap.add_argument("--warm-sweeps", type=int, default=2)
@@ -28,7 +29,7 @@ def main():
     betas = np.linspace(0.4542, 0.4560, args.R) if args.R > 1 else [0.4542]
     sim = xy.Simulation(args.L, args.R, betas, 0x5EED2012)
     if args.ty and args.tz:
-        sim.set_tile(0, args.ty, args.tz)
+        sim.set_tile(0, args.ty, args.tz, args.kind)
     sim.sweep(1, 1, args.warm_sweeps)
     for i in range(args.launches):
         if args.mode == "or":

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libxy.so")
 XY_OK, XY_ERR_ARG, XY_ERR_CUDA, XY_ERR_TIMEOUT, XY_ERR_STATE, XY_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 EXEC_PLAIN, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2
 TAG_INIT, TAG_MET, TAG_PT = 1, 2, 3
+TILE_MARCH, TILE_BLOCK = 0, 1
 
 
 class XYError(RuntimeError):
@@ -71,8 +72,8 @@ _SIGNATURES = {
     "xy_set_packed": (_I, [_P, _P]),
     "xy_debug_draws": (_I, [_P, _I, _I, _I, _U64, _P]),
     "xy_debug_two_atan2": (_I, [_I, _P, _P, _P, _P]),
-    "xy_set_tile": (_I, [_P, _I, _I, _I]),
-    "xy_get_tile": (_I, [_P, _I, _P, _P]),
+    "xy_set_tile": (_I, [_P, _I, _I, _I, _I]),
+    "xy_get_tile": (_I, [_P, _I, _P, _P, _P]),
     "xy_autotune": (_I, [_P, _I, _I]),
     "xy_device_status": (_I, [_P, _P]),
     "xy_debug_barrier_timeout": (_I, [_P, _I, _P]),
@@ -80,6 +81,7 @@ _SIGNATURES = {
     "xy_reweight_forward": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     "xy_reweight_backward": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
     "xy_reweight_noalloc_capacity_bytes": (_SZ, []),
+    "xy_peak_probe": (_I, [_I, _P, _SZ, _P, _P]),
     "xy_reweight_forward_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P]),
 }
 
@@ -269,13 +271,15 @@ class Simulation:
         return out.reshape(-1, 2)
 
     # -- tuning and diagnostics ----------------------------------------
-    def set_tile(self, lattice: int, ty: int, tz: int) -> None:
-        _check(lib().xy_set_tile(self._ctx, int(lattice), int(ty), int(tz)), "xy_set_tile")
+    def set_tile(self, lattice: int, ty: int, tz: int, kind: int = TILE_BLOCK) -> None:
+        _check(lib().xy_set_tile(self._ctx, int(lattice), int(kind), int(ty), int(tz)), "xy_set_tile")
 
     def get_tile(self, lattice: int):
-        ty, tz = ctypes.c_int(0), ctypes.c_int(0)
-        _check(lib().xy_get_tile(self._ctx, int(lattice), ctypes.byref(ty), ctypes.byref(tz)), "xy_get_tile")
-        return int(ty.value), int(tz.value)
+        """(ty, tz, kind) of one lattice's tile."""
+        k, ty, tz = ctypes.c_int(0), ctypes.c_int(0), ctypes.c_int(0)
+        _check(lib().xy_get_tile(self._ctx, int(lattice), ctypes.byref(k), ctypes.byref(ty), ctypes.byref(tz)),
+               "xy_get_tile")
+        return int(ty.value), int(tz.value), int(k.value)
 
     def autotune(self, n_metropolis: int, n_overrelax: int):
         _check(lib().xy_autotune(self._ctx, int(n_metropolis), int(n_overrelax)), "xy_autotune")
@@ -291,6 +295,20 @@ class Simulation:
         s = ctypes.c_int(0)
         rc = lib().xy_debug_barrier_timeout(self._ctx, int(budget_us), ctypes.byref(s))
         return int(rc), int(s.value)
+
+
+PEAK_KINDS = {"sfu_sincos": 0, "sfu_ex2": 1, "fp32_fma": 2, "fp64_fma": 3, "int_mul_wide": 4,
+              "l2_read_bytes": 5}
+
+
+def peak_probe(kind: str) -> float:
+    """Measured operations (or bytes) per second of one unit (see xy_peak_probe)."""
+    torch = _require_cuda()
+    buf = torch.empty(64 << 20, dtype=torch.uint8, device="cuda")
+    out = ctypes.c_double(0.0)
+    _check(lib().xy_peak_probe(PEAK_KINDS[kind], buf.data_ptr(), buf.numel(), ctypes.byref(out),
+                               torch.cuda.current_stream().cuda_stream), "xy_peak_probe")
+    return float(out.value)
 
 
 def debug_two_atan2(x, y) -> np.ndarray:

