@@ -206,52 +206,45 @@ def time_kernel(fn, stream, n, warm=5):
 
 
 def bench_pt(steps: int, warmup: int):
-    """64^3 x 32 replicas, beta in [0.450, 0.458], 1 + 3 passes, exchange
-    every sweep: persistent cooperative launch vs the plain per-replica
-    launch loop (one context per replica, kernels issued replica by
-    replica)."""
+    """64^3 x 32 replicas, beta in [0.450, 0.458], 1 + 3 passes, exchange and
+    lattice sums every sweep, three ways: every replica batched into each
+    half-sweep kernel (CUDA graph), the persistent cooperative launch (one
+    launch per call, graph-captured), and the plain per-replica launch loop
+    (one context per replica, kernels issued replica by replica)."""
     import torch
     from paper_1211_0780_b300 import xy
     L, R, sweeps = 64, 32, 10
     betas = np.linspace(0.450, 0.458, R)
     upd = sweeps * 4 * R * L ** 3
     st = torch.cuda.current_stream()
-    s = xy.Simulation(L, R, betas, SEED, series_capacity=4 * sweeps * (steps + warmup + 2))
-    s.set_exec(xy.EXEC_PERSISTENT)
-    s.autotune(1, 3)
-    for _ in range(warmup):
-        s.sweep(1, 3, sweeps, measure_every=1, pt_swap_every=1)
+    out = {"workload": "64^3 x 32 replicas, beta=linspace(0.450,0.458,32), 1+3 passes, exchange+measure every sweep",
+           "unit": UNIT}
+    for mode, name in ((xy.EXEC_GRAPH, "batched_graph"), (xy.EXEC_PERSISTENT, "batched_persistent")):
+        s = xy.Simulation(L, R, betas, SEED, series_capacity=sweeps * (steps + warmup + 4))
+        s.set_exec(mode)
+        tile = s.autotune(1, 3)[0]
+        step = lambda: s.sweep(1, 3, sweeps, measure_every=1, pt_swap_every=1)
+        for _ in range(warmup):
+            step()
         s.read_series()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(st)
-    for _ in range(steps):
-        s.sweep(1, 3, sweeps, measure_every=1, pt_swap_every=1)
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_p = e0.elapsed_time(e1) / steps
-    s.read_series()
-    tiles = s.get_tile(0)
-    # plain loop: one context per replica, kernel-by-kernel launches
+        ms = time_kernel(step, st, steps, warm=0)
+        s.read_series()
+        out[name] = upd / (ms * 1e6)
+        out[name + "_tile"] = list(tile)
     reps = [xy.Simulation(L, 1, [b], SEED + i) for i, b in enumerate(betas)]
     for r in reps:
-        r.set_tile(0, *tiles)
+        r.set_tile(0, *out["batched_graph_tile"])
+
     def one_step():
         for _ in range(sweeps):
             for r in reps:
                 r.sweep(1, 3, 1)
+
     for _ in range(warmup):
         one_step()
-    torch.cuda.synchronize()
-    e0.record(st)
-    for _ in range(max(1, steps // 2)):
-        one_step()
-    e1.record(st)
-    torch.cuda.synchronize()
-    ms_l = e0.elapsed_time(e1) / max(1, steps // 2)
-    return {"workload": "64^3 x 32 replicas, beta=linspace(0.450,0.458,32), 1+3 passes, exchange+measure every sweep",
-            "batched_persistent": upd / (ms_p * 1e6), "plain_per_replica_loop": upd / (ms_l * 1e6),
-            "unit": UNIT, "tile": list(tiles), "ms_per_10_sweeps_persistent": ms_p}
+    ms_l = time_kernel(one_step, st, max(1, steps // 2), warm=0)
+    out["plain_per_replica_loop"] = upd / (ms_l * 1e6)
+    return out
 
 
 RAGGED_L = (16, 24, 32, 48, 64, 96, 128)

@@ -51,6 +51,7 @@ struct Layout {
 };
 
 constexpr int kMaxPlanBlocks = 8192;
+constexpr size_t kBarBytes = (kBarGroups + 1) * kBarStride * 8;
 
 bool valid_lattices(int n, const int* L, const int* R) {
   if (n <= 0 || n > 4096 || !L || !R) return false;
@@ -90,7 +91,7 @@ Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
   o.acc_swap = take(slots * 8);
   o.ctr = take(kNumCounters * 8);
   o.status = take(64);
-  o.barrier = take(64);
+  o.barrier = take((kBarGroups + 1) * kBarStride * 8);
   o.nswapped = take(64);
   o.lats = take(static_cast<size_t>(n) * sizeof(Lattice));
   o.staging = take(static_cast<size_t>(maxN) * 4);
@@ -113,6 +114,11 @@ struct xy_ctx {
   uint64_t seed = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  // One stream per lattice: the lattices' half-sweep chains run as
+  // concurrent branches between the points where they must meet.
+  std::vector<cudaStream_t> lat_streams;
+  cudaEvent_t fork_ev = nullptr;
+  std::vector<cudaEvent_t> join_ev;
   int device = 0;
   int num_sms = 0;
   int max_block = 1024;  // threads per block the half-sweep kernels can launch with
@@ -304,20 +310,37 @@ int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, in
     const bool meas = due(s, me), swp = due(s, se);
     const bool needE = meas || swp;
     const int n_pass = nM + nOR;
-    for (int p = 0; p < n_pass; ++p) {
-      const bool last = (p == n_pass - 1);
-      for (int colour = 0; colour < 2; ++colour) {
-        const int measure = (needE && last && colour == 1) ? 1 : 0;
-        int rc;
-        if (p < nM) {
-          rc = launch_half_all<kMetropolis>(c, st, colour, c->pass_params(true, bc.mpass, measure));
-        } else {
-          rc = launch_half_all<kOverrelax>(c, st, colour, c->pass_params(true, 0, measure));
-        }
-        if (rc != XY_OK) return rc;
-      }
-      if (p < nM) bc.mpass += 1;
+    const bool branches = c->n_lat > 1;
+    if (branches) {
+      XY_TRY(c, cudaEventRecord(c->fork_ev, st));
+      for (int i = 0; i < c->n_lat; ++i) XY_TRY(c, cudaStreamWaitEvent(c->lat_streams[i], c->fork_ev, 0));
     }
+    for (int i = 0; i < (branches ? c->n_lat : 1); ++i) {
+      uint64_t mp = bc.mpass;
+      for (int p = 0; p < n_pass; ++p) {
+        const bool last = (p == n_pass - 1);
+        for (int colour = 0; colour < 2; ++colour) {
+          const int measure = (needE && last && colour == 1) ? 1 : 0;
+          const PassParams pp = c->pass_params(true, p < nM ? mp : 0, measure);
+          int rc;
+          if (branches)
+            rc = p < nM ? launch_half<kMetropolis>(c, c->lat_streams[i], i, colour, pp)
+                        : launch_half<kOverrelax>(c, c->lat_streams[i], i, colour, pp);
+          else
+            rc = p < nM ? launch_half_all<kMetropolis>(c, st, colour, pp)
+                        : launch_half_all<kOverrelax>(c, st, colour, pp);
+          if (rc != XY_OK) return rc;
+        }
+        if (p < nM) mp += 1;
+      }
+    }
+    if (branches) {
+      for (int i = 0; i < c->n_lat; ++i) {
+        XY_TRY(c, cudaEventRecord(c->join_ev[i], c->lat_streams[i]));
+        XY_TRY(c, cudaStreamWaitEvent(st, c->join_ev[i], 0));
+      }
+    }
+    bc.mpass += nM;
     if (needE) {
       FinishParams f = finish_params(c);
       f.sweep_off = bc.sweeps;
@@ -465,6 +488,17 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
   if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaDeviceGetAttribute"));
   e = cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking);
   if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaStreamCreateWithFlags"));
+  if (n_lattices > 1) {
+    e = cudaEventCreateWithFlags(&c->fork_ev, cudaEventDisableTiming);
+    if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaEventCreateWithFlags"));
+    c->lat_streams.assign(n_lattices, nullptr);
+    c->join_ev.assign(n_lattices, nullptr);
+    for (int i = 0; i < n_lattices; ++i) {
+      e = cudaStreamCreateWithFlags(&c->lat_streams[i], cudaStreamNonBlocking);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&c->join_ev[i], cudaEventDisableTiming);
+      if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "lattice streams"));
+    }
+  }
   const void* half_kernels[10] = {
       reinterpret_cast<const void*>(k_half<kMetropolis, false, kTileMarch>),
       reinterpret_cast<const void*>(k_half<kMetropolis, true, kTileMarch>),
@@ -533,6 +567,11 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
 int xy_destroy(xy_ctx* c) {
   if (!c) return XY_OK;
   drop_graphs(c);
+  for (cudaStream_t s : c->lat_streams)
+    if (s) cudaStreamDestroy(s);
+  for (cudaEvent_t ev : c->join_ev)
+    if (ev) cudaEventDestroy(ev);
+  if (c->fork_ev) cudaEventDestroy(c->fork_ev);
   if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
   delete c;
   return XY_OK;
@@ -972,7 +1011,7 @@ cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& 
 // Records the persistent block: barrier reset, the cooperative kernel, the
 // counter advance.
 int issue_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, const BlockCounts& bc) {
-  XY_TRY(c, cudaMemsetAsync(a.bar, 0, 8, st));
+  XY_TRY(c, cudaMemsetAsync(a.bar, 0, kBarBytes, st));
   XY_TRY(c, launch_persistent(c, st, a));
   k_advance<<<1, 1, 0, st>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
   XY_CHECK_LAUNCH(c);
@@ -1011,7 +1050,7 @@ int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return fail_cuda(c, e, "cudaStreamBeginCapture");
-      cudaError_t e1 = cudaMemsetAsync(a.bar, 0, 8, c->cap_stream);
+      cudaError_t e1 = cudaMemsetAsync(a.bar, 0, kBarBytes, c->cap_stream);
       cudaError_t e2 = e1 == cudaSuccess ? launch_persistent(c, c->cap_stream, a) : e1;
       if (e2 == cudaSuccess) {
         k_advance<<<1, 1, 0, c->cap_stream>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
@@ -1056,7 +1095,7 @@ int xy_debug_barrier_timeout(xy_ctx* c, int budget_us, int* status_out) {
   PersistentArgs a = persistent_args(c, 0, 0, 0, 0, 0);
   a.poison = 1;
   a.budget_ns = static_cast<long long>(budget_us) * 1000;
-  XY_TRY(c, cudaMemsetAsync(a.bar, 0, 8, c->stream));
+  XY_TRY(c, cudaMemsetAsync(a.bar, 0, kBarBytes, c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));
   XY_TRY(c, launch_persistent(c, c->stream, a));
   int st = 0;

@@ -5,13 +5,17 @@
 // scheduler spreads over the blocks by longest-processing-time-first; a
 // bounded grid barrier separates half-sweeps.
 //
-// The barrier is a monotonically increasing arrival counter: barrier number
-// b completes when the counter reaches (b + 1) * gridDim.x.  Thread 0 of each
-// block arrives with a release fence and polls with acquire loads.  Every
-// wait is bounded by a %globaltimer budget; when it runs out the block sets
-// the status word to XY_ERR_TIMEOUT and every block leaves at its next
-// barrier, so a missing block ends the launch with an error, never a hang.
-// Co-residency of all blocks is guaranteed by the cooperative launch.
+// The barrier is two levels of monotonically increasing arrival counters:
+// block b arrives on group counter b mod kBarGroups (each on its own 128-byte
+// line, so arrivals are spread over L2 slices instead of serialising on one
+// address); the block that completes its group's count for this barrier
+// instance adds one to the top counter, which every block polls with
+// acquire loads.  Barrier instance k completes when the top counter reaches
+// (k + 1) * (number of non-empty groups).  Every wait is bounded by a
+// %globaltimer budget; when it runs out the block sets the status word to
+// XY_ERR_TIMEOUT and every block leaves at its next barrier, so a missing
+// block ends the launch with an error, never a hang.  Co-residency of all
+// blocks is guaranteed by the cooperative launch.
 #pragma once
 #include <cstdint>
 
@@ -19,6 +23,9 @@
 #include "sweep.cuh"
 
 namespace xy {
+
+constexpr int kBarGroups = 16;
+constexpr int kBarStride = 16;  // 64-bit words between counters (128 bytes)
 
 struct PersistentArgs {
   PassParams pp;            // mpass_off and measure are set per pass
@@ -28,7 +35,8 @@ struct PersistentArgs {
   const int* offs;          // items of block b: offs[b] .. offs[b+1]-1
   int n_lat;
   int nM, nOR, n_sweeps, me, se;
-  unsigned long long* bar;  // arrival counter, zero at launch
+  unsigned long long* bar;  // kBarGroups group counters then the top counter,
+                            // kBarStride words apart, zero at launch
   int* status;              // 0, or XY_ERR_TIMEOUT
   long long budget_ns;      // bound of one barrier wait
   int poison;               // test hook: the first barrier expects one block too many
@@ -50,16 +58,30 @@ __device__ __forceinline__ void red_release_add(unsigned long long* p, unsigned 
   asm volatile("red.release.gpu.global.add.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Returns false if the launch has failed (this or another block timed out).
-__device__ __forceinline__ bool grid_barrier(const PersistentArgs& a, unsigned long long target) {
+__device__ __forceinline__ unsigned long long atom_acq_rel_add(unsigned long long* p, unsigned long long v) {
+  unsigned long long old;
+  asm volatile("atom.acq_rel.gpu.global.add.u64 %0, [%1], %2;" : "=l"(old) : "l"(p), "l"(v) : "memory");
+  return old;
+}
+
+// Barrier instance `k` (0-based).  Returns false if the launch has failed
+// (this or another block timed out).
+__device__ __forceinline__ bool grid_barrier(const PersistentArgs& a, unsigned long long k) {
   __syncthreads();
   __shared__ int ok;
   if (threadIdx.x == 0) {
+    const unsigned G = gridDim.x;
+    const unsigned g = blockIdx.x % kBarGroups;
+    const unsigned n_groups = G < kBarGroups ? G : kBarGroups;
+    const unsigned long long n_in_group = G / kBarGroups + (g < G % kBarGroups ? 1u : 0u);
+    unsigned long long* top = a.bar + kBarGroups * kBarStride;
     __threadfence();
-    red_release_add(a.bar, 1ull);
+    const unsigned long long old = atom_acq_rel_add(a.bar + g * kBarStride, 1ull);
+    if (old + 1 == (k + 1) * n_in_group) red_release_add(top, 1ull);
+    const unsigned long long target = (k + 1) * n_groups + (a.poison ? 1ull : 0ull);
     const long long t0 = global_ns();
     int good = 1;
-    while (ld_acquire(a.bar) < target) {
+    while (ld_acquire(top) < target) {
       if (*reinterpret_cast<volatile int*>(a.status) != 0) {
         good = 0;
         break;
@@ -69,7 +91,7 @@ __device__ __forceinline__ bool grid_barrier(const PersistentArgs& a, unsigned l
         good = 0;
         break;
       }
-      __nanosleep(64);
+      __nanosleep(32);
     }
     ok = good;
   }
@@ -90,10 +112,9 @@ template <int KIND>
 __global__ void __launch_bounds__(KIND == kTileBlock ? kPersistentBlockThreads : 512, KIND == kTileBlock ? 3 : 1)
     k_persistent(PersistentArgs a) {
   extern __shared__ __align__(16) float sm[];
-  const unsigned long long G = gridDim.x;
   unsigned long long nbar = 0;
-  if (a.poison) {
-    grid_barrier(a, G + 1);
+  if (a.poison) {  // test hook: the first barrier waits for one arrival too many
+    grid_barrier(a, 0);
     return;
   }
   const int tid = threadIdx.x, B = blockDim.x;
@@ -156,7 +177,7 @@ __global__ void __launch_bounds__(KIND == kTileBlock ? kPersistentBlockThreads :
             block_sums_to(pp.partials + part * kNumSums, acc, tid, B, red);
           }
         }
-        if (!grid_barrier(a, (++nbar) * G)) return;
+        if (!grid_barrier(a, nbar++)) return;
       }
     }
     if (meas || swp) {
@@ -169,7 +190,7 @@ __global__ void __launch_bounds__(KIND == kTileBlock ? kPersistentBlockThreads :
       for (int l = blockIdx.x; l < a.n_lat; l += gridDim.x) finish_lattice(a.lats[l], l, fp);
       n_rec += meas ? 1 : 0;
       n_swp += swp ? 1 : 0;
-      if (!grid_barrier(a, (++nbar) * G)) return;
+      if (!grid_barrier(a, nbar++)) return;
     }
   }
 }
