@@ -384,13 +384,23 @@ def run_gpu(args):
     half = L_MAIN ** 3 // 2
     hbm, src = measured_peaks()
     ach = BYTES_PER_UPDATE * half / (ms_or * 1e-3) / 1e9
-    traffic = None
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    # DRAM bytes per launch from the committed ncu capture, valid only for the
+    # tile that capture used (the kernel is otherwise the same code)
+    traffic, traffic_note = None, "no ncu capture for this tile"
+    prof = os.path.join(ROOT, "profiles", "overrelax_L160_march8x8_traffic.txt")
     if os.path.exists(prof):
+        kv = {}
         with open(prof) as f:
-            traffic = json.load(f).get("overrelax_L160_bytes_per_launch")
+            for line in f:
+                if ":" in line and not line.startswith("#"):
+                    k, v = line.split(":", 1)
+                    kv[k.strip()] = v.strip()
+        if kv.get("tile") == ",".join(str(v) for v in tile):
+            traffic = int(kv["dram_bytes_per_launch"])
+            traffic_note = "cold-cache ncu capture (profiles/overrelax_L160_march8x8_ncu.md)"
     roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
-                "traffic": traffic, "kernel": "k_half<over-relaxation>, 160^3 half-sweep",
+                "traffic": traffic, "traffic_note": traffic_note,
+                "kernel": "k_half<over-relaxation>, 160^3 half-sweep",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
                 "note": "12 B/update algorithmic; lattice is L2-resident (16.4 MB < 126 MB)"}
     kernels = {"overrelax_half_ms": ms_or, "metropolis_half_ms": ms_met,

@@ -381,3 +381,31 @@ def test_barrier_timeout_reports_status_without_hanging():
     assert s.device_status() == 0
     s.sweep(1, 1, 3)
     assert s.get_state()[2][1] == 3
+
+
+def test_checkpoint_resume_is_bit_exact():
+    """get_state / set_state (natural layout) and get_packed / set_packed
+    (device layout) resume a run bit for bit: every draw is a pure function
+    of (seed, counters, slot, site)."""
+    from paper_1211_0780_b300 import xy
+    Ls, Rs, betas = [16, 24], [3, 2], [0.40, 0.45, 0.50, 0.44, 0.46]
+    a = sim(Ls, Rs, betas, series_capacity=32)
+    a.sweep(1, 2, 5, measure_every=1, pt_swap_every=1)
+    angles, perm, ctr = a.get_state()
+    packed = a.get_packed()
+    a.read_series()
+    a.sweep(1, 2, 6, measure_every=2, pt_swap_every=1)
+    want = (a.get_state(), a.read_series())
+    for use_packed in (False, True):
+        b = sim(Ls, Rs, betas, series_capacity=32)
+        if use_packed:
+            b.set_packed(packed)
+            b.set_state(None, perm, ctr)
+        else:
+            b.set_state(angles, perm, ctr)
+        b.set_exec(xy.EXEC_GRAPH)
+        b.sweep(1, 2, 6, measure_every=2, pt_swap_every=1)
+        got = (b.get_state(), b.read_series())
+        assert all(np.array_equal(x, y) for x, y in zip(got[0][0], want[0][0]))
+        assert np.array_equal(got[0][1], want[0][1]) and np.array_equal(got[0][2], want[0][2])
+        assert np.array_equal(got[1], want[1])
