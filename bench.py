@@ -397,17 +397,19 @@ def run_gpu(args):
                     kv[k.strip()] = v.strip()
         if kv.get("tile") == ",".join(str(v) for v in tile):
             traffic = int(kv["dram_bytes_per_launch"])
-            traffic_note = "cold-cache ncu capture (profiles/overrelax_L160_march8x8_ncu.md)"
+            traffic_note = ("cold-cache ncu capture (profiles/overrelax_L160_march8x8_ncu.md): the whole "
+                            "(cos, sin) state read once, 8 B per site against the 4 B per site of the "
+                            "12 B/update angle figure")
     roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "traffic_note": traffic_note,
                 "kernel": "k_half<over-relaxation>, 160^3 half-sweep",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
-                "note": "12 B/update algorithmic; lattice is L2-resident (16.4 MB < 126 MB)"}
+                "note": "12 B/update algorithmic; lattice state (cos, sin) is L2-resident (32.8 MB < 126 MB)"}
     kernels = {"overrelax_half_ms": ms_or, "metropolis_half_ms": ms_met,
                "overrelax_updates_per_ns": half / (ms_or * 1e6), "metropolis_updates_per_ns": half / (ms_met * 1e6)}
 
     # --- end to end through the C-ABI with host buffers --------------------
-    pinned = torch.empty(sim.n_angles(), dtype=torch.float32, pin_memory=True)
+    pinned = torch.empty(sim.n_packed(), dtype=torch.float32, pin_memory=True)
     sim.get_packed(pinned)
     e2e_steps = max(3, args.steps // 2)
     torch.cuda.synchronize()
@@ -418,7 +420,7 @@ def run_gpu(args):
         r = sim.read_series()    # D2H of the step's measurement (synchronises)
     t_e2e = time.perf_counter() - t0
     e2e = {"value": world * e2e_steps * UPDATES_PER_STEP / (t_e2e * 1e9), "unit": UNIT,
-           "h2d_bytes_per_step": int(sim.n_angles() * 4), "d2h_bytes_per_step": int(r.nbytes)}
+           "h2d_bytes_per_step": int(sim.n_packed() * 4), "d2h_bytes_per_step": int(r.nbytes)}
 
     extras = {}
     if not args.no_extras and rank == 0:

@@ -19,13 +19,16 @@
  *     data synchronise that stream.
  *   - Errors are sticky per context: after XY_ERR_CUDA or XY_ERR_TIMEOUT
  *     every call on the context returns XY_ERR_STATE until xy_destroy.
- *   - Angles are FP32 radians in [0, 2 pi).
+ *   - A spin is stored on the device as its unit vector (cos theta,
+ *     sin theta) in FP32.  Angles exchanged with the host (xy_get_state /
+ *     xy_set_state) are FP32 radians in [0, 2 pi).
  *
  * Lattice, colours and layout.  Site (x, y, z), 0 <= x, y, z < L, has colour
  * c = (x + y + z) mod 2 (0 = "black", 1 = "white"; Sec. II, Fig. 2).  L must
  * be a multiple of 8 (8 <= L <= 1024).  Host-side angle arrays use the
  * natural layout theta[x + L (y + L z)]; on the device each colour is a
- * separate packed array indexed p = (x >> 1) + (L/2)(y + L z).
+ * packed cos array and a packed sin array, both indexed
+ * p = (x >> 1) + (L/2)(y + L z).
  *
  * Random numbers.  Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11) with
  * key = (seed & 0xffffffff, seed >> 32).  The site with packed index p and
@@ -132,8 +135,8 @@ int xy_set_exec(xy_ctx *ctx, int mode);
  * theta' = 2 pi u0 and accepts iff u1 < exp(-beta dE), with dE = -[h_x
  * (cos theta' - cos theta) + h_y (sin theta' - sin theta)] and h the sum of
  * the six neighbour spin vectors.  Over-relaxation half-sweep (Eq. 2): the
- * spin is reflected about its local field, theta' = 2 atan2(h_y, h_x) -
- * theta (mod 2 pi); h = 0 leaves it.  Errors: XY_ERR_ARG (negative counts,
+ * spin is reflected about its local field, S' = 2 (S.h / h.h) h - S (as an
+ * angle theta' = 2 atan2(h_y, h_x) - theta mod 2 pi); h = 0 leaves it.  Errors: XY_ERR_ARG (negative counts,
  * n_metropolis + n_overrelax == 0 with n_sweeps > 0), XY_ERR_NOMEM (the
  * series buffer would overflow: read it first), XY_ERR_TIMEOUT, XY_ERR_CUDA. */
 int xy_sweep(xy_ctx *ctx, int n_metropolis, int n_overrelax, int n_sweeps,
@@ -168,23 +171,28 @@ int xy_read_series(xy_ctx *ctx, xy_record *host_buf, int64_t cap,
 int xy_series_count(xy_ctx *ctx, int64_t *n_out);
 
 /* State for parity checks and checkpoints.  host_angles: all slots
- * concatenated, natural layout, sum over slots of L^3 floats.  perm: for
- * each ladder in order, n_replicas entries (beta index -> local slot).
- * counters[4] = {Metropolis passes, sweeps, exchange events, records}.
- * Any pointer may be NULL to skip that part.  Because every draw is a pure
- * function of (seed, counters, slot, site), set_state(get_state()) resumes
- * a run bit-exactly. */
+ * concatenated, natural layout, sum over slots of L^3 floats; get_state
+ * returns atan2(sin, cos) of the stored vectors taken into [0, 2 pi),
+ * set_state stores (cos, sin) of the given angles (sincosf; every angle
+ * must be finite).  perm: for each ladder in order, n_replicas entries
+ * (beta index -> local slot).  counters[4] = {Metropolis passes, sweeps,
+ * exchange events, records}.  Any pointer may be NULL to skip that part.
+ * Every draw is a pure function of (seed, counters, slot, site), so
+ * restoring the counters and the packed state (xy_set_packed) resumes a run
+ * bit-exactly; restoring angles resumes it up to the FP32 rounding of the
+ * angle <-> vector conversion. */
 int xy_get_state(xy_ctx *ctx, float *host_angles, int32_t *perm,
                  uint64_t *counters);
 int xy_set_state(xy_ctx *ctx, const float *host_angles, const int32_t *perm,
                  const uint64_t *counters);
 
-/* The angles of every slot in the device's packed layout (for each slot:
- * colour 0's N/2 floats then colour 1's, p = (x >> 1) + (L/2)(y + L z)),
- * copied stream-ordered between the workspace and a host buffer of
- * sum over slots of L^3 floats (pinned memory makes the copy asynchronous;
- * the call returns after it completes).  Checkpoints and host round trips
- * without the layout conversion of xy_get_state / xy_set_state. */
+/* The spins of every slot in the device's packed layout (for each slot:
+ * colour 0's N/2 cosines, its N/2 sines, then colour 1's, indexed
+ * p = (x >> 1) + (L/2)(y + L z)), copied stream-ordered between the
+ * workspace and a host buffer of sum over slots of 2 L^3 floats (pinned
+ * memory makes the copy asynchronous; the call returns after it completes).
+ * Bit-exact checkpoints and host round trips without the conversion of
+ * xy_get_state / xy_set_state; set_packed takes the vectors as given. */
 int xy_get_packed(xy_ctx *ctx, float *host_packed);
 int xy_set_packed(xy_ctx *ctx, const float *host_packed);
 
@@ -199,28 +207,21 @@ int xy_get_accepts(xy_ctx *ctx, uint64_t *met, uint64_t *swap);
 int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
                    uint32_t *host_words);
 
-/* Evaluates the device's reflection-angle function (the one the
- * over-relaxation kernel uses) at n points: d_out[i] = 2 atan2(d_y[i],
- * d_x[i]) taken into [0, 2 pi], device arrays owned by the caller, ordered
- * on `stream`; for accuracy tests.  (x, y) = (0, 0) is not a valid input. */
-int xy_debug_two_atan2(int n, const float *d_x, const float *d_y, float *d_out,
-                       void *stream);
-
 /* Tile of lattice `lattice`.  kind 0 (march): a thread block of (L/8) x ty
  * threads covers full rows in x and ty rows in y and marches over tz planes
- * in z, evaluating each other-colour cos/sin about once.  kind 1 (block): a
+ * in z, loading each other-colour spin about once.  kind 1 (block): a
  * thread block of (L/8) x ty x tz threads covers ty rows x tz planes at
- * once after one cooperative evaluation of the tile's other-colour rows and
+ * once after one cooperative staging of the tile's other-colour rows and
  * face halos.  xy_set_tile checks 1 <= ty, tz <= L, the block size against
  * the kernels' limit (512 threads at their register use on sm_103a), tz <=
  * 64 for kind 1, and that the tile count fits the partial-sum area
- * (ceil(L/ty) ceil(L/tz) <= L^2/4).  Angles do not depend on the tile (the
+ * (ceil(L/ty) ceil(L/tz) <= L^2/4).  Spins do not depend on the tile (the
  * lattice sums only through FP64 summation order). */
 int xy_set_tile(xy_ctx *ctx, int lattice, int kind, int ty, int tz);
 int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
 
 /* Picks each lattice's tile (kind and shape) by timing the candidates on
- * the device for sweeps of `n_metropolis` + `n_overrelax` passes (the angles,
+ * the device for sweeps of `n_metropolis` + `n_overrelax` passes (the spins,
  * counters and accept counts are saved and restored); the choice stays in
  * the context.  In XY_EXEC_PERSISTENT mode only block tiles of at most 256
  * threads are candidates: a persistent launch needs one tile kind for all

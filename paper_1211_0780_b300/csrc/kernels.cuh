@@ -13,8 +13,9 @@ namespace xy {
 
 static_assert(sizeof(xy_record) == 96, "xy_record layout");
 
-// theta = 2 pi u from the initial-state stream; one Philox call per packed
-// pair (2q, 2q+1) of one colour of one slot.
+// theta = 2 pi u from the initial-state stream, stored as (cos, sin) with
+// the accurate sincosf (once per run); one Philox call per packed pair
+// (2q, 2q+1) of one colour of one slot.
 __global__ void k_init(Lattice lat, uint64_t seed) {
   const long long N = static_cast<long long>(lat.L) * lat.L * lat.L;
   const long long Q = N >> 2;  // pairs per colour
@@ -28,8 +29,39 @@ __global__ void k_init(Lattice lat, uint64_t seed) {
     const uint32_t tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) |
                           (static_cast<uint32_t>(c) << 3) | kTagInit;
     const uint4 w = philox4x32_10(make_uint4(q, 0u, 0u, tagw), key);
-    float* a = lat.angles + r * N + c * (N >> 1) + 2 * static_cast<long long>(q);
-    *reinterpret_cast<float2*>(a) = make_float2(u24(w.x) * kTwoPi, u24(w.z) * kTwoPi);
+    float* a = lat.spins + 2 * r * N + c * N + 2 * static_cast<long long>(q);
+    float c0, s0, c1, s1;
+    sincosf(u24(w.x) * kTwoPi, &s0, &c0);
+    sincosf(u24(w.z) * kTwoPi, &s1, &c1);
+    *reinterpret_cast<float2*>(a) = make_float2(c0, c1);
+    *reinterpret_cast<float2*>(a + (N >> 1)) = make_float2(s0, s1);
+  }
+}
+
+// Angles of one slot in the packed order (colour 0 then colour 1, N/2 each):
+// theta = atan2(sin, cos) taken into [0, 2 pi).
+__global__ void k_to_angles(const float* __restrict__ spins, long long N, float* __restrict__ out) {
+  const long long half = N >> 1;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long c = i / half, p = i - c * half;
+    const float* base = spins + c * N;
+    float t = atan2f(base[p + half], base[p]);
+    t = t < 0.f ? t + kTwoPi : t;
+    out[i] = t >= kTwoPi ? 0.f : t;
+  }
+}
+
+// The inverse: packed angles of one slot to stored (cos, sin) with sincosf.
+__global__ void k_from_angles(const float* __restrict__ in, long long N, float* __restrict__ spins) {
+  const long long half = N >> 1;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long c = i / half, p = i - c * half;
+    float sn, cs;
+    sincosf(in[i], &sn, &cs);
+    spins[c * N + p] = cs;
+    spins[c * N + half + p] = sn;
   }
 }
 
@@ -167,11 +199,6 @@ __device__ void finish_lattice(const Lattice& lat, int l, const FinishParams& fp
 __global__ void k_finish(const Lattice* lats, FinishParams fp) {
   chain_wait_and_release();
   finish_lattice(lats[blockIdx.x], blockIdx.x, fp);
-}
-
-__global__ void k_two_atan2(int n, const float* x, const float* y, float* out) {
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) out[i] = two_atan2(y[i], x[i]);
 }
 
 __global__ void k_advance(uint64_t* ctr, uint64_t d_mpass, uint64_t d_sweep, uint64_t d_swap,

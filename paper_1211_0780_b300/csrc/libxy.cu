@@ -26,12 +26,13 @@ namespace {
 
 constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+int conv_blocks(long long n) { return static_cast<int>(std::min<long long>((n + 255) / 256, 4096)); }
 
 struct LatHost {
   int L, R, slot0;
   int kind;  // kTileMarch or kTileBlock
   int ty, tz;
-  size_t angle_off;  // floats from the angle base
+  size_t spin_off;  // floats from the spin base (2N per slot)
   int part0;         // first partial slot
   int part_cap;      // partial slots reserved per slot
   long long N() const { return static_cast<long long>(L) * L * L; }
@@ -45,7 +46,7 @@ struct LatHost {
 int part_cap_for(int L) { return std::max(1, (L * L) / 4); }
 
 struct Layout {
-  size_t angles, ladder_beta, perm, beta_slot, beta_slot64, bidx_slot, E_slot, sums_slot, partials,
+  size_t spins, ladder_beta, perm, beta_slot, beta_slot64, bidx_slot, E_slot, sums_slot, partials,
       acc_met, acc_swap, ctr, status, barrier, nswapped, lats, staging, plan_items, plan_offs,
       series, total;
 };
@@ -65,10 +66,10 @@ bool valid_lattices(int n, const int* L, const int* R) {
 Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
   Layout o{};
   size_t off = 0;
-  long long angle_floats = 0, slots = 0, parts = 0, maxN = 0;
+  long long spin_floats = 0, slots = 0, parts = 0, maxN = 0;
   for (int i = 0; i < n; ++i) {
     const long long N = static_cast<long long>(L[i]) * L[i] * L[i];
-    angle_floats += N * R[i];
+    spin_floats += 2 * N * R[i];  // (cos, sin) per site
     slots += R[i];
     parts += static_cast<long long>(part_cap_for(L[i])) * R[i];
     maxN = std::max(maxN, N);
@@ -78,7 +79,7 @@ Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
     off = align_up(off + bytes);
     return at;
   };
-  o.angles = take(static_cast<size_t>(angle_floats) * 4);
+  o.spins = take(static_cast<size_t>(spin_floats) * 4);
   o.ladder_beta = take(slots * 8);
   o.perm = take(slots * 4);
   o.beta_slot = take(slots * 4);
@@ -137,12 +138,12 @@ struct xy_ctx {
 
   template <typename T>
   T* at(size_t off) const { return reinterpret_cast<T*>(ws + off); }
-  float* angles() const { return at<float>(lay.angles); }
+  float* spins() const { return at<float>(lay.spins); }
   uint64_t* ctr() const { return at<uint64_t>(lay.ctr); }
   Lattice dev_lat(int i) const {
     const LatHost& h = lat[i];
     Lattice d;
-    d.angles = angles() + h.angle_off;
+    d.spins = spins() + h.spin_off;
     d.L = h.L;
     d.R = h.R;
     d.slot0 = h.slot0;
@@ -458,10 +459,10 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
     h.R = n_replicas[i];
     h.slot0 = slot;
     default_tile(h);
-    h.angle_off = aoff;
+    h.spin_off = aoff;
     h.part_cap = part_cap_for(h.L);
     h.part0 = part;
-    aoff += static_cast<size_t>(h.N()) * h.R;
+    aoff += 2 * static_cast<size_t>(h.N()) * h.R;  // (cos, sin) per site
     slot += h.R;
     part += h.part_cap * h.R;
     c->lat.push_back(h);
@@ -731,7 +732,10 @@ int xy_get_state(xy_ctx* c, float* host_angles, int32_t* perm, uint64_t* counter
       const int Hh = h.L / 2;
       std::vector<float> packed(static_cast<size_t>(N));
       for (int r = 0; r < h.R; ++r) {
-        XY_TRY(c, cudaMemcpyAsync(packed.data(), c->angles() + h.angle_off + r * N, N * 4, cudaMemcpyDeviceToHost, c->stream));
+        float* stage = c->at<float>(c->lay.staging);
+        k_to_angles<<<conv_blocks(N), 256, 0, c->stream>>>(c->spins() + h.spin_off + 2 * r * N, N, stage);
+        XY_CHECK_LAUNCH(c);
+        XY_TRY(c, cudaMemcpyAsync(packed.data(), stage, N * 4, cudaMemcpyDeviceToHost, c->stream));
         XY_TRY(c, cudaStreamSynchronize(c->stream));
         float* dst = host_angles + at;
         for (int z = 0; z < h.L; ++z)
@@ -780,7 +784,10 @@ int xy_set_state(xy_ctx* c, const float* host_angles, const int32_t* perm, const
               if (!std::isfinite(v)) return XY_ERR_ARG;
               packed[col * (N / 2) + p] = v;
             }
-        XY_TRY(c, cudaMemcpyAsync(c->angles() + h.angle_off + r * N, packed.data(), N * 4, cudaMemcpyHostToDevice, c->stream));
+        float* stage = c->at<float>(c->lay.staging);
+        XY_TRY(c, cudaMemcpyAsync(stage, packed.data(), N * 4, cudaMemcpyHostToDevice, c->stream));
+        k_from_angles<<<conv_blocks(N), 256, 0, c->stream>>>(stage, N, c->spins() + h.spin_off + 2 * r * N);
+        XY_CHECK_LAUNCH(c);
         XY_TRY(c, cudaStreamSynchronize(c->stream));
         at += static_cast<size_t>(N);
       }
@@ -818,10 +825,9 @@ int xy_set_state(xy_ctx* c, const float* host_angles, const int32_t* perm, const
 int xy_get_packed(xy_ctx* c, float* host_packed) {
   XY_ENTER(c);
   if (!host_packed) return XY_ERR_ARG;
-  const size_t bytes = c->lay.ladder_beta - c->lay.angles;
   size_t n = 0;
-  for (const LatHost& h : c->lat) n += static_cast<size_t>(h.N()) * h.R;
-  XY_TRY(c, cudaMemcpyAsync(host_packed, c->angles(), std::min(bytes, n * 4), cudaMemcpyDeviceToHost, c->stream));
+  for (const LatHost& h : c->lat) n += 2 * static_cast<size_t>(h.N()) * h.R;
+  XY_TRY(c, cudaMemcpyAsync(host_packed, c->spins(), n * 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
   return XY_OK;
 }
@@ -830,8 +836,8 @@ int xy_set_packed(xy_ctx* c, const float* host_packed) {
   XY_ENTER(c);
   if (!host_packed) return XY_ERR_ARG;
   size_t n = 0;
-  for (const LatHost& h : c->lat) n += static_cast<size_t>(h.N()) * h.R;
-  XY_TRY(c, cudaMemcpyAsync(c->angles(), host_packed, n * 4, cudaMemcpyHostToDevice, c->stream));
+  for (const LatHost& h : c->lat) n += 2 * static_cast<size_t>(h.N()) * h.R;
+  XY_TRY(c, cudaMemcpyAsync(c->spins(), host_packed, n * 4, cudaMemcpyHostToDevice, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
   return XY_OK;
 }
@@ -858,14 +864,6 @@ int xy_debug_draws(xy_ctx* c, int slot, int colour, int tag, uint64_t count, uin
   XY_CHECK_LAUNCH(c);
   XY_TRY(c, cudaMemcpyAsync(host_words, dev, 2 * half * 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
-  return XY_OK;
-}
-
-int xy_debug_two_atan2(int n, const float* d_x, const float* d_y, float* d_out, void* stream) {
-  if (n <= 0 || !d_x || !d_y || !d_out) return XY_ERR_ARG;
-  k_two_atan2<<<(n + 255) / 256, 256, 0, static_cast<cudaStream_t>(stream)>>>(n, d_x, d_y, d_out);
-  const cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return fail_cuda(nullptr, e, "k_two_atan2");
   return XY_OK;
 }
 
@@ -1109,11 +1107,11 @@ int xy_debug_barrier_timeout(xy_ctx* c, int budget_us, int* status_out) {
 int xy_autotune(xy_ctx* c, int nM, int nOR) {
   XY_ENTER(c);
   if (nM < 0 || nOR < 0 || nM + nOR == 0) return XY_ERR_ARG;
-  // Save what trial sweeps change: angles, counters, Metropolis accepts.
-  const size_t angle_bytes = c->lay.ladder_beta - c->lay.angles;
-  std::vector<char> angles(angle_bytes);
+  // Save what trial sweeps change: spins, counters, Metropolis accepts.
+  const size_t spin_bytes = c->lay.ladder_beta - c->lay.spins;
+  std::vector<char> saved(spin_bytes);
   std::vector<char> ctr(kNumCounters * 8), acc(static_cast<size_t>(c->n_slots) * 8);
-  XY_TRY(c, cudaMemcpyAsync(angles.data(), c->ws + c->lay.angles, angle_bytes, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(saved.data(), c->ws + c->lay.spins, spin_bytes, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemcpyAsync(ctr.data(), c->ws + c->lay.ctr, ctr.size(), cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemcpyAsync(acc.data(), c->ws + c->lay.acc_met, acc.size(), cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1177,7 +1175,7 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
   if (rc != XY_OK) return rc;
   rc = sync_lats(c);
   if (rc != XY_OK) return rc;
-  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.angles, angles.data(), angle_bytes, cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.spins, saved.data(), spin_bytes, cudaMemcpyHostToDevice, c->stream));
   XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.ctr, ctr.data(), ctr.size(), cudaMemcpyHostToDevice, c->stream));
   XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.acc_met, acc.data(), acc.size(), cudaMemcpyHostToDevice, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));

@@ -2,30 +2,38 @@
 // (Sec. II, Fig. 2), over-relaxation (Sec. II, Eq. 2) and the lattice sums of
 // Eqs. (4)-(6), fused into one tile pass.
 //
-// Layout.  Each slot (replica) of an L^3 lattice holds two packed FP32 angle
-// arrays, colour 0 then colour 1, of N/2 floats each; site (x, y, z) of colour
-// c = (x+y+z) & 1 sits at p = (x >> 1) + (L/2)(y + L z) of array c.  A row
-// (y, z) of one colour is L/2 contiguous floats, so a thread owns one float4
-// = 4 same-colour sites of a row (x = 2k + s, k = 4 tx .. 4 tx + 3, with
+// State.  A spin is stored as its unit vector S = (cos theta, sin theta) in
+// FP32, not as its angle: the reflection of Eq. (2) is then plain vector
+// arithmetic, S' = 2 (S.h / h.h) h - S, and neither the neighbour cos/sin nor
+// an arctangent is evaluated on the hot path.  Metropolis proposals
+// theta' = 2 pi u are turned into vectors once, when drawn.  Angles are
+// computed only when the state is read out.
+//
+// Layout.  Each slot (replica) of an L^3 lattice holds colour 0 then colour
+// 1; each colour is a packed cos array then a packed sin array of N/2 floats;
+// site (x, y, z) of colour c = (x+y+z) & 1 sits at p = (x >> 1) + (L/2)(y + L z)
+// of both arrays of colour c.  A row (y, z) of one colour is L/2 contiguous
+// floats per component, so a thread owns one float4 per component = 4
+// same-colour sites of a row (x = 2k + s, k = 4 tx .. 4 tx + 3, with
 // s = (y + z + c) & 1).  Its six neighbours are all of the other colour:
 //   x-1, x+1 -> same row, packed k-1+s and k+s (one element comes from the
 //               neighbouring float4, with periodic wrap along the row);
 //   y+-1, z+-1 -> the other colour's rows (y+-1, z), (y, z+-1) at the same k.
 //
 // Tile.  A thread block covers full rows in x, `ty` rows in y and marches
-// over `tz` planes in z.  The cos/sin of every other-colour site it needs is
-// evaluated once per block: a thread evaluates its own row of plane z+1 and
-// keeps planes z-1, z, z+1 of its own column in registers; planes are shared
-// through three shared-memory buffers (one barrier per plane) for the y
-// neighbours and the x halo element.  The thread rows at the tile's y edges
-// also evaluate the halo rows y0-1 and y0+ty.  Cost per update:
-// (ty+2)(tz+2)/(ty tz) sincos evaluations instead of six.  The plane loop is
+// over `tz` planes in z.  A thread loads its own row of the other colour's
+// plane z+1 and keeps planes z-1, z, z+1 of its own column in registers;
+// planes are shared through three shared-memory buffers (one barrier per
+// plane) for the y neighbours and the x halo element.  The thread rows at the
+// tile's y edges also load the halo rows y0-1 and y0+ty.  The plane loop is
 // unrolled three times so the register planes and the buffer indices rotate
 // without copies.
 //
-// Accuracy.  Angles live in [0, 2 pi); the fast sincos is evaluated at
-// theta - pi, inside [-pi, pi) where its absolute error is ~2^-21.4, and
-// negated.  The reflection angle uses the polynomial two_atan2 below.
+// Accuracy.  The reflection renormalises its result with one Newton step
+// towards |S| = 1, so stored vectors stay within a few ulp of the unit
+// circle however many reflections a spin goes through; the direction (the
+// angle) is not changed by that step.  Proposal vectors use the fast sincos,
+// evaluated at theta - pi inside [-pi, pi) (absolute error ~2^-21.4).
 #pragma once
 #include <cstdint>
 
@@ -43,10 +51,10 @@ constexpr int kReduceBytes = kNumSums * 32 * 8;   // per-warp FP64 partials
 enum Mode : int { kMetropolis = 0, kOverrelax = 1, kMeasureOnly = 2 };
 
 // Tile kinds.  kTileMarch: a block of (L/8) x ty threads marches over tz
-// planes (each other-colour site's cos/sin evaluated ~once, but the planes
-// are processed in sequence).  kTileBlock: a block of (L/8) x ty x tz threads
-// updates its whole tile at once after one cooperative evaluation of the
-// tile's other-colour rows and face halos (more evaluations, no sequence).
+// planes (each other-colour site loaded ~once, but the planes are processed
+// in sequence).  kTileBlock: a block of (L/8) x ty x tz threads updates its
+// whole tile at once after one cooperative staging of the tile's
+// other-colour rows and face halos (more loads, no sequence).
 enum TileKind : int { kTileMarch = 0, kTileBlock = 1 };
 
 // Device-resident counters (graph replays read them instead of baking
@@ -62,7 +70,7 @@ enum Counter : int {
 
 // One lattice (= one exchange ladder) as the kernels see it.
 struct Lattice {
-  float* angles;  // slot r, colour c at angles + r*N + c*(N/2)
+  float* spins;   // slot r, colour c: cos at spins + 2rN + cN, sin N/2 further
   int L;
   int R;
   int slot0;      // global index of local slot 0
@@ -114,48 +122,20 @@ __device__ __forceinline__ void spin(float th, float& c, float& s) {
   s = -sn;
 }
 
-// 2 atan2(y, x) taken into [0, 2 pi] (the doubled field angle the
-// reflection needs), for (x, y) != (0, 0).  Octant reduction: r = min(|x|,|y|)
-// / max(|x|,|y|) in [0, 1] and q = 2 atan(r) = r P(r^2), with a degree-7
-// polynomial in r^2 fitted to 2 atan(r) / r on [0, 1] (weighted least squares
-// iterated towards the minimax error; |error| of atan <= 3.8e-8 in exact
-// arithmetic, <= 1.5e-7 with FP32 Horner).  The three reflections of the
-// octant reduction (|y| > |x|: pi - q; x < 0: 2 pi - ...; y < 0: 2 pi - ...)
-// compose to base + (-1)^k q, where k counts the reflections applied and
-// base = pi if |y| > |x|, else 2 pi if x and y have opposite signs, else 0.
-// Tested against FP64 atan2.
-__device__ __forceinline__ float two_atan2(float y, float x) {
-  const float ax = fabsf(x), ay = fabsf(y);
-  float rc;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rc) : "f"(fmaxf(ax, ay)));
-  const float r = fminf(ax, ay) * rc;
-  const float s = r * r;
-  float p = -8.109124919e-03f;
-  p = fmaf(p, s, 4.372588046e-02f);
-  p = fmaf(p, s, -1.118246012e-01f);
-  p = fmaf(p, s, 1.928439072e-01f);
-  p = fmaf(p, s, -2.781725752e-01f);
-  p = fmaf(p, s, 3.989313098e-01f);
-  p = fmaf(p, s, -6.665972154e-01f);
-  p = fmaf(p, s, 1.999998671e+00f);
-  const bool swap = ay > ax;
-  const uint32_t xb = __float_as_uint(x), yb = __float_as_uint(y);
-  // sign of (-1)^k: one bit each for swap, x < 0, y < 0 (signed zeros count
-  // as their sign, which only moves the result between 0 and 2 pi)
-  const uint32_t flip = (xb ^ yb ^ (swap ? 0x80000000u : 0u)) & 0x80000000u;
-  const float sq = __uint_as_float(__float_as_uint(p * r) ^ flip);
-  const float base = swap ? kPi : (((xb ^ yb) & 0x80000000u) ? kTwoPi : 0.f);
-  return base + sq;
-}
-
-// The reflection of Eq. (2) as an angle: theta' = 2 phi - theta mod 2 pi,
-// phi = arg h, branch free.  h = 0 leaves theta (Sec. II reading: no field,
-// no reflection).  Result in [0, 2 pi).
-__device__ __forceinline__ float reflect(float hx, float hy, float th) {
-  float t = two_atan2(hy, hx) - th;      // in (-2 pi, 2 pi]
-  t = (t < 0.f) ? t + kTwoPi : t;
-  t = (t >= kTwoPi) ? t - kTwoPi : t;
-  return (hx == 0.f && hy == 0.f) ? th : t;
+// The reflection of Eq. (2) at the field h = sum of the six neighbour
+// vectors: S' = 2 (S.h / h.h) h - S, followed by one Newton step of the norm
+// (S' *= 3/2 - |S'|^2 / 2).  h = 0 leaves S (Sec. II reading: no field, no
+// reflection); so does a field whose squared length underflows.
+__device__ __forceinline__ void reflect(float hx, float hy, float c, float s, float& c1, float& s1) {
+  const float n2 = fmaf(hy, hy, hx * hx);
+  float rn;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rn) : "f"(n2));
+  const float k = 2.f * fmaf(s, hy, c * hx) * rn;
+  const float a = fmaf(k, hx, -c), b = fmaf(k, hy, -s);
+  const float f = fmaf(-0.5f, fmaf(b, b, a * a), 1.5f);
+  const bool keep = !(n2 > 0.f);
+  c1 = keep ? c : a * f;
+  s1 = keep ? s : b * f;
 }
 
 struct Spins4 {
@@ -163,22 +143,26 @@ struct Spins4 {
   float s[4];
 };
 
-__device__ __forceinline__ Spins4 spins4(float4 t) {
-  Spins4 v;
-  spin(t.x, v.c[0], v.s[0]);
-  spin(t.y, v.c[1], v.s[1]);
-  spin(t.z, v.c[2], v.s[2]);
-  spin(t.w, v.c[3], v.s[3]);
-  return v;
-}
-
-// Angle loads and stores go through L2 (.cg): the persistent kernel reads
+// Spin loads and stores go through L2 (.cg): the persistent kernel reads
 // values other blocks wrote earlier in the same launch.
 __device__ __forceinline__ float4 ld4(const float* p) {
   return __ldcg(reinterpret_cast<const float4*>(p));
 }
 __device__ __forceinline__ void st4(float* p, float4 v) {
   __stcg(reinterpret_cast<float4*>(p), v);
+}
+
+// The 4 spins of one thread's row segment: cos at p, sin at p + half.
+__device__ __forceinline__ Spins4 ld_spins(const float* p, uint32_t half) {
+  const float4 c = ld4(p), s = ld4(p + half);
+  Spins4 v;
+  v.c[0] = c.x; v.c[1] = c.y; v.c[2] = c.z; v.c[3] = c.w;
+  v.s[0] = s.x; v.s[1] = s.y; v.s[2] = s.z; v.s[3] = s.w;
+  return v;
+}
+__device__ __forceinline__ void st_spins(float* p, uint32_t half, const float c[4], const float s[4]) {
+  st4(p, make_float4(c[0], c[1], c[2], c[3]));
+  st4(p + half, make_float4(s[0], s[1], s[2], s[3]));
 }
 
 __device__ __forceinline__ void put_row(float* row, int H, int tx, const Spins4& v) {
@@ -246,9 +230,9 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
   const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
   const bool act = in_block && ty < TYa;
   const int y = y0 + ty;
-  float* const slot = lat.angles + static_cast<size_t>(r) * (2 * static_cast<size_t>(half));
-  float* const own = slot + colour * half;
-  const float* const oth = slot + (colour ^ 1) * half;
+  float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  float* const own = slot + colour * (2 * half);            // cos; sin at + half
+  const float* const oth = slot + (colour ^ 1) * (2 * half);
   const int rows = lat.ty + 2;
   const int ym = (y0 == 0 ? L : y0) - 1;          // halo row y0 - 1 (periodic)
   const int yp = (y0 + TYa == L) ? 0 : y0 + TYa;  // halo row y0 + TYa
@@ -275,21 +259,21 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
   SumAcc<MEAS> sums;
 
   Spins4 pa{}, pb{}, pc{};  // rotating register planes (other colour, own column)
-  float4 nx_oth = make_float4(0.f, 0.f, 0.f, 0.f), nx_own = nx_oth, nx_h0 = nx_oth, nx_h1 = nx_oth;
+  Spins4 nx_oth{}, nx_own{}, nx_h0{}, nx_h1{};
   if (act) {
     const uint32_t zb = static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS;
     const uint32_t zz = static_cast<uint32_t>(z0) * PS;
     const uint32_t z1 = static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS;
-    pa = spins4(ld4(oth + offy + zb));
-    pb = spins4(ld4(oth + offy + zz));
+    pa = ld_spins(oth + offy + zb, half);
+    pb = ld_spins(oth + offy + zz, half);
     put_row(row_ptr(0, ty + 1), H, tx, pb);
-    if (top) put_row(row_ptr(0, 0), H, tx, spins4(ld4(oth + offym + zz)));
-    if (bot) put_row(row_ptr(0, TYa + 1), H, tx, spins4(ld4(oth + offyp + zz)));
-    nx_oth = ld4(oth + offy + z1);
-    nx_own = ld4(own + offy + zz);
+    if (top) put_row(row_ptr(0, 0), H, tx, ld_spins(oth + offym + zz, half));
+    if (bot) put_row(row_ptr(0, TYa + 1), H, tx, ld_spins(oth + offyp + zz, half));
+    nx_oth = ld_spins(oth + offy + z1, half);
+    nx_own = ld_spins(own + offy + zz, half);
     if (TZa > 1) {
-      if (top) nx_h0 = ld4(oth + offym + z1);
-      if (bot) nx_h1 = ld4(oth + offyp + z1);
+      if (top) nx_h0 = ld_spins(oth + offym + z1, half);
+      if (bot) nx_h1 = ld_spins(oth + offyp + z1, half);
     }
   }
   __syncthreads();
@@ -300,22 +284,21 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
     constexpr int b1 = b0 == 2 ? 0 : b0 + 1;
     const int z = z0 + i;
     if (act) {
-      const float4 t_oth = nx_oth, t_own = nx_own, t_h0 = nx_h0, t_h1 = nx_h1;
-      if (i + 1 < TZa) {  // prefetch the next plane's operands
-        const uint32_t pz1 = static_cast<uint32_t>(z + 1) * PS;
-        const uint32_t pz2 = static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS;
-        nx_oth = ld4(oth + offy + pz2);
-        nx_own = ld4(own + offy + pz1);
-        if (i + 2 < TZa) {
-          if (top) nx_h0 = ld4(oth + offym + pz2);
-          if (bot) nx_h1 = ld4(oth + offyp + pz2);
-        }
-      }
-      zn = spins4(t_oth);
+      const Spins4 t_own = nx_own;
+      zn = nx_oth;
       if (i + 1 < TZa) {
         put_row(row_ptr(b1, ty + 1), H, tx, zn);
-        if (top) put_row(row_ptr(b1, 0), H, tx, spins4(t_h0));
-        if (bot) put_row(row_ptr(b1, TYa + 1), H, tx, spins4(t_h1));
+        if (top) put_row(row_ptr(b1, 0), H, tx, nx_h0);
+        if (bot) put_row(row_ptr(b1, TYa + 1), H, tx, nx_h1);
+        // prefetch the next plane's operands
+        const uint32_t pz1 = static_cast<uint32_t>(z + 1) * PS;
+        const uint32_t pz2 = static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS;
+        nx_oth = ld_spins(oth + offy + pz2, half);
+        nx_own = ld_spins(own + offy + pz1, half);
+        if (i + 2 < TZa) {
+          if (top) nx_h0 = ld_spins(oth + offym + pz2, half);
+          if (bot) nx_h1 = ld_spins(oth + offyp + pz2, half);
+        }
       }
       const float* rm = row_ptr(b0, ty);
       const float* rp = row_ptr(b0, ty + 2);
@@ -338,8 +321,7 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
         Xs[e] = s ? a_s : b_s;
       }
       const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
-      const float th[4] = {t_own.x, t_own.y, t_own.z, t_own.w};
-      float tn[4], nc[4], ns[4];
+      float nc[4], ns[4];
       uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
       if (MODE == kMetropolis) {
         const uint32_t q0 = offz >> 1;
@@ -353,29 +335,26 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
       for (int e = 0; e < 4; ++e) {
         const float hx = (Xc[e] + Xc[e + 1]) + (comp(ymc, e) + comp(ypc, e)) + (zm.c[e] + zn.c[e]);
         const float hy = (Xs[e] + Xs[e + 1]) + (comp(yms, e) + comp(yps, e)) + (zm.s[e] + zn.s[e]);
+        const float co = t_own.c[e], so = t_own.s[e];
         if (MODE == kMetropolis) {
           const uint4& w = (e < 2) ? w0 : w1;
           const uint32_t wprop = (e & 1) ? w.z : w.x;
           const uint32_t wacc = (e & 1) ? w.w : w.y;
           const float tp = static_cast<float>(wprop >> 8) * kTwoPiOver2p24;  // = u0 * 2 pi
-          float cp, sp, co, so;
+          float cp, sp;
           spin(tp, cp, sp);
-          spin(th[e], co, so);
           // -beta dE with dE = -[h_x (cos t' - cos t) + h_y (sin t' - sin t)]
           const float x = beta * (hx * (cp - co) + hy * (sp - so));
           // u1 < exp(x)  <=>  (w >> 8) < exp(x) 2^24 (exact scaling)
           const bool accept = static_cast<float>(wacc >> 8) < __expf(x) * 16777216.0f;
           n_acc += accept ? 1u : 0u;
-          tn[e] = accept ? tp : th[e];
           nc[e] = accept ? cp : co;
           ns[e] = accept ? sp : so;
         } else if (MODE == kOverrelax) {
-          const float t = reflect(hx, hy, th[e]);  // reflection about the field
-          tn[e] = t;
-          if (MEAS) spin(t, nc[e], ns[e]);
+          reflect(hx, hy, co, so, nc[e], ns[e]);  // reflection about the field
         } else {
-          tn[e] = th[e];
-          spin(th[e], nc[e], ns[e]);
+          nc[e] = co;
+          ns[e] = so;
         }
         if (MEAS) {
           // Bonds (w, w+mu) and (w-mu, w) of the white site w: every bond has
@@ -395,7 +374,7 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
         }
       }
       if (MEAS) sums.add_plane(stepv);
-      if (MODE != kMeasureOnly) st4(own + offz, make_float4(tn[0], tn[1], tn[2], tn[3]));
+      if (MODE != kMeasureOnly) st_spins(own + offz, half, nc, ns);
     }
     __syncthreads();
   };
@@ -410,14 +389,14 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
   if (MEAS) sums.export_to(acc_out);
 }
 
-// One tile of one half-sweep, kTileBlock: thread (tx, ty, tz) owns the float4
-// at row y0+ty of plane z0+tz.  Prologue: every thread evaluates the
-// other-colour cos/sin of its own row; threads on the tile's faces also
-// evaluate the face-halo rows (y0-1, y0+TYa at each plane; z0-1, z0+TZa at
-// each row).  One barrier, then each thread reads its six neighbours from
-// shared memory.  The per-site arithmetic (field in the same association
-// order, Metropolis, reflection, lattice sums) is the march kind's, so both
-// kinds give bit-identical angles.
+// One tile of one half-sweep, kTileBlock: thread (tx, ty, tz) owns the 4
+// sites at row y0+ty of plane z0+tz.  Prologue: every thread stages the
+// other-colour spins of its own row in shared memory; threads on the tile's
+// faces also stage the face-halo rows (y0-1, y0+TYa at each plane; z0-1,
+// z0+TZa at each row).  One barrier, then each thread reads its six
+// neighbours from shared memory.  The per-site arithmetic (field in the same
+// association order, Metropolis, reflection, lattice sums) is the march
+// kind's, so both kinds give bit-identical spins.
 template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, int zt, int colour,
                                            int tx, int ty, int tz, bool in_block, const PassParams& pp,
@@ -431,9 +410,9 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
   const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
   const bool act = in_block && ty < TYa && tz < TZa;
   const int y = y0 + ty, z = z0 + tz;
-  float* const slot = lat.angles + static_cast<size_t>(r) * (2 * static_cast<size_t>(half));
-  float* const own = slot + colour * half;
-  const float* const oth = slot + (colour ^ 1) * half;
+  float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  float* const own = slot + colour * (2 * half);            // cos; sin at + half
+  const float* const oth = slot + (colour ^ 1) * (2 * half);
   const int stride_z = lat.ty + 2;  // rows per plane in shared memory
   auto row_ptr = [&](int dy, int dz) -> float* { return sm + (dz * stride_z + dy) * 2 * H; };
   const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
@@ -452,25 +431,25 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
     mhi = static_cast<uint32_t>(mp >> 32);
   }
 
-  float4 t_own = make_float4(0.f, 0.f, 0.f, 0.f);
+  Spins4 t_own{};
   if (act) {
-    t_own = ld4(own + offz);
+    t_own = ld_spins(own + offz, half);
     const bool zlo = tz == 0, zhi = tz == TZa - 1, ylo = ty == 0, yhi = ty == TYa - 1;
     const uint32_t pzm = static_cast<uint32_t>(z == 0 ? L - 1 : z - 1) * PS;
     const uint32_t pzp = static_cast<uint32_t>(z + 1 == L ? 0 : z + 1) * PS;
     const uint32_t oym = static_cast<uint32_t>(H * (y == 0 ? L - 1 : y - 1) + 4 * tx);
     const uint32_t oyp = static_cast<uint32_t>(H * (y + 1 == L ? 0 : y + 1) + 4 * tx);
-    const float4 a0 = ld4(oth + offz);
-    float4 a1 = a0, a2 = a0, a3 = a0, a4 = a0;
-    if (zlo) a1 = ld4(oth + offy + pzm);
-    if (zhi) a2 = ld4(oth + offy + pzp);
-    if (ylo) a3 = ld4(oth + oym + static_cast<uint32_t>(z) * PS);
-    if (yhi) a4 = ld4(oth + oyp + static_cast<uint32_t>(z) * PS);
-    put_row(row_ptr(ty + 1, tz + 1), H, tx, spins4(a0));
-    if (zlo) put_row(row_ptr(ty + 1, 0), H, tx, spins4(a1));
-    if (zhi) put_row(row_ptr(ty + 1, TZa + 1), H, tx, spins4(a2));
-    if (ylo) put_row(row_ptr(0, tz + 1), H, tx, spins4(a3));
-    if (yhi) put_row(row_ptr(TYa + 1, tz + 1), H, tx, spins4(a4));
+    const Spins4 a0 = ld_spins(oth + offz, half);
+    Spins4 a1 = a0, a2 = a0, a3 = a0, a4 = a0;
+    if (zlo) a1 = ld_spins(oth + offy + pzm, half);
+    if (zhi) a2 = ld_spins(oth + offy + pzp, half);
+    if (ylo) a3 = ld_spins(oth + oym + static_cast<uint32_t>(z) * PS, half);
+    if (yhi) a4 = ld_spins(oth + oyp + static_cast<uint32_t>(z) * PS, half);
+    put_row(row_ptr(ty + 1, tz + 1), H, tx, a0);
+    if (zlo) put_row(row_ptr(ty + 1, 0), H, tx, a1);
+    if (zhi) put_row(row_ptr(ty + 1, TZa + 1), H, tx, a2);
+    if (ylo) put_row(row_ptr(0, tz + 1), H, tx, a3);
+    if (yhi) put_row(row_ptr(TYa + 1, tz + 1), H, tx, a4);
   }
   __syncthreads();
   if (act) {
@@ -502,8 +481,7 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
       Xc[e] = s ? a_c : b_c;
       Xs[e] = s ? a_s : b_s;
     }
-    const float th[4] = {t_own.x, t_own.y, t_own.z, t_own.w};
-    float tn[4], nc[4], ns[4];
+    float nc[4], ns[4];
     uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
     if (MODE == kMetropolis) {
       const uint32_t q0 = offz >> 1;
@@ -517,27 +495,24 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
     for (int e = 0; e < 4; ++e) {
       const float hx = (Xc[e] + Xc[e + 1]) + (comp(ymc, e) + comp(ypc, e)) + (comp(zmc, e) + comp(zpc, e));
       const float hy = (Xs[e] + Xs[e + 1]) + (comp(yms, e) + comp(yps, e)) + (comp(zms, e) + comp(zps, e));
+      const float co = t_own.c[e], so = t_own.s[e];
       if (MODE == kMetropolis) {
         const uint4& w = (e < 2) ? w0 : w1;
         const uint32_t wprop = (e & 1) ? w.z : w.x;
         const uint32_t wacc = (e & 1) ? w.w : w.y;
         const float tp = static_cast<float>(wprop >> 8) * kTwoPiOver2p24;
-        float cp, sp, co, so;
+        float cp, sp;
         spin(tp, cp, sp);
-        spin(th[e], co, so);
         const float x = beta * (hx * (cp - co) + hy * (sp - so));
         const bool accept = static_cast<float>(wacc >> 8) < __expf(x) * 16777216.0f;
         n_acc += accept ? 1u : 0u;
-        tn[e] = accept ? tp : th[e];
         nc[e] = accept ? cp : co;
         ns[e] = accept ? sp : so;
       } else if (MODE == kOverrelax) {
-        const float t = reflect(hx, hy, th[e]);
-        tn[e] = t;
-        if (MEAS) spin(t, nc[e], ns[e]);
+        reflect(hx, hy, co, so, nc[e], ns[e]);
       } else {
-        tn[e] = th[e];
-        spin(th[e], nc[e], ns[e]);
+        nc[e] = co;
+        ns[e] = so;
       }
       if (MEAS) {
         const float c = nc[e], sn = ns[e];
@@ -558,7 +533,7 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
 #pragma unroll
       for (int j = 0; j < kNumSums; ++j) acc_out[j] = stepv[j];
     }
-    if (MODE != kMeasureOnly) st4(own + offz, make_float4(tn[0], tn[1], tn[2], tn[3]));
+    if (MODE != kMeasureOnly) st_spins(own + offz, half, nc, ns);
   }
   // The shared rows may be overwritten by the caller's next tile.
   __syncthreads();

@@ -71,7 +71,6 @@ _SIGNATURES = {
     "xy_get_packed": (_I, [_P, _P]),
     "xy_set_packed": (_I, [_P, _P]),
     "xy_debug_draws": (_I, [_P, _I, _I, _I, _U64, _P]),
-    "xy_debug_two_atan2": (_I, [_I, _P, _P, _P, _P]),
     "xy_set_tile": (_I, [_P, _I, _I, _I, _I]),
     "xy_get_tile": (_I, [_P, _I, _P, _P, _P]),
     "xy_autotune": (_I, [_P, _I, _I]),
@@ -237,14 +236,15 @@ class Simulation:
                                   _ptr(p) if p is not None else None,
                                   _ptr(c) if c is not None else None), "xy_set_state")
 
-    def n_angles(self) -> int:
-        return int(sum(L ** 3 * R for L, R in zip(self.L, self.R)))
+    def n_packed(self) -> int:
+        """Floats of the device state: (cos, sin) of every site of every slot."""
+        return int(sum(2 * L ** 3 * R for L, R in zip(self.L, self.R)))
 
     def get_packed(self, out=None):
-        """All angles in the device layout into ``out`` (numpy float32 or a
-        pinned CPU torch tensor of n_angles() floats)."""
+        """All spins in the device layout into ``out`` (numpy float32 or a
+        pinned CPU torch tensor of n_packed() floats)."""
         if out is None:
-            out = np.zeros(self.n_angles(), dtype=np.float32)
+            out = np.zeros(self.n_packed(), dtype=np.float32)
         ptr = out.data_ptr() if hasattr(out, "data_ptr") else _ptr(out)
         _check(lib().xy_get_packed(self._ctx, ptr), "xy_get_packed")
         return out
@@ -309,17 +309,6 @@ def peak_probe(kind: str) -> float:
     _check(lib().xy_peak_probe(PEAK_KINDS[kind], buf.data_ptr(), buf.numel(), ctypes.byref(out),
                                torch.cuda.current_stream().cuda_stream), "xy_peak_probe")
     return float(out.value)
-
-
-def debug_two_atan2(x, y) -> np.ndarray:
-    """The device's 2 atan2(y, x) at the given points (accuracy tests)."""
-    torch = _require_cuda()
-    xd = torch.as_tensor(np.ascontiguousarray(x, dtype=np.float32), device="cuda")
-    yd = torch.as_tensor(np.ascontiguousarray(y, dtype=np.float32), device="cuda")
-    out = torch.empty_like(xd)
-    _check(lib().xy_debug_two_atan2(xd.numel(), xd.data_ptr(), yd.data_ptr(), out.data_ptr(),
-                                    torch.cuda.current_stream().cuda_stream), "xy_debug_two_atan2")
-    return out.cpu().numpy()
 
 
 # ---------------------------------------------------------------------------

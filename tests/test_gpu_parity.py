@@ -18,9 +18,12 @@ pytestmark = pytest.mark.gpu
 SEED = 0x5EED2012
 TOL_RAD = 1e-5
 MARGIN = 1e-6
-# Error of one term of the fused lattice sums: a bond term cos(a - b) =
-# ca cb + sa sb from fast sincos values (<= 6e-7 each) is off by <= 2e-6, a
-# site term by <= 1e-6; FP64 accumulation adds nothing at these sizes.
+# Error of one term of the fused lattice sums against the oracle's unit
+# vectors at the read-back angles: a stored FP32 spin differs from that unit
+# vector by <= 8e-7 (its length error <= 5e-7 after a fast-sincos proposal or
+# a renormalised reflection, plus the angle read-back rounding <= 3e-7), so
+# a bond term ca cb + sa sb is off by <= 2e-6 and a site term by <= 1e-6;
+# FP64 accumulation adds nothing at these sizes.
 BOND_TOL, SITE_TOL = 2e-6, 1e-6
 
 
@@ -69,34 +72,30 @@ def test_initial_state_matches_oracle():
 
 
 def test_state_roundtrip_and_layout():
-    """set_state/get_state round-trip a random natural-layout state exactly."""
+    """set_state/get_state round-trip a random natural-layout state within
+    the angle -> (cos, sin) -> angle rounding (sincosf and atan2f <= 2 ulp,
+    the wrap into [0, 2 pi) <= 2.4e-7: below 1e-6 rad), and get_packed /
+    set_packed round-trip the device state exactly."""
     from paper_1211_0780_b300.inputs import random_angles
     s = sim(24, 2, [0.4, 0.5])
     st = [random_angles((24, 24, 24), 3).astype(np.float32), random_angles((24, 24, 24), 4).astype(np.float32)]
     s.set_state(st, perm=[1, 0], counters=[5, 6, 7, 8])
     a, p, c = s.get_state()
-    assert all(np.array_equal(x, y) for x, y in zip(a, st))
+    assert all(np.max(circ_dist(x, y)) < 1e-6 for x, y in zip(a, st))
+    assert all(x.min() >= 0 and x.max() < 2 * np.pi for x in a)
     assert list(p) == [1, 0] and list(c) == [5, 6, 7, 8]
-
-
-def test_two_atan2_error_bound():
-    """The reflection angle 2 atan2(y, x) of the over-relaxation kernel is
-    within 8e-7 rad of the FP64 value over the plane (all octants, signed
-    zeros, magnitudes 1e-3..6, the range of the local field): twice the
-    polynomial (1.5e-7) and division (1.2e-7) errors plus the final FP32
-    rounding near 2 pi (2.4e-7)."""
-    from paper_1211_0780_b300 import xy
-    rng = np.random.default_rng(5)
-    r = 10 ** rng.uniform(-3, np.log10(6.0), 200000)
-    a = rng.uniform(-np.pi, np.pi, 200000)
-    x = np.concatenate([r * np.cos(a), [1, -1, 0, 0, 2, -2, 3, -3]]).astype(np.float32)
-    y = np.concatenate([r * np.sin(a), [0, 0, 1, -1, 2, 2, -3, -3]]).astype(np.float32)
-    y[-8] = -0.0
-    g = xy.debug_two_atan2(x, y).astype(np.float64)
-    ref = 2 * np.arctan2(y.astype(np.float64), x.astype(np.float64))
-    d = np.abs(np.mod(g - ref + np.pi, 2 * np.pi) - np.pi)
-    assert d.max() < 8e-7, d.max()
-    assert np.all(g >= 0) and np.all(g <= 2 * np.pi + 1e-6)
+    packed = s.get_packed()
+    assert packed.size == 2 * 2 * 24 ** 3
+    # cos^2 + sin^2 = 1 at every site of the packed layout
+    half = 24 ** 3 // 2
+    for slot in range(2):
+        for col in range(2):
+            base = (2 * slot + col) * 2 * half
+            cs, sn = packed[base:base + half].astype(np.float64), packed[base + half:base + 2 * half]
+            assert np.max(np.abs(cs ** 2 + sn.astype(np.float64) ** 2 - 1)) < 1e-6
+    s.sweep(1, 1, 2)
+    s.set_packed(packed)
+    assert np.array_equal(s.get_packed(), packed)
 
 
 # ---------------------------------------------------------------- half-sweeps
@@ -113,10 +112,11 @@ def test_metropolis_half_parity(L, tile):
     s = sim(L, 1, [beta])
     if tile:
         s.set_tile(0, *tile)
-    th32 = s.get_state()[0][0].copy()
+    th32 = s.get_state()[0][0].copy()  # angles of the stored vectors
+    pk = s.get_packed()
     excluded = 0
     for colour, mpass in ((0, 3), (1, 3), (0, 11)):
-        s.set_state([th32])
+        s.set_packed(pk)  # the same stored state for every pass
         acc0 = s.accepts()[0][0]
         s.metropolis_half(colour, mpass)
         g = s.get_state()[0][0]
@@ -130,14 +130,18 @@ def test_metropolis_half_parity(L, tile):
         gacc = int(s.accepts()[0][0] - acc0)
         assert abs(gacc - n_acc) <= int(close.sum())
         th32 = g.copy()
+        pk = s.get_packed()
     assert excluded <= max(2, 1e-4 * 3 * L ** 3 / 2)
 
 
-# Worst-case deviation of one over-relaxation update from the FP64 value on
-# the same FP32 inputs: each neighbour's fast sincos (evaluated at theta - pi)
-# is off by <= 6e-7 per component, the six-term FP32 field sum adds <= 1.2e-6,
-# so |dh| <= 6.8e-6 and the reflected angle 2 atan2(h) - theta moves by
-# <= 2 |dh| / |h| plus the rounding of atan2 and of the wrap (<= 2e-6).
+# Worst-case deviation of one over-relaxation update from the oracle's FP64
+# reflection of the read-back angles: each stored neighbour vector differs
+# from the oracle's unit vector by <= 8e-7, the six-term FP32 field sum adds
+# <= 1.2e-6 per component, so |dh| <= 6e-6 and the field direction moves by
+# <= |dh| / |h|, the reflected angle by twice that; the own spin's direction
+# (<= 3e-7), the approximate reciprocal and the FP32 products of
+# S' = k h - S (<= 1e-6 together) and the read-back of the result (<= 2.4e-7)
+# add a constant.
 OR_A, OR_B = 1.5e-5, 2e-6
 
 
@@ -152,9 +156,10 @@ def test_overrelax_half_parity(L, tile):
     if tile:
         s.set_tile(0, *tile)
     s.sweep(1, 1, 3)
-    th32 = s.get_state()[0][0].copy()
+    th32 = s.get_state()[0][0].copy()  # angles of the stored vectors
+    pk = s.get_packed()
     for colour in (0, 1):
-        s.set_state([th32])
+        s.set_packed(pk)
         s.overrelax_half(colour)
         g = s.get_state()[0][0]
         ref = f64(th32)
@@ -166,6 +171,7 @@ def test_overrelax_half_parity(L, tile):
         assert np.mean(d[m] > TOL_RAD) < 5e-3
         assert np.all(d[~m] == 0)
         th32 = g.copy()
+        pk = s.get_packed()
 
 
 def test_overrelax_involution_and_energy():
@@ -384,9 +390,11 @@ def test_barrier_timeout_reports_status_without_hanging():
 
 
 def test_checkpoint_resume_is_bit_exact():
-    """get_state / set_state (natural layout) and get_packed / set_packed
-    (device layout) resume a run bit for bit: every draw is a pure function
-    of (seed, counters, slot, site)."""
+    """get_packed / set_packed (device layout) with the permutation and
+    counters of get_state / set_state resume a run bit for bit, in another
+    execution mode too: every draw is a pure function of (seed, counters,
+    slot, site).  The natural-layout angles restore the state up to the
+    angle <-> vector rounding."""
     from paper_1211_0780_b300 import xy
     Ls, Rs, betas = [16, 24], [3, 2], [0.40, 0.45, 0.50, 0.44, 0.46]
     a = sim(Ls, Rs, betas, series_capacity=32)
@@ -395,17 +403,19 @@ def test_checkpoint_resume_is_bit_exact():
     packed = a.get_packed()
     a.read_series()
     a.sweep(1, 2, 6, measure_every=2, pt_swap_every=1)
-    want = (a.get_state(), a.read_series())
-    for use_packed in (False, True):
-        b = sim(Ls, Rs, betas, series_capacity=32)
-        if use_packed:
-            b.set_packed(packed)
-            b.set_state(None, perm, ctr)
-        else:
-            b.set_state(angles, perm, ctr)
-        b.set_exec(xy.EXEC_GRAPH)
-        b.sweep(1, 2, 6, measure_every=2, pt_swap_every=1)
-        got = (b.get_state(), b.read_series())
-        assert all(np.array_equal(x, y) for x, y in zip(got[0][0], want[0][0]))
-        assert np.array_equal(got[0][1], want[0][1]) and np.array_equal(got[0][2], want[0][2])
-        assert np.array_equal(got[1], want[1])
+    want = (a.get_state(), a.read_series(), a.get_packed())
+    b = sim(Ls, Rs, betas, series_capacity=32)
+    b.set_packed(packed)
+    b.set_state(None, perm, ctr)
+    b.set_exec(xy.EXEC_GRAPH)
+    b.sweep(1, 2, 6, measure_every=2, pt_swap_every=1)
+    got = (b.get_state(), b.read_series(), b.get_packed())
+    assert np.array_equal(got[2], want[2])
+    assert all(np.array_equal(x, y) for x, y in zip(got[0][0], want[0][0]))
+    assert np.array_equal(got[0][1], want[0][1]) and np.array_equal(got[0][2], want[0][2])
+    assert np.array_equal(got[1], want[1])
+    c = sim(Ls, Rs, betas, series_capacity=32)
+    c.set_state(angles, perm, ctr)
+    back = c.get_state()
+    assert all(np.max(circ_dist(x, y)) < 1e-6 for x, y in zip(back[0], angles))
+    assert np.array_equal(back[1], perm) and np.array_equal(back[2], ctr)
