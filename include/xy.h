@@ -212,7 +212,11 @@ int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
  * in z, loading each other-colour spin about once.  kind 1 (block): a
  * thread block of (L/8) x ty x tz threads covers ty rows x tz planes at
  * once after one cooperative staging of the tile's other-colour rows and
- * face halos.  xy_set_tile checks 1 <= ty, tz <= L, the block size against
+ * face halos.  kind 2 (stream): the march's thread layout, with every plane
+ * the tile reads (the other colour's rows with their y halo, the own
+ * colour's rows) copied ahead into a ring of shared-memory stages by bulk
+ * asynchronous copies (TMA); not run by XY_EXEC_PERSISTENT, whose blocks
+ * write planes other blocks read within one launch.  xy_set_tile checks 1 <= ty, tz <= L, the block size against
  * the kernels' limit (512 threads at their register use on sm_103a), tz <=
  * 64 for kind 1, and that the tile count fits the partial-sum area
  * (ceil(L/ty) ceil(L/tz) <= L^2/4).  Spins do not depend on the tile (the
@@ -237,6 +241,15 @@ int xy_device_status(xy_ctx *ctx, int *status_out);
  * through the status word without hanging.  The context stays usable (the
  * timeout is reported, not made sticky).  No GPU fault is involved. */
 int xy_debug_barrier_timeout(xy_ctx *ctx, int budget_us, int *status_out);
+
+/* Test hook for the bounded plane waits of stream tiles (kind 2): lattice 0
+ * must use a stream tile.  Runs one over-relaxation half-sweep of colour 0
+ * of lattice 0 in which no block copies its third plane, so every block's
+ * wait for it runs out after `budget_us` microseconds; the blocks set the
+ * status word to XY_ERR_TIMEOUT, update nothing, let their other copies
+ * land and return.  The state is unchanged and the context stays usable
+ * (the timeout is reported, not made sticky).  No GPU fault is involved. */
+int xy_debug_stream_timeout(xy_ctx *ctx, int budget_us, int *status_out);
 
 /* Throughput probe of one hardware unit, for roofline denominators:
  * kind 0 = special-function unit sin+cos (2 ops per pair), 1 = ex2,

@@ -30,7 +30,7 @@ int conv_blocks(long long n) { return static_cast<int>(std::min<long long>((n + 
 
 struct LatHost {
   int L, R, slot0;
-  int kind;  // kTileMarch or kTileBlock
+  int kind;  // kTileMarch, kTileBlock or kTileStream
   int ty, tz;
   size_t spin_off;  // floats from the spin base (2N per slot)
   int part0;         // first partial slot
@@ -164,6 +164,9 @@ struct xy_ctx {
     p.partials = at<double>(lay.partials);
     p.acc_met = at<unsigned long long>(lay.acc_met);
     p.measure = measure;
+    p.poison = 0;
+    p.status = at<int>(lay.status);
+    p.wait_ns = 1000000000ll;  // a copied plane lands in microseconds
     return p;
   }
 };
@@ -192,6 +195,21 @@ int fail_cuda(xy_ctx* c, cudaError_t e, const char* what) {
     if ((c)->sticky != XY_OK) return XY_ERR_STATE;           \
     XY_TRY((c), cudaSetDevice((c)->device));                 \
   } while (0)
+
+// Synchronises the context's stream and reads the device status word: a
+// bounded wait that ran out inside a kernel (a stream tile waiting for a
+// copied plane, the persistent grid barrier) fails the context with
+// XY_ERR_TIMEOUT.
+int sync_checked(xy_ctx* c) {
+  int st = 0;
+  XY_TRY(c, cudaMemcpyAsync(&st, c->ws + c->lay.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  if (st != 0) {
+    c->sticky = XY_ERR_TIMEOUT;
+    return XY_ERR_TIMEOUT;
+  }
+  return XY_OK;
+}
 
 // Default tile: the block kind with up to 8 x 8 rows and at most 256 threads.
 void default_tile(LatHost& h) {
@@ -242,7 +260,7 @@ template <int MODE, int KIND>
 cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st, int colour,
                              const PassParams& pp) {
   const dim3 grid(h.nyt() * h.nzt(), h.R);
-  const dim3 block = KIND == kTileBlock ? dim3(h.L / 8, h.ty, h.tz) : dim3(h.L / 8, h.ty);
+  const dim3 block = KIND == kTileBlock ? dim3(h.L / 8, h.ty, h.tz) : dim3(h.L / 8, h.ty);  // march, stream
   const int smem = h.smem();
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
   if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);
@@ -254,8 +272,9 @@ template <int MODE>
 int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams& pp) {
   const LatHost& h = c->lat[i];
   const Lattice d = c->dev_lat(i);
-  const cudaError_t e = h.kind == kTileBlock ? launch_half_kind<MODE, kTileBlock>(h, d, st, colour, pp)
-                                             : launch_half_kind<MODE, kTileMarch>(h, d, st, colour, pp);
+  const cudaError_t e = h.kind == kTileBlock    ? launch_half_kind<MODE, kTileBlock>(h, d, st, colour, pp)
+                       : h.kind == kTileStream ? launch_half_kind<MODE, kTileStream>(h, d, st, colour, pp)
+                                               : launch_half_kind<MODE, kTileMarch>(h, d, st, colour, pp);
   XY_TRY(c, e);
   return XY_OK;
 }
@@ -500,7 +519,7 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
       if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "lattice streams"));
     }
   }
-  const void* half_kernels[10] = {
+  const void* half_kernels[15] = {
       reinterpret_cast<const void*>(k_half<kMetropolis, false, kTileMarch>),
       reinterpret_cast<const void*>(k_half<kMetropolis, true, kTileMarch>),
       reinterpret_cast<const void*>(k_half<kOverrelax, false, kTileMarch>),
@@ -510,7 +529,12 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
       reinterpret_cast<const void*>(k_half<kMetropolis, true, kTileBlock>),
       reinterpret_cast<const void*>(k_half<kOverrelax, false, kTileBlock>),
       reinterpret_cast<const void*>(k_half<kOverrelax, true, kTileBlock>),
-      reinterpret_cast<const void*>(k_half<kMeasureOnly, true, kTileBlock>)};
+      reinterpret_cast<const void*>(k_half<kMeasureOnly, true, kTileBlock>),
+      reinterpret_cast<const void*>(k_half<kMetropolis, false, kTileStream>),
+      reinterpret_cast<const void*>(k_half<kMetropolis, true, kTileStream>),
+      reinterpret_cast<const void*>(k_half<kOverrelax, false, kTileStream>),
+      reinterpret_cast<const void*>(k_half<kOverrelax, true, kTileStream>),
+      reinterpret_cast<const void*>(k_half<kMeasureOnly, true, kTileStream>)};
   for (const void* fn : half_kernels) {
     // Tiles need up to ~64 KB of shared memory on the largest lattices.
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -665,7 +689,7 @@ int xy_measure(xy_ctx* c, xy_record* out) {
   XY_TRY(c, cudaMemcpyAsync(E.data(), c->ws + c->lay.E_slot, S * 8, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemcpyAsync(b64.data(), c->ws + c->lay.beta_slot64, S * 8, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemcpyAsync(bidx.data(), c->ws + c->lay.bidx_slot, S * 4, cudaMemcpyDeviceToHost, c->stream));
-  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  if ((rc = sync_checked(c)) != XY_OK) return rc;
   for (int g = 0; g < S; ++g) {
     xy_record& r = out[g];
     const double* v = &sums[static_cast<size_t>(g) * kNumSums];
@@ -695,7 +719,7 @@ int xy_pt_swap(xy_ctx* c, int parity, int* n_accepted_out) {
   c->h_ctr[kCtrSwap] += 1;
   int n = 0;
   XY_TRY(c, cudaMemcpyAsync(&n, c->ws + c->lay.nswapped, 4, cudaMemcpyDeviceToHost, c->stream));
-  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  if ((rc = sync_checked(c)) != XY_OK) return rc;
   if (n_accepted_out) *n_accepted_out = n;
   return XY_OK;
 }
@@ -717,7 +741,8 @@ int xy_read_series(xy_ctx* c, xy_record* buf, int64_t cap, int64_t* n_out) {
     XY_TRY(c, cudaMemcpyAsync(buf, c->ws + c->lay.series, n * sizeof(xy_record), cudaMemcpyDeviceToHost, c->stream));
   }
   XY_TRY(c, cudaMemsetAsync(c->ws + c->lay.ctr + kCtrSeries * 8, 0, 8, c->stream));
-  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  const int rc = sync_checked(c);
+  if (rc != XY_OK) return rc;
   c->h_ctr[kCtrSeries] = 0;
   *n_out = n;
   return XY_OK;
@@ -751,8 +776,7 @@ int xy_get_state(xy_ctx* c, float* host_angles, int32_t* perm, uint64_t* counter
   }
   if (perm) XY_TRY(c, cudaMemcpyAsync(perm, c->ws + c->lay.perm, c->n_slots * 4, cudaMemcpyDeviceToHost, c->stream));
   if (counters) XY_TRY(c, cudaMemcpyAsync(counters, c->ctr(), 4 * 8, cudaMemcpyDeviceToHost, c->stream));
-  XY_TRY(c, cudaStreamSynchronize(c->stream));
-  return XY_OK;
+  return sync_checked(c);
 }
 
 int xy_set_state(xy_ctx* c, const float* host_angles, const int32_t* perm, const uint64_t* counters) {
@@ -828,8 +852,7 @@ int xy_get_packed(xy_ctx* c, float* host_packed) {
   size_t n = 0;
   for (const LatHost& h : c->lat) n += 2 * static_cast<size_t>(h.N()) * h.R;
   XY_TRY(c, cudaMemcpyAsync(host_packed, c->spins(), n * 4, cudaMemcpyDeviceToHost, c->stream));
-  XY_TRY(c, cudaStreamSynchronize(c->stream));
-  return XY_OK;
+  return sync_checked(c);
 }
 
 int xy_set_packed(xy_ctx* c, const float* host_packed) {
@@ -870,7 +893,7 @@ int xy_debug_draws(xy_ctx* c, int slot, int colour, int tag, uint64_t count, uin
 int xy_set_tile(xy_ctx* c, int lattice, int kind, int ty, int tz) {
   XY_ENTER(c);
   if (lattice < 0 || lattice >= c->n_lat) return XY_ERR_ARG;
-  if (kind != kTileMarch && kind != kTileBlock) return XY_ERR_ARG;
+  if (kind != kTileMarch && kind != kTileBlock && kind != kTileStream) return XY_ERR_ARG;
   LatHost h = c->lat[lattice];
   h.kind = kind;
   h.ty = ty;
@@ -916,6 +939,9 @@ int build_plan(xy_ctx* c) {
   const int kind = c->lat[0].kind;
   for (const LatHost& h : c->lat) {
     if (h.kind != kind) return XY_ERR_ARG;  // one tile kind per persistent launch
+    // stream tiles copy planes with TMA, which does not see what other blocks
+    // of the same launch wrote
+    if (h.kind == kTileStream) return XY_ERR_ARG;
     B = std::max(B, h.threads());
     smem = std::max(smem, h.smem());
   }
@@ -1016,17 +1042,6 @@ int issue_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, const 
   return XY_OK;
 }
 
-int check_status(xy_ctx* c) {
-  int st = 0;
-  XY_TRY(c, cudaMemcpyAsync(&st, c->ws + c->lay.status, 4, cudaMemcpyDeviceToHost, c->stream));
-  XY_TRY(c, cudaStreamSynchronize(c->stream));
-  if (st != 0) {
-    c->sticky = XY_ERR_TIMEOUT;
-    return XY_ERR_TIMEOUT;
-  }
-  return XY_OK;
-}
-
 int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
   int rc = build_plan(c);
   if (rc != XY_OK) return rc;
@@ -1078,7 +1093,7 @@ int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
     if (rc != XY_OK) return rc;
   }
   mirror_advance(c, bc);
-  return check_status(c);
+  return sync_checked(c);
 }
 
 }  // namespace
@@ -1099,6 +1114,24 @@ int xy_debug_barrier_timeout(xy_ctx* c, int budget_us, int* status_out) {
   int st = 0;
   XY_TRY(c, cudaMemcpyAsync(&st, a.status, 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  if (status_out) *status_out = st;
+  return st == 0 ? XY_OK : XY_ERR_TIMEOUT;
+}
+
+int xy_debug_stream_timeout(xy_ctx* c, int budget_us, int* status_out) {
+  XY_ENTER(c);
+  if (budget_us <= 0 || budget_us > 2000000) return XY_ERR_ARG;
+  if (c->lat[0].kind != kTileStream) return XY_ERR_ARG;
+  PassParams pp = c->pass_params(false, 0, 0);
+  pp.poison = 1;
+  pp.wait_ns = static_cast<long long>(budget_us) * 1000;
+  XY_TRY(c, cudaMemsetAsync(pp.status, 0, 4, c->stream));
+  const int rc = launch_half<kOverrelax>(c, c->stream, 0, 0, pp);
+  if (rc != XY_OK) return rc;
+  int st = 0;
+  XY_TRY(c, cudaMemcpyAsync(&st, pp.status, 4, cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaMemsetAsync(pp.status, 0, 4, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
   if (status_out) *status_out = st;
   return st == 0 ? XY_OK : XY_ERR_TIMEOUT;
@@ -1129,7 +1162,7 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
     LatHost best_h = h;
     const int zs[] = {1, 2, 4, 8, 16, 32};
     const bool persistent = exec == XY_EXEC_PERSISTENT;
-    for (int kind = persistent ? kTileBlock : 0; kind < 2 && rc == XY_OK; ++kind) {
+    for (int kind = persistent ? kTileBlock : 0; kind < (persistent ? 2 : 3) && rc == XY_OK; ++kind) {
       for (int ty = 1; ty <= h.L && rc == XY_OK; ++ty) {
         if (h.L % ty != 0) continue;
         for (int tz : zs) {
@@ -1138,7 +1171,7 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
           cand.kind = kind;
           cand.ty = ty;
           cand.tz = tz;
-          if (kind == kTileMarch && tz < 2) continue;
+          if (kind != kTileBlock && tz < 2) continue;  // a march covers two planes or more
           if (cand.threads() > c->max_block || cand.threads() < 32) continue;
           if (persistent && cand.threads() > kPersistentBlockThreads) continue;
           if (cand.nyt() * cand.nzt() > h.part_cap || cand.smem() > 200 * 1024) continue;

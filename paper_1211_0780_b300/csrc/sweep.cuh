@@ -37,6 +37,7 @@
 #pragma once
 #include <cstdint>
 
+#include "../../include/xy.h"
 #include "philox.cuh"
 
 namespace xy {
@@ -55,7 +56,16 @@ enum Mode : int { kMetropolis = 0, kOverrelax = 1, kMeasureOnly = 2 };
 // in sequence).  kTileBlock: a block of (L/8) x ty x tz threads updates its
 // whole tile at once after one cooperative staging of the tile's
 // other-colour rows and face halos (more loads, no sequence).
-enum TileKind : int { kTileMarch = 0, kTileBlock = 1 };
+// kTileStream: the march of kTileMarch, but every plane the tile needs
+// (the other colour's rows with their y halo, the own colour's rows) is
+// brought into a ring of shared-memory stages by bulk asynchronous copies
+// (TMA) that run ahead of the computation; threads only read shared memory
+// and store their results.
+enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2 };
+
+// Stages of the kTileStream ring: planes z-1, z, z+1 in use, the rest in
+// flight.
+constexpr int kStreamStages = 5;
 
 // Device-resident counters (graph replays read them instead of baking
 // values into kernel arguments).
@@ -89,6 +99,9 @@ struct PassParams {
   double* partials;             // [tiles][kNumSums], written when measuring
   unsigned long long* acc_met;  // accepted proposals per global slot
   int measure;                  // fuse the lattice sums (white passes only)
+  int poison;                   // test hook (kTileStream): plane 2 is never copied
+  int* status;                  // set to XY_ERR_TIMEOUT when a bounded wait runs out
+  long long wait_ns;            // bound of one wait for a copied plane
 };
 
 // Shared-memory bytes of one tile pass: three plane buffers of ty+2 rows of
@@ -99,8 +112,16 @@ __host__ __device__ inline int tile_smem_bytes(int L, int ty) {
 }
 // kTileBlock: (ty+2) x (tz+2) rows of L/2 (cos, sin) pairs.
 __host__ __device__ inline int block_tile_floats(int L, int ty, int tz) { return (ty + 2) * (tz + 2) * L; }
+// kTileStream: per stage, the cosines of the other colour's ty+2 rows, their
+// sines, then the cosines and the sines of the own colour's ty rows (L/2
+// floats per row); after the stages, one 8-byte mbarrier per stage.
+__host__ __device__ inline int stream_stage_floats(int L, int ty) { return (2 * ty + 2) * L; }
+__host__ __device__ inline int stream_tile_floats(int L, int ty) {
+  return kStreamStages * stream_stage_floats(L, ty) + 2 * kStreamStages;
+}
 __host__ __device__ inline int tile_floats(int kind, int L, int ty, int tz) {
-  return kind == kTileBlock ? block_tile_floats(L, ty, tz) : tile_plane_floats(L, ty);
+  return kind == kTileBlock ? block_tile_floats(L, ty, tz)
+                            : (kind == kTileStream ? stream_tile_floats(L, ty) : tile_plane_floats(L, ty));
 }
 __host__ __device__ inline int tile_bytes(int kind, int L, int ty, int tz) {
   return tile_floats(kind, L, ty, tz) * 4 + kReduceBytes;
@@ -122,25 +143,8 @@ __device__ __forceinline__ void spin(float th, float& c, float& s) {
   s = -sn;
 }
 
-// The reflection of Eq. (2) at the field h = sum of the six neighbour
-// vectors: S' = 2 (S.h / h.h) h - S, followed by one Newton step of the norm
-// (S' *= 3/2 - |S'|^2 / 2).  h = 0 leaves S (Sec. II reading: no field, no
-// reflection); so does a field whose squared length underflows.
-__device__ __forceinline__ void reflect(float hx, float hy, float c, float s, float& c1, float& s1) {
-  const float n2 = fmaf(hy, hy, hx * hx);
-  float rn;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(rn) : "f"(n2));
-  const float k = 2.f * fmaf(s, hy, c * hx) * rn;
-  const float a = fmaf(k, hx, -c), b = fmaf(k, hy, -s);
-  const float f = fmaf(-0.5f, fmaf(b, b, a * a), 1.5f);
-  const bool keep = !(n2 > 0.f);
-  c1 = keep ? c : a * f;
-  s1 = keep ? s : b * f;
-}
-
 struct Spins4 {
-  float c[4];
-  float s[4];
+  float4 c, s;
 };
 
 // Spin loads and stores go through L2 (.cg): the persistent kernel reads
@@ -154,20 +158,19 @@ __device__ __forceinline__ void st4(float* p, float4 v) {
 
 // The 4 spins of one thread's row segment: cos at p, sin at p + half.
 __device__ __forceinline__ Spins4 ld_spins(const float* p, uint32_t half) {
-  const float4 c = ld4(p), s = ld4(p + half);
   Spins4 v;
-  v.c[0] = c.x; v.c[1] = c.y; v.c[2] = c.z; v.c[3] = c.w;
-  v.s[0] = s.x; v.s[1] = s.y; v.s[2] = s.z; v.s[3] = s.w;
+  v.c = ld4(p);
+  v.s = ld4(p + half);
   return v;
 }
-__device__ __forceinline__ void st_spins(float* p, uint32_t half, const float c[4], const float s[4]) {
-  st4(p, make_float4(c[0], c[1], c[2], c[3]));
-  st4(p + half, make_float4(s[0], s[1], s[2], s[3]));
+__device__ __forceinline__ void st_spins(float* p, uint32_t half, const float4& c, const float4& s) {
+  st4(p, c);
+  st4(p + half, s);
 }
 
 __device__ __forceinline__ void put_row(float* row, int H, int tx, const Spins4& v) {
-  reinterpret_cast<float4*>(row)[tx] = make_float4(v.c[0], v.c[1], v.c[2], v.c[3]);
-  reinterpret_cast<float4*>(row + H)[tx] = make_float4(v.s[0], v.s[1], v.s[2], v.s[3]);
+  reinterpret_cast<float4*>(row)[tx] = v.c;
+  reinterpret_cast<float4*>(row + H)[tx] = v.s;
 }
 
 __device__ __forceinline__ float comp(const float4& v, int e) {
@@ -210,6 +213,121 @@ struct SumAcc<true> {
     for (int j = 0; j < kNumSums; ++j) out[j] = acc[j];
   }
 };
+
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+__device__ __forceinline__ float2 neg2(float2 v) { return make_float2(-v.x, -v.y); }
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+// The reflection of Eq. (2) for two sites at once, in the paired FP32
+// instructions of sm_100 and later (each lane rounds exactly as the scalar
+// instruction would): S' = 2 (S.h / h.h) h - S, then one Newton step of the
+// norm, S' *= 3/2 - |S'|^2 / 2.  h = 0 leaves S (Sec. II reading: no field,
+// no reflection); so does a field whose squared length underflows.
+__device__ __forceinline__ void reflect2(float2 hx, float2 hy, float2 c, float2 s, float2& c1, float2& s1) {
+  const float2 n2 = __ffma2_rn(hy, hy, __fmul2_rn(hx, hx));
+  const float2 rn = make_float2(rcp_approx(n2.x), rcp_approx(n2.y));
+  const float2 d = __ffma2_rn(s, hy, __fmul2_rn(c, hx));
+  const float2 k = __fmul2_rn(__fadd2_rn(d, d), rn);
+  const float2 a = __ffma2_rn(k, hx, neg2(c)), b = __ffma2_rn(k, hy, neg2(s));
+  const float2 f = __ffma2_rn(make_float2(-0.5f, -0.5f), __ffma2_rn(b, b, __fmul2_rn(a, a)), make_float2(1.5f, 1.5f));
+  const float2 ca = __fmul2_rn(a, f), sb = __fmul2_rn(b, f);
+  c1 = make_float2(n2.x > 0.f ? ca.x : c.x, n2.y > 0.f ? ca.y : c.y);
+  s1 = make_float2(n2.x > 0.f ? sb.x : s.x, n2.y > 0.f ? sb.y : s.y);
+}
+
+// The update of one thread's 4 same-colour sites (one float4 per component
+// of a row, packed k = 4t .. 4t+3), shared by every tile kind so that all of
+// them produce bit-identical spins.  z: the other colour's float4 of the same
+// row (cos, sin), h: its x-halo element, s: the row's parity (x = 2k + s), so
+// the -x and +x neighbours of site e are X[e] and X[e+1] with X = (z0, z1,
+// z2, z3, h) if s = 1 and (h, z0, z1, z2, z3) if s = 0; ym, yp, zm, zp: the
+// other colour's float4s of rows y-1, y+1 and planes z-1, z+1 at the same k;
+// o: the own spins.  w0, w1: the Philox words of sites (0, 1) and (2, 3)
+// (Metropolis).  Returns the new spins; accumulates the accepted proposals
+// and, when measuring, this plane's lattice-sum terms (stepv).
+template <int MODE, bool MEAS>
+__device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int s, const Spins4& ym,
+                                        const Spins4& yp, const Spins4& zm, const Spins4& zp, const Spins4& o,
+                                        const uint4& w0, const uint4& w1, float beta, Spins4& n, uint32_t& n_acc,
+                                        float* stepv) {
+  float Xc[5], Xs[5];
+#pragma unroll
+  for (int e = 0; e < 5; ++e) {
+    const float a_c = (e < 4) ? comp(z.c, e < 4 ? e : 0) : hc, a_s = (e < 4) ? comp(z.s, e < 4 ? e : 0) : hs;
+    const float b_c = (e == 0) ? hc : comp(z.c, e == 0 ? 0 : e - 1);
+    const float b_s = (e == 0) ? hs : comp(z.s, e == 0 ? 0 : e - 1);
+    Xc[e] = s ? a_c : b_c;
+    Xs[e] = s ? a_s : b_s;
+  }
+  // field h = (x- + x+) + (y- + y+) + (z- + z+), sites in pairs
+  float2 hx[2], hy[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float2 xx = make_float2(Xc[2 * q] + Xc[2 * q + 1], Xc[2 * q + 1] + Xc[2 * q + 2]);
+    const float2 xy = make_float2(Xs[2 * q] + Xs[2 * q + 1], Xs[2 * q + 1] + Xs[2 * q + 2]);
+    const float2 yyc = q ? __fadd2_rn(hi2(ym.c), hi2(yp.c)) : __fadd2_rn(lo2(ym.c), lo2(yp.c));
+    const float2 yys = q ? __fadd2_rn(hi2(ym.s), hi2(yp.s)) : __fadd2_rn(lo2(ym.s), lo2(yp.s));
+    const float2 zzc = q ? __fadd2_rn(hi2(zm.c), hi2(zp.c)) : __fadd2_rn(lo2(zm.c), lo2(zp.c));
+    const float2 zzs = q ? __fadd2_rn(hi2(zm.s), hi2(zp.s)) : __fadd2_rn(lo2(zm.s), lo2(zp.s));
+    hx[q] = __fadd2_rn(__fadd2_rn(xx, yyc), zzc);
+    hy[q] = __fadd2_rn(__fadd2_rn(xy, yys), zzs);
+  }
+  float2 nc[2], ns[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const float2 co = q ? hi2(o.c) : lo2(o.c), so = q ? hi2(o.s) : lo2(o.s);
+    if (MODE == kMetropolis) {
+      const uint4& w = q ? w1 : w0;
+      // proposal theta' = 2 pi u0 (words 0 and 2), acceptance u1 (words 1 and 3)
+      const float2 tp = make_float2(static_cast<float>(w.x >> 8) * kTwoPiOver2p24,
+                                    static_cast<float>(w.z >> 8) * kTwoPiOver2p24);
+      float2 cp, sp;
+      spin(tp.x, cp.x, sp.x);
+      spin(tp.y, cp.y, sp.y);
+      // -beta dE with dE = -[h_x (cos t' - cos t) + h_y (sin t' - sin t)]
+      const float2 x = __fmul2_rn(make_float2(beta, beta),
+                                  __ffma2_rn(hx[q], __fadd2_rn(cp, neg2(co)), __fmul2_rn(hy[q], __fadd2_rn(sp, neg2(so)))));
+      // u1 < exp(x)  <=>  (w >> 8) < exp(x) 2^24 (exact scaling)
+      const bool a0 = static_cast<float>(w.y >> 8) < __expf(x.x) * 16777216.0f;
+      const bool a1 = static_cast<float>(w.w >> 8) < __expf(x.y) * 16777216.0f;
+      n_acc += (a0 ? 1u : 0u) + (a1 ? 1u : 0u);
+      nc[q] = make_float2(a0 ? cp.x : co.x, a1 ? cp.y : co.y);
+      ns[q] = make_float2(a0 ? sp.x : so.x, a1 ? sp.y : so.y);
+    } else if (MODE == kOverrelax) {
+      reflect2(hx[q], hy[q], co, so, nc[q], ns[q]);
+    } else {
+      nc[q] = co;
+      ns[q] = so;
+    }
+  }
+  n.c = make_float4(nc[0].x, nc[0].y, nc[1].x, nc[1].y);
+  n.s = make_float4(ns[0].x, ns[0].y, ns[1].x, ns[1].y);
+  if (MEAS) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      // Bonds (w, w+mu) and (w-mu, w) of the white site w: every bond has
+      // exactly one white end, so each is counted once.
+      const float c = comp(n.c, e), sn = comp(n.s, e);
+      const float pxc = Xc[e + 1], qxc = Xc[e], pxs = Xs[e + 1], qxs = Xs[e];
+      const float pyc = comp(yp.c, e), qyc = comp(ym.c, e), pys = comp(yp.s, e), qys = comp(ym.s, e);
+      const float pzc = comp(zp.c, e), qzc = comp(zm.c, e), pzs = comp(zp.s, e), qzs = comp(zm.s, e);
+      stepv[0] += c + comp(z.c, e);  // white site + the black site of this column
+      stepv[1] += sn + comp(z.s, e);
+      stepv[2] += c * (pxc + qxc) + sn * (pxs + qxs);
+      stepv[3] += c * (pyc + qyc) + sn * (pys + qys);
+      stepv[4] += c * (pzc + qzc) + sn * (pzs + qzs);
+      stepv[5] += sn * (pxc - qxc) - c * (pxs - qxs);
+      stepv[6] += sn * (pyc - qyc) - c * (pys - qys);
+      stepv[7] += sn * (pzc - qzc) - c * (pzs - qzs);
+    }
+  }
+}
 
 // One tile of one half-sweep of colour `colour` on local slot r.
 // (tx, ty): thread coordinates, tx in [0, L/8); in_block = the thread maps
@@ -303,25 +421,15 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
       const float* rm = row_ptr(b0, ty);
       const float* rp = row_ptr(b0, ty + 2);
       const float* r0 = row_ptr(b0, ty + 1);
-      const float4 ymc = reinterpret_cast<const float4*>(rm)[tx];
-      const float4 yms = reinterpret_cast<const float4*>(rm + H)[tx];
-      const float4 ypc = reinterpret_cast<const float4*>(rp)[tx];
-      const float4 yps = reinterpret_cast<const float4*>(rp + H)[tx];
+      Spins4 ysm, ysp;
+      ysm.c = reinterpret_cast<const float4*>(rm)[tx];
+      ysm.s = reinterpret_cast<const float4*>(rm + H)[tx];
+      ysp.c = reinterpret_cast<const float4*>(rp)[tx];
+      ysp.s = reinterpret_cast<const float4*>(rp + H)[tx];
       const int s = (y + z + colour) & 1;
       const int kh = s ? kh1 : kh0;
       const float hc = r0[kh], hs = r0[H + kh];
-      // X[e] = the -x neighbour of site e, X[e+1] its +x neighbour.
-      float Xc[5], Xs[5];
-#pragma unroll
-      for (int e = 0; e < 5; ++e) {
-        const float a_c = (e < 4) ? zc.c[e] : hc, a_s = (e < 4) ? zc.s[e] : hs;
-        const float b_c = (e == 0) ? hc : zc.c[e - 1 < 0 ? 0 : e - 1];
-        const float b_s = (e == 0) ? hs : zc.s[e - 1 < 0 ? 0 : e - 1];
-        Xc[e] = s ? a_c : b_c;
-        Xs[e] = s ? a_s : b_s;
-      }
       const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
-      float nc[4], ns[4];
       uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
       if (MODE == kMetropolis) {
         const uint32_t q0 = offz >> 1;
@@ -331,50 +439,10 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
       float stepv[kNumSums];
 #pragma unroll
       for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float hx = (Xc[e] + Xc[e + 1]) + (comp(ymc, e) + comp(ypc, e)) + (zm.c[e] + zn.c[e]);
-        const float hy = (Xs[e] + Xs[e + 1]) + (comp(yms, e) + comp(yps, e)) + (zm.s[e] + zn.s[e]);
-        const float co = t_own.c[e], so = t_own.s[e];
-        if (MODE == kMetropolis) {
-          const uint4& w = (e < 2) ? w0 : w1;
-          const uint32_t wprop = (e & 1) ? w.z : w.x;
-          const uint32_t wacc = (e & 1) ? w.w : w.y;
-          const float tp = static_cast<float>(wprop >> 8) * kTwoPiOver2p24;  // = u0 * 2 pi
-          float cp, sp;
-          spin(tp, cp, sp);
-          // -beta dE with dE = -[h_x (cos t' - cos t) + h_y (sin t' - sin t)]
-          const float x = beta * (hx * (cp - co) + hy * (sp - so));
-          // u1 < exp(x)  <=>  (w >> 8) < exp(x) 2^24 (exact scaling)
-          const bool accept = static_cast<float>(wacc >> 8) < __expf(x) * 16777216.0f;
-          n_acc += accept ? 1u : 0u;
-          nc[e] = accept ? cp : co;
-          ns[e] = accept ? sp : so;
-        } else if (MODE == kOverrelax) {
-          reflect(hx, hy, co, so, nc[e], ns[e]);  // reflection about the field
-        } else {
-          nc[e] = co;
-          ns[e] = so;
-        }
-        if (MEAS) {
-          // Bonds (w, w+mu) and (w-mu, w) of the white site w: every bond has
-          // exactly one white end, so each is counted once.
-          const float c = nc[e], sn = ns[e];
-          const float pxc = Xc[e + 1], qxc = Xc[e], pxs = Xs[e + 1], qxs = Xs[e];
-          const float pyc = comp(ypc, e), qyc = comp(ymc, e), pys = comp(yps, e), qys = comp(yms, e);
-          const float pzc = zn.c[e], qzc = zm.c[e], pzs = zn.s[e], qzs = zm.s[e];
-          stepv[0] += c + zc.c[e];  // white site + the black site of this column
-          stepv[1] += sn + zc.s[e];
-          stepv[2] += c * (pxc + qxc) + sn * (pxs + qxs);
-          stepv[3] += c * (pyc + qyc) + sn * (pys + qys);
-          stepv[4] += c * (pzc + qzc) + sn * (pzs + qzs);
-          stepv[5] += sn * (pxc - qxc) - c * (pxs - qxs);
-          stepv[6] += sn * (pyc - qyc) - c * (pys - qys);
-          stepv[7] += sn * (pzc - qzc) - c * (pzs - qzs);
-        }
-      }
+      Spins4 nw;
+      update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
       if (MEAS) sums.add_plane(stepv);
-      if (MODE != kMeasureOnly) st_spins(own + offz, half, nc, ns);
+      if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
     }
     __syncthreads();
   };
@@ -385,6 +453,228 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
     step(IC<1>{}, pb, pc, pa, i + 1);
     if (i + 2 >= TZa) break;
     step(IC<2>{}, pc, pa, pb, i + 2);
+  }
+  if (MEAS) sums.export_to(acc_out);
+}
+
+__device__ __forceinline__ long long global_ns() {
+  long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+// Arrives once on the barrier and adds `bytes` to the transfer count its
+// current phase waits for.
+__device__ __forceinline__ void mbar_arrive_expect(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Waits for the phase with the given parity to complete, at most `budget_ns`
+// of %globaltimer time; false if the budget ran out.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long long budget_ns) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = global_ns();
+  while (!mbar_test(bar, parity))
+    if (global_ns() - t0 > budget_ns) return false;
+  return true;
+}
+
+// Bulk asynchronous copy (TMA) of `bytes` (a multiple of 16; both addresses
+// 16-byte aligned) from global to shared memory, completing on `bar`.
+__device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const float* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+// One tile of one half-sweep, kTileStream: thread (tx, ty) owns the float4
+// pair (cos, sin) of packed k = 4 tx .. 4 tx + 3 of row y0+ty, as in the
+// march, but reads every operand from a ring of kStreamStages shared-memory
+// stages, stage j mod kStreamStages holding plane z0-1+j (the other colour's
+// rows y0-1 .. y0+TYa, the own colour's rows y0 .. y0+TYa-1 for the planes
+// the tile updates).  Lanes 0..7 of warp 0 issue the bulk copies of a plane
+// (one row range of one component each) after the first lane has armed the
+// stage's mbarrier with the byte count; the stage of plane j is refilled
+// with plane j+kStreamStages after the barrier that ends the update of plane
+// j+1 (the last one that reads it).  Every wait for a plane is bounded: when
+// it runs out the block sets *pp.status, stops updating, drains the copies
+// it issued (again bounded) and returns.  Not for the persistent kernel,
+// whose other blocks write the planes in the same launch.
+template <int MODE, bool MEAS>
+__device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, int zt, int colour, int tx,
+                                            int ty, const PassParams& pp, float* sm, float* acc_out,
+                                            uint32_t& n_acc) {
+  static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
+  constexpr int D = kStreamStages;
+  const int L = lat.L;
+  const int H = L >> 1;
+  const uint32_t PS = static_cast<uint32_t>(H) * static_cast<uint32_t>(L);
+  const uint32_t half = PS * static_cast<uint32_t>(L);
+  const int y0 = yt * lat.ty, z0 = zt * lat.tz;
+  const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
+  const bool act = ty < TYa;
+  const int y = y0 + ty;
+  float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  float* const own = slot + colour * (2 * half);
+  const float* const oth = slot + (colour ^ 1) * (2 * half);
+  // stage layout (floats): other cos rows, other sin rows, own cos rows, own sin rows
+  const int SF = stream_stage_floats(L, lat.ty);
+  const int OS = (lat.ty + 2) * H;           // other sin
+  const int WC = 2 * (lat.ty + 2) * H;       // own cos
+  const int WS = WC + lat.ty * H;            // own sin
+  const uint32_t bar0 = smem_addr(sm + D * SF);
+  const int n_planes = TZa + 2;              // planes z0-1 .. z0+TZa
+  const int warp = (tx + (L >> 3) * ty) >> 5, lane = (tx + (L >> 3) * ty) & 31;
+  const int w0n = min(32, (L >> 3) * lat.ty);  // threads of warp 0
+  const unsigned w0mask = w0n == 32 ? 0xffffffffu : ((1u << w0n) - 1u);
+  const int ym = (y0 == 0 ? L : y0) - 1;
+  const int yp = (y0 + TYa == L) ? 0 : y0 + TYa;
+  __shared__ int s_abort;
+
+  // Warp 0: copy plane j into its stage.
+  auto issue = [&](int j) {
+    const int st = j % D;
+    int zz = z0 - 1 + j;
+    zz += zz < 0 ? L : 0;
+    zz -= zz >= L ? L : 0;
+    const bool has_own = j >= 1 && j <= TZa;
+    const uint32_t row = static_cast<uint32_t>(H) * 4u;
+    const uint32_t bar = bar0 + 8u * st;
+    if (pp.poison && j == 2) return;
+    if (lane == 0) mbar_arrive_expect(bar, 2u * row * static_cast<uint32_t>(TYa + 2 + (has_own ? TYa : 0)));
+    __syncwarp(w0mask);
+    const uint32_t zoff = static_cast<uint32_t>(zz) * PS;
+    const uint32_t dst0 = smem_addr(sm + st * SF);
+    // copy k: 0-2 other cos (top halo row, body rows, bottom halo row),
+    // 3-5 the same of other sin, 6 and 7 own cos and own sin body rows
+    for (int k = lane; k < 8; k += w0n) {
+      if (k < 6) {
+        const int cs = k / 3, part = k % 3;
+        const int yrow = part == 0 ? ym : (part == 1 ? y0 : yp);
+        const int srow = part == 0 ? 0 : (part == 1 ? 1 : TYa + 1);
+        const int nrow = part == 1 ? TYa : 1;
+        const float* src = oth + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(yrow);
+        bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs * OS + srow * H), src, row * nrow, bar);
+      } else if (has_own) {
+        const int cs = k - 6;
+        const float* src = own + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(y0);
+        bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs ? WS : WC), src, row * TYa, bar);
+      }
+    }
+  };
+
+  if (tx == 0 && ty == 0) {
+    for (int st = 0; st < D; ++st) mbar_init(bar0 + 8u * st, 1u);
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  __syncthreads();
+  int n_issued = min(D, n_planes);
+  if (warp == 0)
+    for (int j = 0; j < n_issued; ++j) issue(j);
+
+  float beta = 0.f;
+  uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
+  if (MODE == kMetropolis) {
+    beta = __ldcg(pp.beta_slot + lat.slot0 + r);
+    tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) | kTagMet;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    mlo = static_cast<uint32_t>(mp);
+    mhi = static_cast<uint32_t>(mp >> 32);
+  }
+  SumAcc<MEAS> sums;
+  const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
+  const int kh0 = (tx == 0) ? H - 1 : 4 * tx - 1;
+  const int kh1 = (4 * tx + 4 == H) ? 0 : 4 * tx + 4;
+  int waited = 0;  // planes 0 .. waited-1 seen complete by this thread
+  bool ok = mbar_wait(bar0, 0u, pp.wait_ns);
+  waited = ok ? 1 : 0;
+  ok = ok && mbar_wait(bar0 + 8u, 0u, pp.wait_ns);
+  waited = ok ? 2 : waited;
+
+  for (int i = 0; i < TZa; ++i) {
+    // planes i, i+1, i+2 = z-1, z, z+1
+    if (ok) {
+      ok = mbar_wait(bar0 + 8u * ((i + 2) % D), static_cast<uint32_t>(((i + 2) / D) & 1), pp.wait_ns);
+      waited = ok ? i + 3 : waited;
+    }
+    if (!ok) {
+      s_abort = 1;
+      atomicCAS(pp.status, 0, XY_ERR_TIMEOUT);
+    }
+    if (ok && act) {
+      const int z = z0 + i;
+      const float* sm_m = sm + (i % D) * SF;
+      const float* sm_0 = sm + ((i + 1) % D) * SF;
+      const float* sm_p = sm + ((i + 2) % D) * SF;
+      auto ld = [&](const float* base, int off) { return reinterpret_cast<const float4*>(base + off)[tx]; };
+      Spins4 zc, ysm, ysp, zsm, zsp, ow;
+      zc.c = ld(sm_0, (ty + 1) * H);
+      zc.s = ld(sm_0, OS + (ty + 1) * H);
+      ysm.c = ld(sm_0, ty * H);
+      ysm.s = ld(sm_0, OS + ty * H);
+      ysp.c = ld(sm_0, (ty + 2) * H);
+      ysp.s = ld(sm_0, OS + (ty + 2) * H);
+      zsm.c = ld(sm_m, (ty + 1) * H);
+      zsm.s = ld(sm_m, OS + (ty + 1) * H);
+      zsp.c = ld(sm_p, (ty + 1) * H);
+      zsp.s = ld(sm_p, OS + (ty + 1) * H);
+      ow.c = ld(sm_0, WC + ty * H);
+      ow.s = ld(sm_0, WS + ty * H);
+      const int s = (y + z + colour) & 1;
+      const int kh = s ? kh1 : kh0;
+      const float hc = sm_0[(ty + 1) * H + kh], hs = sm_0[OS + (ty + 1) * H + kh];
+      const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
+      uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+      if (MODE == kMetropolis) {
+        const uint32_t q0 = offz >> 1;
+        w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+        w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+      }
+      float stepv[kNumSums];
+#pragma unroll
+      for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
+      Spins4 nw;
+      update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zsm, zsp, ow, w0, w1, beta, nw, n_acc, stepv);
+      if (MEAS) sums.add_plane(stepv);
+      if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+    }
+    __syncthreads();
+    if (s_abort) break;
+    // plane i has been read for the last time (by this update): its stage
+    // takes plane i + D
+    if (warp == 0 && n_issued < n_planes && n_issued == i + D) {
+      issue(n_issued);
+      ++n_issued;
+    }
+  }
+  if (s_abort && tx == 0 && ty == 0) {
+    // let the copies still in flight land before the block's shared memory
+    // can be handed to another block
+    for (int j = waited; j < n_issued; ++j)
+      if (!(pp.poison && j == 2)) mbar_wait(bar0 + 8u * (j % D), static_cast<uint32_t>((j / D) & 1), pp.wait_ns);
   }
   if (MEAS) sums.export_to(acc_out);
 }
@@ -458,30 +748,16 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
     const float* rp = row_ptr(ty + 2, tz + 1);
     const float* rzm = row_ptr(ty + 1, tz);
     const float* rzp = row_ptr(ty + 1, tz + 2);
-    const float4 zcc = reinterpret_cast<const float4*>(r0)[tx];
-    const float4 zcs = reinterpret_cast<const float4*>(r0 + H)[tx];
-    const float4 ymc = reinterpret_cast<const float4*>(rm)[tx];
-    const float4 yms = reinterpret_cast<const float4*>(rm + H)[tx];
-    const float4 ypc = reinterpret_cast<const float4*>(rp)[tx];
-    const float4 yps = reinterpret_cast<const float4*>(rp + H)[tx];
-    const float4 zmc = reinterpret_cast<const float4*>(rzm)[tx];
-    const float4 zms = reinterpret_cast<const float4*>(rzm + H)[tx];
-    const float4 zpc = reinterpret_cast<const float4*>(rzp)[tx];
-    const float4 zps = reinterpret_cast<const float4*>(rzp + H)[tx];
+    auto row = [&](const float* r) {
+      Spins4 v;
+      v.c = reinterpret_cast<const float4*>(r)[tx];
+      v.s = reinterpret_cast<const float4*>(r + H)[tx];
+      return v;
+    };
+    const Spins4 zc = row(r0), ysm = row(rm), ysp = row(rp), zsm = row(rzm), zsp = row(rzp);
     const int s = (y + z + colour) & 1;
     const int kh = s ? kh1 : kh0;
     const float hc = r0[kh], hs = r0[H + kh];
-    float Xc[5], Xs[5];
-#pragma unroll
-    for (int e = 0; e < 5; ++e) {
-      const float a_c = (e < 4) ? comp(zcc, e < 4 ? e : 0) : hc;
-      const float a_s = (e < 4) ? comp(zcs, e < 4 ? e : 0) : hs;
-      const float b_c = (e == 0) ? hc : comp(zcc, e == 0 ? 0 : e - 1);
-      const float b_s = (e == 0) ? hs : comp(zcs, e == 0 ? 0 : e - 1);
-      Xc[e] = s ? a_c : b_c;
-      Xs[e] = s ? a_s : b_s;
-    }
-    float nc[4], ns[4];
     uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
     if (MODE == kMetropolis) {
       const uint32_t q0 = offz >> 1;
@@ -491,49 +767,13 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
     float stepv[kNumSums];
 #pragma unroll
     for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const float hx = (Xc[e] + Xc[e + 1]) + (comp(ymc, e) + comp(ypc, e)) + (comp(zmc, e) + comp(zpc, e));
-      const float hy = (Xs[e] + Xs[e + 1]) + (comp(yms, e) + comp(yps, e)) + (comp(zms, e) + comp(zps, e));
-      const float co = t_own.c[e], so = t_own.s[e];
-      if (MODE == kMetropolis) {
-        const uint4& w = (e < 2) ? w0 : w1;
-        const uint32_t wprop = (e & 1) ? w.z : w.x;
-        const uint32_t wacc = (e & 1) ? w.w : w.y;
-        const float tp = static_cast<float>(wprop >> 8) * kTwoPiOver2p24;
-        float cp, sp;
-        spin(tp, cp, sp);
-        const float x = beta * (hx * (cp - co) + hy * (sp - so));
-        const bool accept = static_cast<float>(wacc >> 8) < __expf(x) * 16777216.0f;
-        n_acc += accept ? 1u : 0u;
-        nc[e] = accept ? cp : co;
-        ns[e] = accept ? sp : so;
-      } else if (MODE == kOverrelax) {
-        reflect(hx, hy, co, so, nc[e], ns[e]);
-      } else {
-        nc[e] = co;
-        ns[e] = so;
-      }
-      if (MEAS) {
-        const float c = nc[e], sn = ns[e];
-        const float pxc = Xc[e + 1], qxc = Xc[e], pxs = Xs[e + 1], qxs = Xs[e];
-        const float pyc = comp(ypc, e), qyc = comp(ymc, e), pys = comp(yps, e), qys = comp(yms, e);
-        const float pzc = comp(zpc, e), qzc = comp(zmc, e), pzs = comp(zps, e), qzs = comp(zms, e);
-        stepv[0] += c + comp(zcc, e);
-        stepv[1] += sn + comp(zcs, e);
-        stepv[2] += c * (pxc + qxc) + sn * (pxs + qxs);
-        stepv[3] += c * (pyc + qyc) + sn * (pys + qys);
-        stepv[4] += c * (pzc + qzc) + sn * (pzs + qzs);
-        stepv[5] += sn * (pxc - qxc) - c * (pxs - qxs);
-        stepv[6] += sn * (pyc - qyc) - c * (pys - qys);
-        stepv[7] += sn * (pzc - qzc) - c * (pzs - qzs);
-      }
-    }
+    Spins4 nw;
+    update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zsm, zsp, t_own, w0, w1, beta, nw, n_acc, stepv);
     if (MEAS) {
 #pragma unroll
       for (int j = 0; j < kNumSums; ++j) acc_out[j] = stepv[j];
     }
-    if (MODE != kMeasureOnly) st_spins(own + offz, half, nc, ns);
+    if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
   }
   // The shared rows may be overwritten by the caller's next tile.
   __syncthreads();

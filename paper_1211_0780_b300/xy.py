@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libxy.so")
 XY_OK, XY_ERR_ARG, XY_ERR_CUDA, XY_ERR_TIMEOUT, XY_ERR_STATE, XY_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 EXEC_PLAIN, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2
 TAG_INIT, TAG_MET, TAG_PT = 1, 2, 3
-TILE_MARCH, TILE_BLOCK = 0, 1
+TILE_MARCH, TILE_BLOCK, TILE_STREAM = 0, 1, 2
 
 
 class XYError(RuntimeError):
@@ -76,6 +76,7 @@ _SIGNATURES = {
     "xy_autotune": (_I, [_P, _I, _I]),
     "xy_device_status": (_I, [_P, _P]),
     "xy_debug_barrier_timeout": (_I, [_P, _I, _P]),
+    "xy_debug_stream_timeout": (_I, [_P, _I, _P]),
     "xy_reweight_scratch_bytes": (_SZ, [_I64, _I]),
     "xy_reweight_forward": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     "xy_reweight_backward": (_I, [_I, _P, _I, _P, _P, _P, _P, _P, _P, _P]),
@@ -294,6 +295,13 @@ class Simulation:
         """Runs the bounded-barrier test hook; returns (status code, device status)."""
         s = ctypes.c_int(0)
         rc = lib().xy_debug_barrier_timeout(self._ctx, int(budget_us), ctypes.byref(s))
+        return int(rc), int(s.value)
+
+    def debug_stream_timeout(self, budget_us: int):
+        """Runs the stream-tile plane-wait test hook (lattice 0 on a stream
+        tile); returns (status code, device status)."""
+        s = ctypes.c_int(0)
+        rc = lib().xy_debug_stream_timeout(self._ctx, int(budget_us), ctypes.byref(s))
         return int(rc), int(s.value)
 
 

@@ -100,12 +100,13 @@ def test_state_roundtrip_and_layout():
 
 # ---------------------------------------------------------------- half-sweeps
 
-MARCH, BLOCK = 0, 1
+MARCH, BLOCK, STREAM = 0, 1, 2
 
 
 @pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (40, (3, 16, MARCH)),
                                     (32, (32, 32, MARCH)), (24, (3, 5, BLOCK)), (40, (8, 4, BLOCK)),
-                                    (16, (16, 16, BLOCK))])
+                                    (16, (16, 16, BLOCK)), (24, (5, 7, STREAM)), (40, (3, 16, STREAM)),
+                                    (16, (16, 16, STREAM)), (8, (1, 8, STREAM))])
 def test_metropolis_half_parity(L, tile):
     """One Metropolis half-sweep of each colour from the same FP32 state."""
     beta = 0.4542
@@ -146,7 +147,8 @@ OR_A, OR_B = 1.5e-5, 2e-6
 
 
 @pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (40, (3, 16, MARCH)),
-                                    (24, (5, 7, BLOCK)), (40, (8, 3, BLOCK))])
+                                    (24, (5, 7, BLOCK)), (40, (8, 3, BLOCK)), (24, (5, 7, STREAM)),
+                                    (40, (8, 40, STREAM))])
 def test_overrelax_half_parity(L, tile):
     """One over-relaxation half-sweep (Eq. 2) of each colour from the same
     FP32 state: every site within the conditioning bound A/|h| + B (no
@@ -227,7 +229,7 @@ def test_measure_plane_wave_closed_form():
 
 
 @pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (48, (7, 9, MARCH)),
-                                    (24, (5, 7, BLOCK)), (48, (6, 5, BLOCK))])
+                                    (24, (5, 7, BLOCK)), (48, (6, 5, BLOCK)), (48, (7, 9, STREAM))])
 def test_measure_parity(L, tile):
     s = sim(L, 2, [0.40, 0.4542])
     if tile:
@@ -335,7 +337,8 @@ def test_exec_modes_bit_identical():
 def test_tile_shapes_give_identical_angles():
     res = []
     for tile in ((16, 16, MARCH), (4, 8, MARCH), (5, 3, MARCH), (2, 4, MARCH), (8, 8, BLOCK),
-                 (5, 4, BLOCK), (40, 1, BLOCK), (1, 40, BLOCK)):
+                 (5, 4, BLOCK), (40, 1, BLOCK), (1, 40, BLOCK), (8, 8, STREAM), (5, 3, STREAM),
+                 (40, 2, STREAM), (1, 40, STREAM)):
         s = sim(40, 1, [0.4542])
         s.set_tile(0, *tile)
         s.sweep(1, 3, 4)
@@ -387,6 +390,27 @@ def test_barrier_timeout_reports_status_without_hanging():
     assert s.device_status() == 0
     s.sweep(1, 1, 3)
     assert s.get_state()[2][1] == 3
+
+
+def test_stream_tile_wait_timeout_reports_and_recovers():
+    """A stream tile whose plane copy never lands ends its bounded wait with
+    XY_ERR_TIMEOUT in the status word (no hang, nothing updated); the
+    context keeps working and the next half-sweep matches a fresh run."""
+    from paper_1211_0780_b300 import xy
+    a = sim(32, 2, [0.44, 0.46])
+    b = sim(32, 2, [0.44, 0.46])
+    for s in (a, b):
+        s.set_tile(0, 4, 8, STREAM)
+        s.sweep(1, 1, 2)
+    before = a.get_packed()
+    rc, st = a.debug_stream_timeout(20000)
+    assert rc == xy.XY_ERR_TIMEOUT and st == xy.XY_ERR_TIMEOUT
+    assert a.device_status() == 0
+    assert np.array_equal(a.get_packed(), before)
+    for s in (a, b):
+        s.overrelax_half(0)
+        s.sweep(1, 2, 1)
+    assert np.array_equal(a.get_packed(), b.get_packed())
 
 
 def test_checkpoint_resume_is_bit_exact():
