@@ -313,6 +313,54 @@ def bench_reweight(reps: int):
             "fp64_instr_per_s": fp64_ops / (total_ms * 1e-3)}
 
 
+def bench_fss(reps: int):
+    """Finite-size-scaling pass: per-bin reweighting sums of 4 synthetic
+    series (L = 32, 64, 128, 160; T = 10^6 in 200 bins of 5000) to K = 4096
+    beta' in [0.4530, 0.4555], 200 bootstrap resamples of the bins, the
+    resampled U_L and rho_s L curves with derivatives, and the crossings of
+    consecutive sizes (both observables) with 1/nu from the slopes."""
+    import time
+    import torch
+    from paper_1211_0780_b300 import fss, xy
+    from paper_1211_0780_b300.inputs import synthetic_series
+    T, K, n_bins, B = 10 ** 6, 4096, 200, 200
+    st = torch.cuda.current_stream()
+    bp = torch.linspace(0.4530, 0.4555, K, dtype=torch.float64, device="cuda")
+    series = {}
+    for L in (32, 64, 128, 160):
+        s = synthetic_series(L, T, 100 + L)
+        series[L] = dict(zip(("E", "m2", "m4", "c", "s2"), xy._series_tensors(s)))
+    counts = fss.bootstrap_counts(n_bins, B, seed=12)
+    scratch = torch.empty(xy.lib().xy_reweight_bins_scratch_bytes(T, K, n_bins), dtype=torch.uint8, device="cuda")
+    stage = {"bin_sums": 0.0, "resample": 0.0, "curves": 0.0, "crossings": 0.0}
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
+    out = None
+    for rep in range(reps + 1):
+        ev[0].record(st)
+        bins = {L: fss.bin_sums(series[L], 0.4542, bp, n_bins, scratch)[0] for L in series}
+        ev[1].record(st)
+        sums = {L: fss.resample(bins[L], counts) for L in series}
+        ev[2].record(st)
+        cur = {L: fss.curves(sums[L], bp, L) for L in series}
+        ev[3].record(st)
+        Ls = sorted(series)
+        out = {f"{a}-{b}-{w}": fss.crossings(bp, a, cur[a], b, cur[b], w)
+               for a, b in zip(Ls[:-1], Ls[1:]) for w in ("U", "rhoL")}
+        ev[4].record(st)
+        torch.cuda.synchronize()
+        if rep == 0:
+            continue  # warm-up
+        for i, key in enumerate(stage):
+            stage[key] += ev[i].elapsed_time(ev[i + 1]) / reps
+    total = sum(stage.values())
+    crossed = {k: int(torch.isfinite(v[:, 0]).sum()) for k, v in out.items()}
+    pairs = 4 * K * T
+    return {"workload": "4 series (L=32,64,128,160) x T=1e6 in 200 bins x K=4096 beta', 200 bootstrap resamples, "
+                        "U_L and rho_s L crossings of consecutive sizes",
+            "ms_total": total, "ms_per_stage": stage, "pairs_per_ns": pairs / (stage["bin_sums"] * 1e6),
+            "resamples_crossed": crossed}
+
+
 def measured_units():
     from paper_1211_0780_b300 import xy
     out = {}
@@ -427,6 +475,7 @@ def run_gpu(args):
         for key, fn in (("batched_pt", lambda: bench_pt(max(3, args.steps // 2), 2)),
                         ("ragged", lambda: bench_ragged(max(3, args.steps // 4), 2)),
                         ("reweight", lambda: bench_reweight(3)),
+                        ("fss", lambda: bench_fss(3)),
                         ("units", measured_units)):
             try:
                 extras[key] = fn()

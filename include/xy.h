@@ -322,6 +322,52 @@ int xy_reweight_forward_noalloc(int64_t T, const double *d_E, const float *d_m2,
                                 const double *d_betap, int L, double *d_out,
                                 double *d_obs, double *d_cov, void *stream);
 
+/* Per-bin reweighting sums for error analysis by resampling (the paper
+ * blocks its measurements into bins and resamples them, Sec. II-III).  The
+ * series (as for xy_reweight_forward) is cut into n_bins equal contiguous
+ * bins, bin b = samples [b T / n_bins, (b+1) T / n_bins).  d_binsums
+ * [n_bins][K][11] (device f64, caller-owned) receives, for each bin and
+ * target coupling k, the sums over the bin of w_kt x_j for x_j in {1, e,
+ * e^2, m2, m2 e, m4, m4 e, c, c e, s2, s2 e} with e = E - Ebar, c and s2 the
+ * three-direction sums, and w_kt = exp(-(beta'_k - beta0)(e - e_ref)) with a
+ * shift e_ref per k common to all bins: bin sums add, and ratios of
+ * (resampled) sums are reweighted averages.  d_stats[3] (nullable) receives
+ * {Ebar, min e, max e}.  d_scratch: xy_reweight_bins_scratch_bytes(T, K,
+ * n_bins) bytes.  Errors: XY_ERR_ARG (T < 2, K < 1, n_bins outside
+ * [1, min(T, 65535)], NULL pointers), XY_ERR_NOMEM, XY_ERR_CUDA. */
+size_t xy_reweight_bins_scratch_bytes(int64_t T, int K, int n_bins);
+int xy_reweight_bins(int64_t T, const double *d_E, const float *d_m2,
+                     const float *d_m4, const float *d_c, const float *d_s2,
+                     double beta0, int K, const double *d_betap, int n_bins,
+                     double *d_binsums, double *d_stats, void *d_scratch,
+                     size_t scratch_bytes, void *stream);
+
+/* Resampled sums: d_sums[r][K][11] = sum_b d_counts[r][b] d_binsums[b][K][11]
+ * for B resamples given as bin multiplicities (int32 [B][n_bins], device;
+ * bootstrap: drawn with replacement; jackknife: all ones but one zero).
+ * Bins are added in order (deterministic).  n_bins <= 6144, B <= 65535. */
+int xy_fss_resample(int n_bins, int K, const double *d_binsums, int B,
+                    const int32_t *d_counts, double *d_sums, void *stream);
+
+/* Curves of each resample: d_curves[r][4][K] = {U_L (Eq. 5, 1 - <m4> /
+ * (3 <m2>^2)), rho_s L (Eq. 6, (L/3)(<c> - beta' <s2>)), dU_L/dbeta',
+ * d(rho_s L)/dbeta'} from resampled sums, the derivatives by
+ * d<O>/dbeta' = -(<O e> - <O><e>). */
+int xy_fss_curves(int B, int K, const double *d_betap, int L,
+                  const double *d_sums, double *d_curves, void *stream);
+
+/* Crossing of two sizes' curves, row `which` (0 = U_L, 1 = rho_s L), for
+ * each resample (Sec. III: the curves of different L intersect at T_c): the
+ * first grid interval (ascending beta') where A - B changes sign, refined on
+ * the cubic Hermite interpolant of A - B (values and derivatives at the two
+ * grid points) by bisection; slopes of A and B at the crossing from their
+ * Hermite interpolants; 1/nu = ln(|slope B| / |slope A|) / ln(LB / LA),
+ * since a dimensionless ratio scales as Q(t L^{1/nu}).  d_out[B][5] =
+ * {beta*, slope A, slope B, 1/nu, nu}, NaN where the curves do not cross. */
+int xy_fss_crossings(int B, int K, const double *d_betap, int LA,
+                     const double *d_curvesA, int LB, const double *d_curvesB,
+                     int which, double *d_out, void *stream);
+
 /* Backward: given upstream gradients g_U[K] and g_rhoL[K] (device f64) and
  * the forward's d_out, d_cov, returns grad_betap[K] = g_U dU/dbeta' +
  * g_rhoL d(rho_s L)/dbeta' (each output depends only on its own beta'_k).

@@ -112,8 +112,27 @@ __global__ void k_rw_stats_finish(int64_t T, int nblk, const double* part, doubl
   stats[2] = mx - mean;
 }
 
+// Sample range of chunk `chunk`: uniform chunks of t_per_chunk samples, or,
+// with n_bins > 0, chunks_per_bin chunks inside each of n_bins equal bins
+// (bin b = samples [b T / n_bins, (b + 1) T / n_bins)), so that no chunk
+// straddles two bins.
+__device__ __forceinline__ void chunk_range(int chunk, int64_t T, int64_t t_per_chunk, int n_bins,
+                                            int chunks_per_bin, int64_t& t0, int64_t& t1) {
+  if (n_bins <= 0) {
+    t0 = chunk * t_per_chunk;
+    t1 = (t0 + t_per_chunk < T) ? t0 + t_per_chunk : T;
+    return;
+  }
+  const int b = chunk / chunks_per_bin, j = chunk - b * chunks_per_bin;
+  const int64_t b0 = T * b / n_bins, b1 = T * (b + 1) / n_bins;
+  const int64_t per = (b1 - b0 + chunks_per_bin - 1) / chunks_per_bin;
+  t0 = b0 + j * per;
+  t0 = t0 < b1 ? t0 : b1;
+  t1 = (t0 + per < b1) ? t0 + per : b1;
+}
+
 // Pass 2: chunk partial sums S[chunk][k][kNSum].
-__global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chunk,
+__global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chunk, int n_bins, int chunks_per_bin,
                                                     const double* __restrict__ E, const float* __restrict__ m2,
                                                     const float* __restrict__ m4, const float* __restrict__ c,
                                                     const float* __restrict__ s2, double beta0, int K,
@@ -121,8 +140,8 @@ __global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chu
                                                     double* __restrict__ sums) {
   __shared__ double s_e[kChunk], s_m2[kChunk], s_m4[kChunk], s_c[kChunk], s_s2[kChunk];
   const int chunk = blockIdx.y;
-  const int64_t t0 = chunk * t_per_chunk;
-  const int64_t t1 = (t0 + t_per_chunk < T) ? t0 + t_per_chunk : T;
+  int64_t t0, t1;
+  chunk_range(chunk, T, t_per_chunk, n_bins, chunks_per_bin, t0, t1);
   const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * kKT;
   const double Ebar = stats[0], emin = stats[1], emax = stats[2];
 
@@ -280,8 +299,8 @@ int xy_reweight_forward(int64_t T, const double* d_E, const float* d_m2, const f
   double* sums = reinterpret_cast<double*>(ws + p.off_sums);
   k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
   k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, stats);
-  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, d_E, d_m2, d_m4, d_c, d_s2, beta0,
-                                                                  K, d_betap, stats, sums);
+  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, 0, 1, d_E, d_m2, d_m4, d_c, d_s2,
+                                                                  beta0, K, d_betap, stats, sums);
   k_rw_finish<<<(K + 127) / 128, 128, 0, st>>>(K, p.n_tchunks, beta0, d_betap, L, stats, sums, d_out, d_obs, d_cov);
   const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
@@ -391,10 +410,104 @@ int xy_reweight_forward_noalloc(int64_t T, const double* d_E, const float* d_m2,
   double* sums = reinterpret_cast<double*>(ws + off_sums);
   k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
   k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, stats);
-  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, d_E, d_m2, d_m4, d_c, d_s2, beta0,
-                                                                  K, d_betap, stats, sums);
+  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, 0, 1, d_E, d_m2, d_m4, d_c, d_s2,
+                                                                  beta0, K, d_betap, stats, sums);
   k_rw_finish<<<(K + 127) / 128, 128, 0, st>>>(K, p.n_tchunks, beta0, d_betap, L, stats, sums, d_out, d_obs, d_cov);
   e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_rw_err, sizeof g_rw_err, "%s", cudaGetErrorString(e));
+    return XY_ERR_CUDA;
+  }
+  return XY_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Per-bin reweighting sums, for error analysis by resampling whole bins.
+//
+// The series is cut into n_bins equal contiguous bins (the paper bins its
+// measurements before any analysis, Sec. II).  The pass-2 chunks are laid
+// out inside the bins, and pass 3 adds each bin's chunks in order, giving
+// S[b][k][j] for every bin b with the same shift per k for all bins: bin
+// sums add, so the sums of any multiset of bins (a bootstrap or jackknife
+// resample) are a weighted sum of these, and any ratio of them is a
+// reweighted average of that resample.
+// ---------------------------------------------------------------------------
+
+namespace {
+
+struct BinPlan {
+  int n_kblocks, chunks_per_bin, n_tchunks;
+  size_t off_stat_part, off_stats, off_sums, total;
+};
+
+BinPlan bin_plan_for(int64_t T, int K, int n_bins) {
+  BinPlan p{};
+  p.n_kblocks = (K + kKT * kBlock - 1) / (kKT * kBlock);
+  const int64_t per_bin = T / n_bins + 1;
+  const int64_t want = std::max<int64_t>(1, 512 / (static_cast<int64_t>(p.n_kblocks) * n_bins));
+  p.chunks_per_bin = static_cast<int>(std::min<int64_t>(want, (per_bin + kChunk - 1) / kChunk));
+  p.n_tchunks = p.chunks_per_bin * n_bins;
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t at = off;
+    off = (off + b + 255) / 256 * 256;
+    return at;
+  };
+  p.off_stat_part = take(static_cast<size_t>(kStatBlocks) * 3 * 8);
+  p.off_stats = take(4 * 8);
+  p.off_sums = take(static_cast<size_t>(p.n_tchunks) * K * kNSum * 8);
+  p.total = off;
+  return p;
+}
+
+// S[b][k][j] = sum of the chunk partials of bin b in chunk order.
+__global__ void k_rw_bin_sums(int n_bins, int chunks_per_bin, int K, const double* __restrict__ sums,
+                              double* __restrict__ bins) {
+  const int64_t q = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;  // (k, j)
+  const int b = blockIdx.y;
+  if (q >= static_cast<int64_t>(K) * kNSum) return;
+  double v = 0.0;
+  for (int ch = 0; ch < chunks_per_bin; ++ch)
+    v += sums[(static_cast<int64_t>(b) * chunks_per_bin + ch) * K * kNSum + q];
+  bins[static_cast<int64_t>(b) * K * kNSum + q] = v;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t xy_reweight_bins_scratch_bytes(int64_t T, int K, int n_bins) {
+  if (T < 2 || K < 1 || n_bins < 1 || n_bins > T || n_bins > 65535) return 0;
+  return bin_plan_for(T, K, n_bins).total;
+}
+
+int xy_reweight_bins(int64_t T, const double* d_E, const float* d_m2, const float* d_m4, const float* d_c,
+                     const float* d_s2, double beta0, int K, const double* d_betap, int n_bins, double* d_binsums,
+                     double* d_stats, void* d_scratch, size_t scratch_bytes, void* stream) {
+  if (T < 2 || K < 1 || n_bins < 1 || n_bins > T || n_bins > 65535 || !std::isfinite(beta0)) return XY_ERR_ARG;
+  if (!d_E || !d_m2 || !d_m4 || !d_c || !d_s2 || !d_betap || !d_binsums || !d_scratch) return XY_ERR_ARG;
+  if (reinterpret_cast<uintptr_t>(d_scratch) % 256 != 0) return XY_ERR_ARG;
+  const BinPlan p = bin_plan_for(T, K, n_bins);
+  if (scratch_bytes < p.total) return XY_ERR_NOMEM;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  char* ws = static_cast<char*>(d_scratch);
+  double* part = reinterpret_cast<double*>(ws + p.off_stat_part);
+  double* stats = reinterpret_cast<double*>(ws + p.off_stats);
+  double* sums = reinterpret_cast<double*>(ws + p.off_sums);
+  k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
+  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, stats);
+  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, 0, n_bins, p.chunks_per_bin, d_E, d_m2, d_m4, d_c,
+                                                                  d_s2, beta0, K, d_betap, stats, sums);
+  const int64_t nq = static_cast<int64_t>(K) * kNSum;
+  k_rw_bin_sums<<<dim3(static_cast<unsigned>((nq + 255) / 256), n_bins), 256, 0, st>>>(n_bins, p.chunks_per_bin, K,
+                                                                                        sums, d_binsums);
+  if (d_stats) {
+    const cudaError_t ce = cudaMemcpyAsync(d_stats, stats, 3 * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (ce != cudaSuccess) return XY_ERR_CUDA;
+  }
+  const cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     snprintf(g_rw_err, sizeof g_rw_err, "%s", cudaGetErrorString(e));
     return XY_ERR_CUDA;

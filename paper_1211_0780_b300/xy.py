@@ -83,6 +83,11 @@ _SIGNATURES = {
     "xy_reweight_noalloc_capacity_bytes": (_SZ, []),
     "xy_peak_probe": (_I, [_I, _P, _SZ, _P, _P]),
     "xy_reweight_forward_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P]),
+    "xy_reweight_bins_scratch_bytes": (_SZ, [_I64, _I, _I]),
+    "xy_reweight_bins": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _SZ, _P]),
+    "xy_fss_resample": (_I, [_I, _I, _P, _I, _P, _P, _P]),
+    "xy_fss_curves": (_I, [_I, _I, _P, _I, _P, _P, _P]),
+    "xy_fss_crossings": (_I, [_I, _I, _P, _I, _P, _I, _P, _I, _P, _P]),
 }
 
 
