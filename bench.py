@@ -361,6 +361,32 @@ def bench_fss(reps: int):
             "resamples_crossed": crossed}
 
 
+def bench_ladder():
+    """Adaptive ladder: 32^3 x 16 replicas on a linear ladder over
+    [0.40, 0.50], three rounds of 1000 sweeps (1 + 3 passes, exchange every
+    sweep) each followed by the equal-acceptance update; reports the
+    acceptance rates of the first and last ladders and the time per round."""
+    import time
+    import torch
+    from paper_1211_0780_b300 import ladder, xy
+    L, R = 32, 16
+    b0 = np.linspace(0.40, 0.50, R)
+    sim = xy.Simulation(L, R, b0, SEED)
+    sim.set_exec(xy.EXEC_GRAPH)
+    sim.sweep(1, 3, 200, pt_swap_every=1)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hist = ladder.adapt(sim, 0, n_iter=3, sweeps=1000, n_metropolis=1, n_overrelax=3, damping=0.7)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    first, last = hist[0][1], hist[-1][1]
+    return {"workload": "32^3 x 16 replicas, linear ladder on [0.40, 0.50], 3 rounds x 1000 sweeps (1+3 passes)",
+            "ms_per_round": dt * 1e3 / 4, "acceptance_first": [round(float(v), 4) for v in first],
+            "acceptance_last": [round(float(v), 4) for v in last],
+            "spread_first": float(np.ptp(first)), "spread_last": float(np.ptp(last)),
+            "ladder_last": [round(float(v), 5) for v in hist[-1][0]]}
+
+
 def measured_units():
     from paper_1211_0780_b300 import xy
     out = {}
@@ -476,6 +502,7 @@ def run_gpu(args):
                         ("ragged", lambda: bench_ragged(max(3, args.steps // 4), 2)),
                         ("reweight", lambda: bench_reweight(3)),
                         ("fss", lambda: bench_fss(3)),
+                        ("ladder", bench_ladder),
                         ("units", measured_units)):
             try:
                 extras[key] = fn()

@@ -196,6 +196,27 @@ int xy_set_state(xy_ctx *ctx, const float *host_angles, const int32_t *perm,
 int xy_get_packed(xy_ctx *ctx, float *host_packed);
 int xy_set_packed(xy_ctx *ctx, const float *host_packed);
 
+/* Replaces the betas of ladder `lattice` (n_replicas ascending finite
+ * values) in a running context: every slot takes the new beta of its beta
+ * index (the exchange permutation is kept).  Used by an adaptive ladder
+ * (xy_ladder_update); counters, states and records are untouched. */
+int xy_set_betas(xy_ctx *ctx, int lattice, const double *betas);
+
+/* Equal-acceptance ladder update (host only; Sec. II: the temperature set
+ * is chosen so that the exchange acceptance rate does not depend on the
+ * temperature).  betas[R] ascending; acceptance[R-1] = the measured
+ * exchange acceptance of pair (k, k+1).  Model: Gaussian energy
+ * distributions of a common width sigma_k near each pair, for which
+ * A_k = erfc(Delta_k sigma_k / 2); the target widths are Delta*_k =
+ * W (Delta_k / x_k) / sum_j (Delta_j / x_j) with x_k = erfcinv(A_k) (rates
+ * clamped to [1e-6, 1 - 1e-9]) and W = beta_R-1 - beta_0, which equalises
+ * the modelled acceptances.  new_betas[R] keeps both ends and moves each
+ * width the fraction `damping` in [0, 1] of the way to its target.
+ * Errors: XY_ERR_ARG (R < 2, a non-ascending ladder, a rate outside
+ * [0, 1], damping outside [0, 1], NULL). */
+int xy_ladder_update(int R, const double *betas, const double *acceptance,
+                     double damping, double *new_betas);
+
 /* Accepted-move counters: met[total slots] = accepted Metropolis proposals
  * per slot; swap[total slots] = accepted exchanges per ladder pair (entry
  * slot0(l) + k for pair (k, k+1) of ladder l).  Either may be NULL. */

@@ -846,6 +846,35 @@ int xy_set_state(xy_ctx* c, const float* host_angles, const int32_t* perm, const
   return XY_OK;
 }
 
+int xy_set_betas(xy_ctx* c, int lattice, const double* betas) {
+  XY_ENTER(c);
+  if (lattice < 0 || lattice >= c->n_lat || !betas) return XY_ERR_ARG;
+  const LatHost& h = c->lat[lattice];
+  for (int k = 0; k < h.R; ++k) {
+    if (!std::isfinite(betas[k])) return XY_ERR_ARG;
+    if (k > 0 && !(betas[k] > betas[k - 1])) return XY_ERR_ARG;
+  }
+  // The permutation (beta index -> slot) stays; every slot takes the new
+  // beta of its index.
+  std::vector<int> perm(h.R);
+  XY_TRY(c, cudaMemcpyAsync(perm.data(), c->ws + c->lay.perm + 4 * static_cast<size_t>(h.slot0), 4 * h.R,
+                            cudaMemcpyDeviceToHost, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  std::vector<double> b64(h.R);
+  std::vector<float> bs(h.R);
+  for (int k = 0; k < h.R; ++k) {
+    c->betas[h.slot0 + k] = betas[k];
+    b64[perm[k]] = betas[k];
+    bs[perm[k]] = static_cast<float>(betas[k]);
+  }
+  const size_t o8 = 8 * static_cast<size_t>(h.slot0), o4 = 4 * static_cast<size_t>(h.slot0);
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.ladder_beta + o8, betas, 8 * h.R, cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.beta_slot64 + o8, b64.data(), 8 * h.R, cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.beta_slot + o4, bs.data(), 4 * h.R, cudaMemcpyHostToDevice, c->stream));
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
 int xy_get_packed(xy_ctx* c, float* host_packed) {
   XY_ENTER(c);
   if (!host_packed) return XY_ERR_ARG;

@@ -83,6 +83,8 @@ _SIGNATURES = {
     "xy_reweight_noalloc_capacity_bytes": (_SZ, []),
     "xy_peak_probe": (_I, [_I, _P, _SZ, _P, _P]),
     "xy_reweight_forward_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P]),
+    "xy_set_betas": (_I, [_P, _I, _P]),
+    "xy_ladder_update": (_I, [_I, _P, _P, _D, _P]),
     "xy_reweight_bins_scratch_bytes": (_SZ, [_I64, _I, _I]),
     "xy_reweight_bins": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _SZ, _P]),
     "xy_fss_resample": (_I, [_I, _I, _P, _I, _P, _P, _P]),
@@ -258,6 +260,26 @@ class Simulation:
     def set_packed(self, src) -> None:
         ptr = src.data_ptr() if hasattr(src, "data_ptr") else _ptr(np.ascontiguousarray(src, dtype=np.float32))
         _check(lib().xy_set_packed(self._ctx, ptr), "xy_set_packed")
+
+    def counters(self) -> np.ndarray:
+        """{Metropolis passes, sweeps, exchange events, records} (no state copy)."""
+        ctr = np.zeros(4, dtype=np.uint64)
+        _check(lib().xy_get_state(self._ctx, None, None, _ptr(ctr)), "xy_get_state")
+        return ctr
+
+    def set_betas(self, lattice: int, betas) -> None:
+        b = np.ascontiguousarray(np.asarray(betas, dtype=np.float64))
+        if b.size != self.R[lattice]:
+            raise ValueError("one beta per replica of the lattice")
+        _check(lib().xy_set_betas(self._ctx, int(lattice), _ptr(b)), "xy_set_betas")
+        s0 = sum(self.R[:lattice])
+        self.betas = self.betas.copy()
+        self.betas[s0:s0 + self.R[lattice]] = b
+
+    def ladder(self, lattice: int) -> np.ndarray:
+        """The betas of ladder `lattice` (ascending)."""
+        s0 = sum(self.R[:lattice])
+        return self.betas[s0:s0 + self.R[lattice]].copy()
 
     def accepts(self):
         met = np.zeros(self.n_slots, dtype=np.uint64)
