@@ -363,14 +363,15 @@ def bench_fss(reps: int):
 
 def bench_ladder():
     """Adaptive ladder: 32^3 x 16 replicas on a linear ladder over
-    [0.40, 0.50], three rounds of 1000 sweeps (1 + 3 passes, exchange every
-    sweep) each followed by the equal-acceptance update; reports the
-    acceptance rates of the first and last ladders and the time per round."""
+    [0.440, 0.475] (across beta_c), three rounds of 1000 sweeps (1 + 3
+    passes, exchange every sweep) each followed by the equal-acceptance
+    update; reports the acceptance rates of the first and last ladders and
+    the time per round."""
     import time
     import torch
     from paper_1211_0780_b300 import ladder, xy
     L, R = 32, 16
-    b0 = np.linspace(0.40, 0.50, R)
+    b0 = np.linspace(0.440, 0.475, R)
     sim = xy.Simulation(L, R, b0, SEED)
     sim.set_exec(xy.EXEC_GRAPH)
     sim.sweep(1, 3, 200, pt_swap_every=1)
@@ -380,11 +381,45 @@ def bench_ladder():
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     first, last = hist[0][1], hist[-1][1]
-    return {"workload": "32^3 x 16 replicas, linear ladder on [0.40, 0.50], 3 rounds x 1000 sweeps (1+3 passes)",
+    return {"workload": "32^3 x 16 replicas, linear ladder on [0.440, 0.475], 3 rounds x 1000 sweeps (1+3 passes)",
             "ms_per_round": dt * 1e3 / 4, "acceptance_first": [round(float(v), 4) for v in first],
             "acceptance_last": [round(float(v), 4) for v in last],
             "spread_first": float(np.ptp(first)), "spread_last": float(np.ptp(last)),
             "ladder_last": [round(float(v), 5) for v in hist[-1][0]]}
+
+
+def bench_multihist():
+    """Multi-histogram reweighting of a real ladder: 32^3 x 32 replicas on
+    beta = linspace(0.440, 0.468, 32), 3000 measured sweeps (1 + 3 passes,
+    exchange every sweep) -> 96,000 pooled records; the free energies solved
+    to 1e-10 and averages at K = 4096 beta' in [0.440, 0.468]."""
+    import time
+    import torch
+    from paper_1211_0780_b300 import multihist as mh, xy
+    L, R, sweeps, K = 32, 32, 3000, 4096
+    betas = np.linspace(0.440, 0.468, R)
+    sim = xy.Simulation(L, R, betas, SEED, series_capacity=sweeps)
+    sim.set_exec(xy.EXEC_GRAPH)
+    sim.sweep(1, 3, 500, pt_swap_every=1)
+    sim.read_series()
+    sim.sweep(1, 3, sweeps, measure_every=1, pt_swap_every=1)
+    parts, b = mh.series_from_records(sim.read_series(), L, R)
+    pooled, counts = mh.pool(parts)
+    pooled = dict(zip(("E", "m2", "m4", "c", "s2"), xy._series_tensors(pooled)))  # resident on the device
+    T = int(counts.sum())
+    scratch = torch.empty(xy.lib().xy_multihist_scratch_bytes(T, R, K), dtype=torch.uint8, device="cuda")
+    mh.solve(pooled, b, counts, tol=1e-6, scratch=scratch)  # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    f, iters = mh.solve(pooled, b, counts, tol=1e-10, scratch=scratch)
+    torch.cuda.synchronize()
+    t_solve = time.perf_counter() - t0
+    bp = np.linspace(0.440, 0.468, K)
+    st = torch.cuda.current_stream()
+    ms_fwd = time_kernel(lambda: mh.forward(pooled, b, counts, f, bp, L, scratch=scratch), st, 3, warm=1)
+    return {"workload": f"32^3 x 32 replicas, beta=linspace(0.440,0.468,32), {T} pooled records, K=4096 beta'",
+            "records": T, "iterations": iters, "ms_solve": t_solve * 1e3, "ms_per_iteration": t_solve * 1e3 / iters,
+            "ms_forward": ms_fwd, "exp_per_ns_forward": K * T / (ms_fwd * 1e6)}
 
 
 def measured_units():
@@ -503,6 +538,7 @@ def run_gpu(args):
                         ("reweight", lambda: bench_reweight(3)),
                         ("fss", lambda: bench_fss(3)),
                         ("ladder", bench_ladder),
+                        ("multihist", bench_multihist),
                         ("units", measured_units)):
             try:
                 extras[key] = fn()

@@ -343,6 +343,42 @@ int xy_reweight_forward_noalloc(int64_t T, const double *d_E, const float *d_m2,
                                 const double *d_betap, int L, double *d_out,
                                 double *d_obs, double *d_cov, void *stream);
 
+/* Multi-histogram reweighting (Ferrenberg and Swendsen, 1989) of the
+ * pooled series of a whole ladder (not in the paper, which bins each
+ * temperature's series separately, Sec. II).  T records pooled over R <= 64
+ * couplings betas[m] (host, ascending), counts[m] >= 1 of them measured at
+ * betas[m] (host, sum = T), grouped by coupling in that order.  Free
+ * energies: log D_t = log sum_m counts[m] exp(f_m - betas[m] E_t) and
+ * f_k = -log sum_t exp(-betas[k] E_t - log D_t), solved as the minimum of
+ * the convex F(f) = sum_t log D_t - sum_m counts[m] f_m by Newton's method
+ * (f_0 = 0, backtracking line search, steps capped at 20 in any f_k; the
+ * fixed-point step of the equations where the Hessian is not positive
+ * definite) until the step is at most tol.  Start: the caller's f if it is
+ * finite and not all zero, else thermodynamic integration of the group
+ * mean energies.  All FP64 with log-sum-exp shifts; deterministic.
+ * Returns XY_OK, or XY_ERR_TIMEOUT if max_iter steps did not converge (f
+ * holds the last iterate); *iters_out (nullable) gets the number of Newton
+ * steps.  Scratch: xy_multihist_scratch_bytes(T, R, K) bytes (K = 0 for
+ * solving only).  Synchronises `stream` a few times per step. */
+size_t xy_multihist_scratch_bytes(int64_t T, int R, int K);
+int xy_multihist_solve(int64_t T, const double *d_E, int R,
+                       const double *betas, const int64_t *counts, double tol,
+                       int max_iter, double *f, int *iters_out,
+                       void *d_scratch, size_t scratch_bytes, void *stream);
+
+/* Averages at K target couplings from the pooled series and solved f:
+ * <O>_beta' = sum_t O_t exp(-beta' E_t - log D_t) / sum_t exp(...), with the
+ * columns and outputs of xy_reweight_forward (d_out[6][K]: log of the
+ * denominator sum, <E>, <m2>, <m4>, <c>, <s2>; d_obs[2][K]: U_L, rho_s L;
+ * d_cov[5][K]: covariances with E, so xy_reweight_backward gives the
+ * beta' derivatives). */
+int xy_multihist_forward(int64_t T, const double *d_E, const float *d_m2,
+                         const float *d_m4, const float *d_c, const float *d_s2,
+                         int R, const double *betas, const int64_t *counts,
+                         const double *f, int K, const double *d_betap, int L,
+                         double *d_out, double *d_obs, double *d_cov,
+                         void *d_scratch, size_t scratch_bytes, void *stream);
+
 /* Per-bin reweighting sums for error analysis by resampling (the paper
  * blocks its measurements into bins and resamples them, Sec. II-III).  The
  * series (as for xy_reweight_forward) is cut into n_bins equal contiguous

@@ -14,7 +14,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
-SOURCES = ["libxy.cu", "reweight.cu", "fss.cu", "peaks.cu", "ladder.cpp"]
+SOURCES = ["libxy.cu", "reweight.cu", "fss.cu", "multihist.cu", "peaks.cu", "ladder.cpp"]
 HEADERS = ["philox.cuh", "sweep.cuh", "kernels.cuh", "persistent.cuh"]
 LIB = os.path.join(HERE, "libxy.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -85,6 +85,9 @@ _SIGNATURES = {
     "xy_reweight_forward_noalloc": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _P]),
     "xy_set_betas": (_I, [_P, _I, _P]),
     "xy_ladder_update": (_I, [_I, _P, _P, _D, _P]),
+    "xy_multihist_scratch_bytes": (_SZ, [_I64, _I, _I]),
+    "xy_multihist_solve": (_I, [_I64, _P, _I, _P, _P, _D, _I, _P, _P, _P, _SZ, _P]),
+    "xy_multihist_forward": (_I, [_I64, _P, _P, _P, _P, _P, _I, _P, _P, _P, _I, _P, _I, _P, _P, _P, _P, _SZ, _P]),
     "xy_reweight_bins_scratch_bytes": (_SZ, [_I64, _I, _I]),
     "xy_reweight_bins": (_I, [_I64, _P, _P, _P, _P, _P, _D, _I, _P, _I, _P, _P, _P, _SZ, _P]),
     "xy_fss_resample": (_I, [_I, _I, _P, _I, _P, _P, _P]),

@@ -107,3 +107,17 @@ def test_product_path_has_no_fallback(monkeypatch):
     monkeypatch.setattr(xy, "LIB_PATH", "/nonexistent/libxy.so")
     with pytest.raises(RuntimeError):
         xy.lib()
+
+
+def test_scratch_size_queries_on_edge_arguments():
+    """The host-side size queries never divide by zero or overflow on edge
+    arguments (0 = invalid)."""
+    from paper_1211_0780_b300 import xy
+    lb = xy.lib()
+    assert lb.xy_multihist_scratch_bytes(1000, 4, 0) > 0
+    assert lb.xy_multihist_scratch_bytes(1000, 4, 1) > 0
+    assert lb.xy_multihist_scratch_bytes(1000, 257, 4) == 0
+    assert lb.xy_multihist_scratch_bytes(0, 4, 4) == 0
+    assert lb.xy_reweight_bins_scratch_bytes(1000, 1, 1000) > 0
+    assert lb.xy_reweight_bins_scratch_bytes(1000, 1, 1001) == 0
+    assert lb.xy_reweight_scratch_bytes(2, 1) > 0 and lb.xy_reweight_scratch_bytes(1, 1) == 0
