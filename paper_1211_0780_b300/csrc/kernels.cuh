@@ -66,7 +66,8 @@ __global__ void k_from_angles(const float* __restrict__ in, long long N, float* 
 }
 
 // One half-sweep of one lattice: grid (tiles per slot, R); block (L/8, ty) for
-// the march and stream kinds, (L/8, ty, tz) for the block kind.  MEAS: the variant that
+// the march kind, (L/8, ty, tz) for the block kind, 32 (ceil(L ty / 256) + 1)
+// threads in x for the stream kind.  MEAS: the variant that
 // fuses the lattice sums (white passes of measured sweeps and the
 // measurement-only pass).
 template <int MODE, bool MEAS, int KIND>
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(512) k_half(Lattice lat, int colour, PassParam
   if (KIND == kTileBlock)
     tile_block<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, threadIdx.z, true, pp, sm, acc, n_acc);
   else if (KIND == kTileStream)
-    tile_stream<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, sm, acc, n_acc);
+    tile_stream<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, pp, sm, acc, n_acc);
   else
     tile_pass<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);

@@ -38,7 +38,7 @@ struct LatHost {
   long long N() const { return static_cast<long long>(L) * L * L; }
   int nyt() const { return (L + ty - 1) / ty; }
   int nzt() const { return (L + tz - 1) / tz; }
-  int threads() const { return (L / 8) * ty * (kind == kTileBlock ? tz : 1); }
+  int threads() const { return tile_threads(kind, L, ty, tz); }
   int smem() const { return tile_bytes(kind, L, ty, tz); }
 };
 
@@ -260,7 +260,9 @@ template <int MODE, int KIND>
 cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st, int colour,
                              const PassParams& pp) {
   const dim3 grid(h.nyt() * h.nzt(), h.R);
-  const dim3 block = KIND == kTileBlock ? dim3(h.L / 8, h.ty, h.tz) : dim3(h.L / 8, h.ty);  // march, stream
+  const dim3 block = KIND == kTileBlock    ? dim3(h.L / 8, h.ty, h.tz)
+                     : KIND == kTileStream ? dim3(tile_threads(KIND, h.L, h.ty, h.tz))
+                                           : dim3(h.L / 8, h.ty);
   const int smem = h.smem();
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
   if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);

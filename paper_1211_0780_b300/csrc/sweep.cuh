@@ -114,10 +114,18 @@ __host__ __device__ inline int tile_smem_bytes(int L, int ty) {
 __host__ __device__ inline int block_tile_floats(int L, int ty, int tz) { return (ty + 2) * (tz + 2) * L; }
 // kTileStream: per stage, the cosines of the other colour's ty+2 rows, their
 // sines, then the cosines and the sines of the own colour's ty rows (L/2
-// floats per row); after the stages, one 8-byte mbarrier per stage.
+// floats per row); after the stages, a "full" and an "empty" 8-byte
+// mbarrier per stage.
 __host__ __device__ inline int stream_stage_floats(int L, int ty) { return (2 * ty + 2) * L; }
 __host__ __device__ inline int stream_tile_floats(int L, int ty) {
-  return kStreamStages * stream_stage_floats(L, ty) + 2 * kStreamStages;
+  return kStreamStages * stream_stage_floats(L, ty) + 4 * kStreamStages;  // + full and empty mbarriers
+}
+// kTileStream: compute warps covering (L/8) x ty threads, then one producer warp.
+__host__ __device__ inline int stream_compute_warps(int L, int ty) { return ((L / 8) * ty + 31) / 32; }
+__host__ __device__ inline int tile_threads(int kind, int L, int ty, int tz) {
+  return kind == kTileBlock    ? (L / 8) * ty * tz
+         : kind == kTileStream ? 32 * (stream_compute_warps(L, ty) + 1)
+                               : (L / 8) * ty;
 }
 __host__ __device__ inline int tile_floats(int kind, int L, int ty, int tz) {
   return kind == kTileBlock ? block_tile_floats(L, ty, tz)
@@ -508,175 +516,218 @@ __device__ __forceinline__ void bulk_copy_g2s(uint32_t dst, const float* src, ui
       : "memory");
 }
 
-// One tile of one half-sweep, kTileStream: thread (tx, ty) owns the float4
-// pair (cos, sin) of packed k = 4 tx .. 4 tx + 3 of row y0+ty, as in the
-// march, but reads every operand from a ring of kStreamStages shared-memory
-// stages, stage j mod kStreamStages holding plane z0-1+j (the other colour's
-// rows y0-1 .. y0+TYa, the own colour's rows y0 .. y0+TYa-1 for the planes
-// the tile updates).  Lanes 0..7 of warp 0 issue the bulk copies of a plane
-// (one row range of one component each) after the first lane has armed the
-// stage's mbarrier with the byte count; the stage of plane j is refilled
-// with plane j+kStreamStages after the barrier that ends the update of plane
-// j+1 (the last one that reads it).  Every wait for a plane is bounded: when
-// it runs out the block sets *pp.status, stops updating, drains the copies
-// it issued (again bounded) and returns.  Not for the persistent kernel,
-// whose other blocks write the planes in the same launch.
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// One tile of one half-sweep, kTileStream, warp-specialised: a producer warp
+// streams every plane the tile reads into a ring of kStreamStages
+// shared-memory stages with bulk asynchronous copies (TMA), and the compute
+// warps update the sites with no block-wide barrier.  Stage j mod
+// kStreamStages holds plane z0-1+j: the other colour's rows y0-1 .. y0+TYa
+// and, for the planes the tile updates, the own colour's rows y0 .. y0+TYa-1
+// (cosines of all rows, then sines).  Each stage has a "full" mbarrier (the
+// producer arms it with the plane's byte count; the copies complete it) and
+// an "empty" one (every compute warp arrives once it no longer reads the
+// plane).  Compute thread t < (L/8) ty is (tx, ty) = (t mod L/8, t div
+// L/8) of the march; it keeps planes z-1 and z of its column in registers
+// and reads plane z+1's row, the y neighbours, its own spins and the x halo
+// from the ring.  Plane p is read by the updates of planes p-1 (as z+1) and
+// p (current), so it is released after the update of plane p; the producer
+// refills its stage with plane p + kStreamStages, which the compute warps
+// need kStreamStages - 1 updates later.  Every wait is bounded by
+// pp.wait_ns of %globaltimer: when one runs out the block sets *pp.status
+// to XY_ERR_TIMEOUT, every warp leaves its loop (their waits are bounded
+// too), the producer lets the copies it issued land (bounded again) and
+// the tile returns with nothing more written.  Not for the persistent
+// kernel, whose other blocks write the planes within one launch.
 template <int MODE, bool MEAS>
-__device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, int zt, int colour, int tx,
-                                            int ty, const PassParams& pp, float* sm, float* acc_out,
-                                            uint32_t& n_acc) {
+__device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, int zt, int colour, int tid,
+                                            const PassParams& pp, float* sm, float* acc_out, uint32_t& n_acc) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
   constexpr int D = kStreamStages;
   const int L = lat.L;
-  const int H = L >> 1;
+  const int H = L >> 1, TX = L >> 3;
   const uint32_t PS = static_cast<uint32_t>(H) * static_cast<uint32_t>(L);
   const uint32_t half = PS * static_cast<uint32_t>(L);
   const int y0 = yt * lat.ty, z0 = zt * lat.tz;
   const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
-  const bool act = ty < TYa;
+  const int NC = TX * lat.ty;
+  const int nwc = (NC + 31) >> 5;
+  const int warp = tid >> 5, lane = tid & 31;
+  const int tx = tid % TX, ty = tid / TX;
+  const bool act = tid < NC && ty < TYa;
   const int y = y0 + ty;
   float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
   float* const own = slot + colour * (2 * half);
   const float* const oth = slot + (colour ^ 1) * (2 * half);
-  // stage layout (floats): other cos rows, other sin rows, own cos rows, own sin rows
   const int SF = stream_stage_floats(L, lat.ty);
-  const int OS = (lat.ty + 2) * H;           // other sin
-  const int WC = 2 * (lat.ty + 2) * H;       // own cos
-  const int WS = WC + lat.ty * H;            // own sin
-  const uint32_t bar0 = smem_addr(sm + D * SF);
+  const int OS = (lat.ty + 2) * H;           // other sin rows
+  const int WC = 2 * (lat.ty + 2) * H;       // own cos rows
+  const int WS = WC + lat.ty * H;            // own sin rows
+  const uint32_t full0 = smem_addr(sm + D * SF), empty0 = full0 + 8u * D;
   const int n_planes = TZa + 2;              // planes z0-1 .. z0+TZa
-  const int warp = (tx + (L >> 3) * ty) >> 5, lane = (tx + (L >> 3) * ty) & 31;
-  const int w0n = min(32, (L >> 3) * lat.ty);  // threads of warp 0
-  const unsigned w0mask = w0n == 32 ? 0xffffffffu : ((1u << w0n) - 1u);
-  const int ym = (y0 == 0 ? L : y0) - 1;
-  const int yp = (y0 + TYa == L) ? 0 : y0 + TYa;
   __shared__ int s_abort;
 
-  // Warp 0: copy plane j into its stage.
-  auto issue = [&](int j) {
-    const int st = j % D;
-    int zz = z0 - 1 + j;
-    zz += zz < 0 ? L : 0;
-    zz -= zz >= L ? L : 0;
-    const bool has_own = j >= 1 && j <= TZa;
-    const uint32_t row = static_cast<uint32_t>(H) * 4u;
-    const uint32_t bar = bar0 + 8u * st;
-    if (pp.poison && j == 2) return;
-    if (lane == 0) mbar_arrive_expect(bar, 2u * row * static_cast<uint32_t>(TYa + 2 + (has_own ? TYa : 0)));
-    __syncwarp(w0mask);
-    const uint32_t zoff = static_cast<uint32_t>(zz) * PS;
-    const uint32_t dst0 = smem_addr(sm + st * SF);
-    // copy k: 0-2 other cos (top halo row, body rows, bottom halo row),
-    // 3-5 the same of other sin, 6 and 7 own cos and own sin body rows
-    for (int k = lane; k < 8; k += w0n) {
-      if (k < 6) {
-        const int cs = k / 3, part = k % 3;
-        const int yrow = part == 0 ? ym : (part == 1 ? y0 : yp);
-        const int srow = part == 0 ? 0 : (part == 1 ? 1 : TYa + 1);
-        const int nrow = part == 1 ? TYa : 1;
-        const float* src = oth + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(yrow);
-        bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs * OS + srow * H), src, row * nrow, bar);
-      } else if (has_own) {
-        const int cs = k - 6;
-        const float* src = own + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(y0);
-        bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs ? WS : WC), src, row * TYa, bar);
-      }
+  if (tid == 0) {
+    for (int st = 0; st < D; ++st) {
+      mbar_init(full0 + 8u * st, 1u);
+      mbar_init(empty0 + 8u * st, static_cast<uint32_t>(nwc));
     }
-  };
-
-  if (tx == 0 && ty == 0) {
-    for (int st = 0; st < D; ++st) mbar_init(bar0 + 8u * st, 1u);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
-  int n_issued = min(D, n_planes);
-  if (warp == 0)
-    for (int j = 0; j < n_issued; ++j) issue(j);
 
-  float beta = 0.f;
-  uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
-  if (MODE == kMetropolis) {
-    beta = __ldcg(pp.beta_slot + lat.slot0 + r);
-    tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) | kTagMet;
-    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
-    mlo = static_cast<uint32_t>(mp);
-    mhi = static_cast<uint32_t>(mp >> 32);
-  }
-  SumAcc<MEAS> sums;
-  const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
-  const int kh0 = (tx == 0) ? H - 1 : 4 * tx - 1;
-  const int kh1 = (4 * tx + 4 == H) ? 0 : 4 * tx + 4;
-  int waited = 0;  // planes 0 .. waited-1 seen complete by this thread
-  bool ok = mbar_wait(bar0, 0u, pp.wait_ns);
-  waited = ok ? 1 : 0;
-  ok = ok && mbar_wait(bar0 + 8u, 0u, pp.wait_ns);
-  waited = ok ? 2 : waited;
-
-  for (int i = 0; i < TZa; ++i) {
-    // planes i, i+1, i+2 = z-1, z, z+1
-    if (ok) {
-      ok = mbar_wait(bar0 + 8u * ((i + 2) % D), static_cast<uint32_t>(((i + 2) / D) & 1), pp.wait_ns);
-      waited = ok ? i + 3 : waited;
+  if (warp == nwc) {
+    // ---------------------------------------------------------- producer
+    const int ym = (y0 == 0 ? L : y0) - 1;
+    const int yp = (y0 + TYa == L) ? 0 : y0 + TYa;
+    const uint32_t row = static_cast<uint32_t>(H) * 4u;
+    int n_issued = 0;
+    bool ok = true;
+    for (int j = 0; j < n_planes && ok; ++j) {
+      const int st = j % D;
+      if (j >= D) {
+        // every compute warp has released plane j - D
+        bool got = true;
+        if (lane == 0) got = mbar_wait(empty0 + 8u * st, static_cast<uint32_t>((j / D - 1) & 1), pp.wait_ns);
+        ok = __shfl_sync(0xffffffffu, got ? 1 : 0, 0) != 0;
+        if (!ok || *reinterpret_cast<volatile int*>(&s_abort)) {
+          ok = false;
+          break;
+        }
+      }
+      if (!(pp.poison && j == 2)) {
+        int zz = z0 - 1 + j;
+        zz += zz < 0 ? L : 0;
+        zz -= zz >= L ? L : 0;
+        const bool has_own = j >= 1 && j <= TZa;
+        const uint32_t bar = full0 + 8u * st;
+        if (lane == 0) mbar_arrive_expect(bar, 2u * row * static_cast<uint32_t>(TYa + 2 + (has_own ? TYa : 0)));
+        __syncwarp();
+        if (lane < 8) {
+          const uint32_t zoff = static_cast<uint32_t>(zz) * PS;
+          const uint32_t dst0 = smem_addr(sm + st * SF);
+          // Rows y0-1 .. y0+TYa of one component are contiguous unless the
+          // tile touches y = 0 or y = L-1: then one copy per component
+          // (lanes 0, 3), else three (top halo row, body rows, bottom halo
+          // row: lanes 0-2 cos, 3-5 sin).  Lanes 6 and 7: own cos and sin.
+          const bool merged = ym + 1 == y0 && yp == y0 + TYa;
+          if (lane < 6) {
+            const int cs = lane / 3, part = lane % 3;
+            if (!merged || part == 0) {
+              const int yrow = part == 0 ? ym : (part == 1 ? y0 : yp);
+              const int srow = part == 0 ? 0 : (part == 1 ? 1 : TYa + 1);
+              const int nrow = merged ? TYa + 2 : (part == 1 ? TYa : 1);
+              const float* src = oth + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(yrow);
+              bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs * OS + srow * H), src, row * nrow, bar);
+            }
+          } else if (has_own) {
+            const int cs = lane - 6;
+            const float* src = own + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(y0);
+            bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs ? WS : WC), src, row * TYa, bar);
+          }
+        }
+      }
+      n_issued = j + 1;
     }
     if (!ok) {
-      s_abort = 1;
-      atomicCAS(pp.status, 0, XY_ERR_TIMEOUT);
-    }
-    if (ok && act) {
-      const int z = z0 + i;
-      const float* sm_m = sm + (i % D) * SF;
-      const float* sm_0 = sm + ((i + 1) % D) * SF;
-      const float* sm_p = sm + ((i + 2) % D) * SF;
-      auto ld = [&](const float* base, int off) { return reinterpret_cast<const float4*>(base + off)[tx]; };
-      Spins4 zc, ysm, ysp, zsm, zsp, ow;
-      zc.c = ld(sm_0, (ty + 1) * H);
-      zc.s = ld(sm_0, OS + (ty + 1) * H);
-      ysm.c = ld(sm_0, ty * H);
-      ysm.s = ld(sm_0, OS + ty * H);
-      ysp.c = ld(sm_0, (ty + 2) * H);
-      ysp.s = ld(sm_0, OS + (ty + 2) * H);
-      zsm.c = ld(sm_m, (ty + 1) * H);
-      zsm.s = ld(sm_m, OS + (ty + 1) * H);
-      zsp.c = ld(sm_p, (ty + 1) * H);
-      zsp.s = ld(sm_p, OS + (ty + 1) * H);
-      ow.c = ld(sm_0, WC + ty * H);
-      ow.s = ld(sm_0, WS + ty * H);
-      const int s = (y + z + colour) & 1;
-      const int kh = s ? kh1 : kh0;
-      const float hc = sm_0[(ty + 1) * H + kh], hs = sm_0[OS + (ty + 1) * H + kh];
-      const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
-      uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
-      if (MODE == kMetropolis) {
-        const uint32_t q0 = offz >> 1;
-        w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
-        w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+      if (lane == 0) {
+        atomicCAS(pp.status, 0, XY_ERR_TIMEOUT);
+        s_abort = 1;
+        // the copies of the last D issued planes may still be landing
+        for (int j = max(0, n_issued - D); j < n_issued; ++j)
+          if (!(pp.poison && j == 2)) mbar_wait(full0 + 8u * (j % D), static_cast<uint32_t>((j / D) & 1), pp.wait_ns);
       }
-      float stepv[kNumSums];
+      __syncwarp();
+    }
+  } else {
+    // ---------------------------------------------------------- compute
+    float beta = 0.f;
+    uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
+    if (MODE == kMetropolis) {
+      beta = __ldcg(pp.beta_slot + lat.slot0 + r);
+      tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) | kTagMet;
+      const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+      mlo = static_cast<uint32_t>(mp);
+      mhi = static_cast<uint32_t>(mp >> 32);
+    }
+    SumAcc<MEAS> sums;
+    const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
+    const int kh0 = (tx == 0) ? H - 1 : 4 * tx - 1;
+    const int kh1 = (4 * tx + 4 == H) ? 0 : 4 * tx + 4;
+    // per-thread float offsets inside a stage
+    const int o_row = (ty + 1) * H + 4 * tx, o_ym = ty * H + 4 * tx, o_yp = (ty + 2) * H + 4 * tx;
+    const int o_own = WC + ty * H + 4 * tx;
+    auto ld2 = [&](const float* st, int oc, int os) {
+      Spins4 v;
+      v.c = *reinterpret_cast<const float4*>(st + oc);
+      v.s = *reinterpret_cast<const float4*>(st + os);
+      return v;
+    };
+    // warp-uniform outcome (a lane whose wait ran out takes the warp with it)
+    auto wait_plane = [&](int j) -> bool {
+      const bool got = mbar_wait(full0 + 8u * (j % D), static_cast<uint32_t>((j / D) & 1), pp.wait_ns);
+      return __all_sync(0xffffffffu, got);
+    };
+    auto release = [&](int j) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(empty0 + 8u * (j % D));
+    };
+    bool ok = wait_plane(0) && wait_plane(1);
+    Spins4 pa{}, pb{}, pc{};
+    if (ok && act) {
+      pa = ld2(sm, o_row, OS + o_row);
+      pb = ld2(sm + SF, o_row, OS + o_row);
+    }
+    if (ok) release(0);
+    int s1 = 1;  // stage of plane i+1 (the current plane of update i)
+    auto step = [&](Spins4& zm, Spins4& zc, Spins4& zn, int i) {
+      const int s2 = s1 + 1 == D ? 0 : s1 + 1;
+      ok = ok && wait_plane(i + 2);
+      if (!ok) return;
+      if (act) {
+        const int z = z0 + i;
+        const float* cur = sm + s1 * SF;
+        zn = ld2(sm + s2 * SF, o_row, OS + o_row);
+        const Spins4 ysm = ld2(cur, o_ym, OS + o_ym), ysp = ld2(cur, o_yp, OS + o_yp);
+        const Spins4 t_own = ld2(cur, o_own, o_own + lat.ty * H);
+        const int s = (y + z + colour) & 1;
+        const int kh = (ty + 1) * H + (s ? kh1 : kh0);
+        const float hc = cur[kh], hs = cur[OS + kh];
+        const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
+        uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+        if (MODE == kMetropolis) {
+          const uint32_t q0 = offz >> 1;
+          w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+          w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+        }
+        float stepv[kNumSums];
 #pragma unroll
-      for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
-      Spins4 nw;
-      update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zsm, zsp, ow, w0, w1, beta, nw, n_acc, stepv);
-      if (MEAS) sums.add_plane(stepv);
-      if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+        for (int q = 0; q < kNumSums; ++q) stepv[q] = 0.f;
+        Spins4 nw;
+        update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
+        if (MEAS) sums.add_plane(stepv);
+        if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+      }
+      release(i + 1);
+      s1 = s2;
+    };
+    for (int i = 0; i < TZa && ok; i += 3) {
+      step(pa, pb, pc, i);
+      if (i + 1 >= TZa || !ok) break;
+      step(pb, pc, pa, i + 1);
+      if (i + 2 >= TZa || !ok) break;
+      step(pc, pa, pb, i + 2);
     }
-    __syncthreads();
-    if (s_abort) break;
-    // plane i has been read for the last time (by this update): its stage
-    // takes plane i + D
-    if (warp == 0 && n_issued < n_planes && n_issued == i + D) {
-      issue(n_issued);
-      ++n_issued;
+    if (!ok) {
+      if (lane == 0) atomicCAS(pp.status, 0, XY_ERR_TIMEOUT);
+      s_abort = 1;
     }
+    if (MEAS) sums.export_to(acc_out);
   }
-  if (s_abort && tx == 0 && ty == 0) {
-    // let the copies still in flight land before the block's shared memory
-    // can be handed to another block
-    for (int j = waited; j < n_issued; ++j)
-      if (!(pp.poison && j == 2)) mbar_wait(bar0 + 8u * (j % D), static_cast<uint32_t>((j / D) & 1), pp.wait_ns);
-  }
-  if (MEAS) sums.export_to(acc_out);
 }
 
 // One tile of one half-sweep, kTileBlock: thread (tx, ty, tz) owns the 4
