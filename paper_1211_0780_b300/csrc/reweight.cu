@@ -12,15 +12,17 @@
 // exponent is <= 0 (the log-sum-exp shift, known in closed form from the
 // extremes of the series).
 //
-// Work split.  Pass 1 reduces (sum E, min E, max E) in a fixed order.
-// Pass 2: a block owns 4 * blockDim.x consecutive k and one chunk of t;
-// each thread owns 4 consecutive k.  It evaluates the weight of its first k
-// exactly and, when its four couplings are evenly spaced (the usual
-// linspace grid), steps to the next ones by multiplying with
-// rho_t = exp(-delta (e_t - e_ref)) (two FP64 exps per four (k, t) pairs;
-// relative error of the stepped weights <= 3 roundings).  The per-chunk
-// partial sums go to scratch; pass 3 adds the chunks in chunk order
-// (deterministic) and forms the outputs.  The FP64 pipe bounds pass 2.
+// Work split.  Pass 1 reduces (sum E, min E, max E) in a fixed order and
+// takes the grid step (beta'_K-1 - beta'_0) / (K - 1).  Pass 2: a block owns
+// 4 * blockDim.x consecutive k and one chunk of t; each thread owns 4
+// consecutive k.  It evaluates the weight of its first k exactly and, when
+// its four couplings sit on the grid step (the usual linspace grid), steps
+// to the next ones by multiplying with rho_t = exp(-step (e_t - e_ref)),
+// whose sample-dependent factor exp(-step (e_t - e_mid)) the block
+// evaluates once per staged sample in shared memory (one FP64 exp per four
+// (k, t) pairs; relative error of the stepped weights <= 5 roundings).  The
+// per-chunk partial sums go to scratch; pass 3 adds the chunks in chunk
+// order (deterministic) and forms the outputs.  The FP64 pipe bounds pass 2.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -97,8 +99,10 @@ __global__ void k_rw_stats(int64_t T, const double* __restrict__ E, double* part
   }
 }
 
-// Pass 1b: stats = {Ebar, e_min, e_max} with e = E - Ebar.
-__global__ void k_rw_stats_finish(int64_t T, int nblk, const double* part, double* stats) {
+// Pass 1b: stats = {Ebar, e_min, e_max, grid step} with e = E - Ebar and
+// grid step = (beta'_K-1 - beta'_0) / (K - 1) (0 for K = 1).
+__global__ void k_rw_stats_finish(int64_t T, int nblk, const double* part, int K, const double* betap,
+                                  double* stats) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   double sum = 0.0, mn = INFINITY, mx = -INFINITY;
   for (int b = 0; b < nblk; ++b) {
@@ -110,6 +114,7 @@ __global__ void k_rw_stats_finish(int64_t T, int nblk, const double* part, doubl
   stats[0] = mean;
   stats[1] = mn - mean;
   stats[2] = mx - mean;
+  stats[3] = K > 1 ? (betap[K - 1] - betap[0]) / (K - 1) : 0.0;
 }
 
 // Sample range of chunk `chunk`: uniform chunks of t_per_chunk samples, or,
@@ -138,12 +143,13 @@ __global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chu
                                                     const float* __restrict__ s2, double beta0, int K,
                                                     const double* __restrict__ betap, const double* __restrict__ stats,
                                                     double* __restrict__ sums) {
-  __shared__ double s_e[kChunk], s_m2[kChunk], s_m4[kChunk], s_c[kChunk], s_s2[kChunk];
+  __shared__ double s_e[kChunk], s_m2[kChunk], s_m4[kChunk], s_c[kChunk], s_s2[kChunk], s_rho[kChunk];
   const int chunk = blockIdx.y;
   int64_t t0, t1;
   chunk_range(chunk, T, t_per_chunk, n_bins, chunks_per_bin, t0, t1);
   const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * kKT;
-  const double Ebar = stats[0], emin = stats[1], emax = stats[2];
+  const double Ebar = stats[0], emin = stats[1], emax = stats[2], gstep = stats[3];
+  const double emid = 0.5 * (emin + emax);
 
   double d[kKT];
   int nk = 0;
@@ -154,12 +160,18 @@ __global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chu
     nk += (k < K) ? 1 : 0;
   }
   const double eref = d[0] >= 0.0 ? emin : emax;
-  // Even spacing of this thread's couplings (to rounding) allows stepping.
-  const double step = (nk > 1) ? d[1] - d[0] : 0.0;
-  bool even = nk > 1;
+  // Even spacing of this thread's couplings (to rounding) at the grid's
+  // step allows stepping: w_{i+1} = w_i rho_t with rho_t = exp(-step (e_t -
+  // eref)) = exp(-step (e_t - emid)) exp(-step (emid - eref)); the first
+  // factor is the same for every thread, so the block evaluates it once per
+  // sample into shared memory, and each thread multiplies by its constant.
+  const double step = gstep;
+  bool even = nk > 1 && step != 0.0;
 #pragma unroll
-  for (int i = 2; i < kKT; ++i)
-    if (i < nk) even = even && fabs(d[i] - (d[0] + i * step)) <= 1e-15 * (fabs(d[0]) + fabs(step) * i + 1e-300);
+  for (int i = 1; i < kKT; ++i)
+    if (i < nk)  // a few ulps of the couplings themselves (grids from linspace round to them)
+      even = even && fabs(d[i] - (d[0] + i * step)) <= 8.0 * 2.220446049250313e-16 * (fabs(beta0) + fabs(d[i]));
+  const double rho_c = even ? exp(-step * (emid - eref)) : 0.0;
   // Stepping from a coupling whose shift differs in sign is also fine: the
   // exponent stays bounded by |step| * kKT * (emax - emin).
 
@@ -179,6 +191,7 @@ __global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chu
       s_m4[j] = static_cast<double>(m4[t]);
       s_c[j] = static_cast<double>(c[t]) + static_cast<double>(c[T + t]) + static_cast<double>(c[2 * T + t]);
       s_s2[j] = static_cast<double>(s2[t]) + static_cast<double>(s2[T + t]) + static_cast<double>(s2[2 * T + t]);
+      s_rho[j] = exp(-step * (s_e[j] - emid));
     }
     __syncthreads();
     if (nk > 0) {
@@ -186,7 +199,7 @@ __global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chu
         const double e = s_e[j], x2 = s_m2[j], x4 = s_m4[j], xc = s_c[j], xs = s_s2[j];
         const double de = e - eref;
         double w = exp(-d[0] * de);
-        const double rho = even ? exp(-step * de) : 0.0;
+        const double rho = even ? s_rho[j] * rho_c : 0.0;
 #pragma unroll
         for (int i = 0; i < kKT; ++i) {
           if (i > 0) w = even ? w * rho : exp(-d[i] * de);
@@ -298,7 +311,7 @@ int xy_reweight_forward(int64_t T, const double* d_E, const float* d_m2, const f
   double* stats = reinterpret_cast<double*>(ws + p.off_stats);
   double* sums = reinterpret_cast<double*>(ws + p.off_sums);
   k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
-  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, stats);
+  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, K, d_betap, stats);
   k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, 0, 1, d_E, d_m2, d_m4, d_c, d_s2,
                                                                   beta0, K, d_betap, stats, sums);
   k_rw_finish<<<(K + 127) / 128, 128, 0, st>>>(K, p.n_tchunks, beta0, d_betap, L, stats, sums, d_out, d_obs, d_cov);
@@ -409,7 +422,7 @@ int xy_reweight_forward_noalloc(int64_t T, const double* d_E, const float* d_m2,
   double* stats = reinterpret_cast<double*>(ws + off_stats);
   double* sums = reinterpret_cast<double*>(ws + off_sums);
   k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
-  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, stats);
+  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, K, d_betap, stats);
   k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, 0, 1, d_E, d_m2, d_m4, d_c, d_s2,
                                                                   beta0, K, d_betap, stats, sums);
   k_rw_finish<<<(K + 127) / 128, 128, 0, st>>>(K, p.n_tchunks, beta0, d_betap, L, stats, sums, d_out, d_obs, d_cov);
@@ -497,7 +510,7 @@ int xy_reweight_bins(int64_t T, const double* d_E, const float* d_m2, const floa
   double* stats = reinterpret_cast<double*>(ws + p.off_stats);
   double* sums = reinterpret_cast<double*>(ws + p.off_sums);
   k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
-  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, stats);
+  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, K, d_betap, stats);
   k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, 0, n_bins, p.chunks_per_bin, d_E, d_m2, d_m4, d_c,
                                                                   d_s2, beta0, K, d_betap, stats, sums);
   const int64_t nq = static_cast<int64_t>(K) * kNSum;
