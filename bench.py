@@ -175,7 +175,8 @@ def run_reference(args):
     value = args.steps * upd / (total * 1e9)
     sample = f"{args.steps} sweeps (1 Metropolis + 5 over-relaxation passes) of the 160^3 lattice, one per step"
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "device": f"host CPU, {n} threads (the FP64 oracle; rank 0 only)",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD + " (reference step = 1 sweep)"},
