@@ -51,7 +51,7 @@ Plan plan_for(int64_t T, int R, int K) {
   Plan p{};
   p.n_tblocks = static_cast<int>(std::min<int64_t>(512, (T + kBlock - 1) / kBlock));
   p.n_kblocks = std::max(1, (K + kKT * kBlock - 1) / (kKT * kBlock));  // K = 0: solving only
-  const int64_t want = std::max<int64_t>(1, 512 / p.n_kblocks);
+  const int64_t want = std::max<int64_t>(1, 4 * 148 / p.n_kblocks);  // four full waves on 148 SMs
   p.n_tchunks = static_cast<int>(std::min<int64_t>(want, (T + kChunk - 1) / kChunk));
   p.t_per_chunk = (T + p.n_tchunks - 1) / p.n_tchunks;
   size_t off = 0;

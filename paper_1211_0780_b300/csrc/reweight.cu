@@ -40,6 +40,26 @@ constexpr int kBlock = 256;     // threads per block in pass 2
 constexpr int kChunk = 256;     // samples staged in shared memory at a time
 constexpr int kNSum = 11;       // 1, e, e^2, m2, m2 e, m4, m4 e, c, c e, s2, s2 e
 constexpr int kStatBlocks = 256;
+// Pass-2 grids are sized in whole waves of B300's 148 SMs: one 256-thread
+// block of the sums kernel fits per SM (178 registers a thread), so a grid
+// of 4 x 148 blocks runs as four full waves with no partial last wave.
+constexpr int kWaveBlocks = 4 * 148;
+
+// Chunks per bin (1..8) whose grid n_kblocks * n_bins * c fills its last
+// wave of 148 blocks best (the smallest on ties).
+int chunks_for_waves(int64_t n_kblocks, int64_t n_bins, int64_t max_c) {
+  int best = 1;
+  double best_eff = 0.0;
+  for (int c = 1; c <= 8 && c <= max_c; ++c) {
+    const double waves = static_cast<double>(n_kblocks * n_bins * c) / 148.0;
+    const double eff = waves / std::ceil(waves);
+    if (eff > best_eff + 1e-9) {
+      best_eff = eff;
+      best = c;
+    }
+  }
+  return best;
+}
 
 struct Plan {
   int n_kblocks, n_tchunks;
@@ -50,7 +70,7 @@ struct Plan {
 Plan plan_for(int64_t T, int K) {
   Plan p{};
   p.n_kblocks = (K + kKT * kBlock - 1) / (kKT * kBlock);
-  const int64_t want = std::max<int64_t>(1, 512 / p.n_kblocks);
+  const int64_t want = std::max<int64_t>(1, kWaveBlocks / p.n_kblocks);
   p.n_tchunks = static_cast<int>(std::min<int64_t>(want, (T + kChunk - 1) / kChunk));
   p.t_per_chunk = (T + p.n_tchunks - 1) / p.n_tchunks;
   size_t off = 0;
@@ -459,8 +479,7 @@ BinPlan bin_plan_for(int64_t T, int K, int n_bins) {
   BinPlan p{};
   p.n_kblocks = (K + kKT * kBlock - 1) / (kKT * kBlock);
   const int64_t per_bin = T / n_bins + 1;
-  const int64_t want = std::max<int64_t>(1, 512 / (static_cast<int64_t>(p.n_kblocks) * n_bins));
-  p.chunks_per_bin = static_cast<int>(std::min<int64_t>(want, (per_bin + kChunk - 1) / kChunk));
+  p.chunks_per_bin = chunks_for_waves(p.n_kblocks, n_bins, (per_bin + kChunk - 1) / kChunk);
   p.n_tchunks = p.chunks_per_bin * n_bins;
   size_t off = 0;
   auto take = [&](size_t b) {

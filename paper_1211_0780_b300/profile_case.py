@@ -4,7 +4,9 @@ python -m paper_1211_0780_b300.profile_case --L 160 --ty 8 --tz 2 --kind 1 --mod
 
 Creates one lattice (seeded hot start), runs a few warm-up sweeps, then
 issues `--launches` half-sweeps of the chosen kernel (or = over-relaxation,
-met = Metropolis, meas = measurement-only) and synchronises.  No autotuning,
+met = Metropolis, meas = measurement-only) and synchronises; reweight =
+`--launches` forward reweightings of one synthetic series of `--T` samples to
+`--K` couplings.  No autotuning,
 so the launch list is short and deterministic.
 """
 
@@ -20,12 +22,25 @@ def main():
     ap.add_argument("--ty", type=int, default=0)
     ap.add_argument("--tz", type=int, default=0)
     ap.add_argument("--kind", type=int, default=1, help="0 = march tile, 1 = block tile")
-    ap.add_argument("--mode", default="or", choices=["or", "met", "meas", "sweep"])
+    ap.add_argument("--mode", default="or", choices=["or", "met", "meas", "sweep", "reweight"])
+    ap.add_argument("--T", type=int, default=200000, help="samples of the reweight mode's series")
+    ap.add_argument("--K", type=int, default=4096, help="couplings of the reweight mode")
     ap.add_argument("--launches", type=int, default=5)
     ap.add_argument("--warm-sweeps", type=int, default=2)
     args = ap.parse_args()
     import torch
     from paper_1211_0780_b300 import xy
+    if args.mode == "reweight":
+        # forward reweighting of one synthetic series (L sets its scale)
+        from paper_1211_0780_b300.inputs import synthetic_series
+        s = synthetic_series(args.L, args.T, 100 + args.L)
+        tens = dict(zip(("E", "m2", "m4", "c", "s2"), xy._series_tensors(s)))
+        bp = torch.linspace(0.4530, 0.4555, args.K, dtype=torch.float64, device="cuda")
+        for _ in range(args.launches):
+            xy.reweight_forward(tens, 0.4542, bp, args.L)
+        torch.cuda.synchronize()
+        print("reweight done")
+        return
     betas = np.linspace(0.4542, 0.4560, args.R) if args.R > 1 else [0.4542]
     sim = xy.Simulation(args.L, args.R, betas, 0x5EED2012)
     if args.ty and args.tz:
