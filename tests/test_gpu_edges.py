@@ -1,0 +1,80 @@
+"""Edge cases of the analysis kernels: one bin, two couplings, one
+resample, unequal record counts, the largest ladder, and argument checks."""
+
+import numpy as np
+import pytest
+
+from oracle import fss as ofss
+from oracle import multihist as omh
+
+pytestmark = pytest.mark.gpu
+
+
+def _synthetic(L, T, seed):
+    from paper_1211_0780_b300.inputs import synthetic_series
+    return synthetic_series(L, T, seed)
+
+
+def test_single_bin_two_couplings_one_resample():
+    from paper_1211_0780_b300 import fss
+    s = _synthetic(16, 3001, 4)
+    bp = np.array([0.4530, 0.4555])
+    bins, _ = fss.bin_sums(s, 0.4542, bp, 1)
+    cur = fss.curves(fss.resample(bins, np.ones((1, 1), np.int32)), bp, 16).cpu().numpy()
+    ref = ofss.curves_at(s, 0.4542, bp, 16)
+    np.testing.assert_allclose(cur[0, 0], ref["U"], rtol=1e-9)
+    np.testing.assert_allclose(cur[0, 1], ref["rhoL"], rtol=1e-9)
+
+
+def test_bins_as_many_as_samples_and_zero_multiplicities():
+    from paper_1211_0780_b300 import fss
+    s = _synthetic(8, 64, 5)
+    bp = np.linspace(0.445, 0.462, 9)
+    bins, _ = fss.bin_sums(s, 0.4542, bp, 64)  # one sample per bin
+    counts = np.zeros((2, 64), np.int32)
+    counts[0, :] = 1
+    counts[1, ::2] = 2  # even samples twice, odd ones dropped
+    cur = fss.curves(fss.resample(bins, counts), bp, 8).cpu().numpy()
+    for r in range(2):
+        ref = ofss.curves_at(ofss.resampled_series(s, 64, counts[r]), 0.4542, bp, 8)
+        np.testing.assert_allclose(cur[r, 0], ref["U"], rtol=1e-9)
+
+
+def test_reweighting_argument_checks():
+    from paper_1211_0780_b300 import fss, xy
+    s = _synthetic(8, 100, 6)
+    with pytest.raises(xy.XYError):
+        fss.bin_sums(s, 0.45, [0.45, 0.46], 101)  # more bins than samples
+    with pytest.raises(xy.XYError):
+        fss.bin_sums(s, 0.45, [0.45, 0.46], 0)
+
+
+def test_multihist_unequal_counts_and_largest_ladder():
+    from paper_1211_0780_b300 import multihist as mh
+    rng = np.random.default_rng(8)
+    R = 64
+    betas = np.linspace(0.40, 0.50, R)
+    n = rng.integers(200, 600, R)
+    s = 60.0
+    parts = []
+    for b, k in zip(betas, n):
+        E = -4000.0 - b * s * s + s * rng.standard_normal(k)
+        m2 = np.clip(0.05 + 0.001 * rng.standard_normal(k), 0, 1)
+        parts.append({"E": E, "m2": m2.astype(np.float32), "m4": (m2 * m2).astype(np.float32),
+                      "c": np.full((3, k), 0.4, np.float32), "s2": np.full((3, k), 0.1, np.float32)})
+    pooled, counts = mh.pool(parts)
+    f, it = mh.solve(pooled, betas, counts, tol=1e-11)
+    fo, _ = omh.solve(pooled["E"], betas, counts, tol=1e-13)
+    np.testing.assert_allclose(f, fo, atol=1e-8)
+    with pytest.raises(Exception):
+        mh.solve(pooled, np.linspace(0.40, 0.50, 65), np.append(counts, 1))  # 65 couplings
+
+
+def test_ladder_two_replicas_and_bad_betas():
+    from paper_1211_0780_b300 import ladder, xy
+    np.testing.assert_array_equal(ladder.update([0.4, 0.5], [0.3]), [0.4, 0.5])
+    sim = xy.Simulation(8, 3, [0.40, 0.42, 0.44], 3)
+    with pytest.raises(xy.XYError):
+        sim.set_betas(0, [0.40, 0.39, 0.44])
+    sim.set_betas(0, [0.41, 0.42, 0.43])
+    np.testing.assert_array_equal(sim.ladder(0), [0.41, 0.42, 0.43])
