@@ -443,3 +443,35 @@ def test_checkpoint_resume_is_bit_exact():
     back = c.get_state()
     assert all(np.max(circ_dist(x, y)) < 1e-6 for x, y in zip(back[0], angles))
     assert np.array_equal(back[1], perm) and np.array_equal(back[2], ctr)
+
+
+@pytest.mark.parametrize("tile", [(8, 8, MARCH), (4, 2, BLOCK), (8, 4, STREAM)])
+def test_zero_field_degenerate_case(tile):
+    """Where the six neighbours cancel exactly (h = 0: opposite unit vectors
+    (1, 0) and (-1, 0) along each axis, written into the device state
+    directly so that no rounding of pi spoils the cancellation),
+    over-relaxation leaves the spin unchanged (Sec. II reading: no field, no
+    reflection) and every Metropolis proposal is accepted (dE = 0)."""
+    L = 16
+    H, N = L // 2, L ** 3
+    z, y, x = np.meshgrid(*(np.arange(L),) * 3, indexing="ij")
+    col = (x + y + z) % 2
+    p = (x >> 1) + H * (y + L * z)
+    # black sites (1, 0) or (-1, 0) by the parity of x//2 + y//2 + z//2:
+    # every white site sees opposite spins at x+-1, y+-1 and z+-1
+    sign = np.where((x // 2 + y // 2 + z // 2) % 2 == 0, 1.0, -1.0)
+    cs = np.where(col == 0, sign, np.cos(0.7))
+    sn = np.where(col == 0, 0.0, np.sin(0.7))
+    packed = np.zeros(2 * N, np.float32)
+    for c in (0, 1):
+        m = col == c
+        packed[c * N + p[m]] = cs[m]
+        packed[c * N + N // 2 + p[m]] = sn[m]
+    s = sim(L, 1, [0.4542])
+    s.set_tile(0, *tile)
+    s.set_packed(packed)
+    s.overrelax_half(1)
+    assert np.array_equal(s.get_packed(), packed)
+    acc0 = s.accepts()[0][0]
+    s.metropolis_half(1, 4)
+    assert s.accepts()[0][0] - acc0 == N // 2
