@@ -240,3 +240,33 @@ def test_multihist_full_size_is_a_fixed_point_of_the_oracle_equations():
     g = mh.forward(pooled, b, counts, f, bp, L)
     mE, _, _ = omh.averages(pooled["E"], pooled["E"][:, None], b, counts, f, bp)
     np.testing.assert_allclose(g["E"].cpu().numpy(), mE, rtol=1e-10)
+
+
+def test_large_lattice_properties():
+    """L = 512 (134M sites, beyond every benchmark size): an over-relaxation
+    half-sweep conserves the energy, applying it twice returns the state
+    (the reflection is an involution with the field frozen), and the
+    Metropolis half-sweep touches only its colour.  Properties that hold at
+    any size; index arithmetic past 2^26 sites per colour."""
+    from paper_1211_0780_b300 import xy
+    L = 512
+    s = xy.Simulation(L, 1, [0.4542], SEED, series_capacity=4)
+    s.sweep(1, 1, 2)
+    E0 = s.measure()["E"][0]
+    pk0 = s.get_packed()
+    s.overrelax_half(0)
+    E1 = s.measure()["E"][0]
+    assert abs(E1 - E0) < 1e-6 * abs(E0)
+    s.overrelax_half(0)
+    pk2 = s.get_packed()
+    half = L ** 3 // 2
+    # colour 1 untouched bit for bit, colour 0 back to within FP32 rounding
+    assert np.array_equal(pk2[2 * half:], pk0[2 * half:])
+    dc = np.abs(pk2[:half] - pk0[:half])
+    ds = np.abs(pk2[half:2 * half] - pk0[half:2 * half])
+    assert np.mean(np.maximum(dc, ds) > 1e-5) < 1e-3
+    s.set_packed(pk0)
+    s.metropolis_half(1, 3)
+    pk3 = s.get_packed()
+    assert np.array_equal(pk3[:2 * half], pk0[:2 * half])
+    assert not np.array_equal(pk3[2 * half:], pk0[2 * half:])
