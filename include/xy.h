@@ -248,9 +248,12 @@ int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
 /* Picks each lattice's tile (kind and shape) by timing the candidates on
  * the device for sweeps of `n_metropolis` + `n_overrelax` passes (the spins,
  * counters and accept counts are saved and restored); the choice stays in
- * the context.  In XY_EXEC_PERSISTENT mode only block tiles of at most 256
- * threads are candidates: a persistent launch needs one tile kind for all
- * lattices (xy_sweep returns XY_ERR_ARG otherwise). */
+ * the context.  In XY_EXEC_PERSISTENT mode one tile kind serves every
+ * lattice (xy_sweep returns XY_ERR_ARG otherwise) and the block is as wide
+ * as the widest tile: for the march and the block kind and for tiles of at
+ * most 64, 128 and 256 threads, each lattice's best tile is found as above,
+ * and the six sets are timed in the persistent launch itself; the fastest
+ * is kept. */
 int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
 
 /* Device-side status word of the last persistent launch (0 = fine). */

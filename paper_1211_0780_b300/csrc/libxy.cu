@@ -1187,24 +1187,26 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
   XY_TRY(c, cudaEventCreate(&e0));
   XY_TRY(c, cudaEventCreate(&e1));
   int rc = XY_OK;
-  for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) {
+  const bool persistent = exec == XY_EXEC_PERSISTENT;
+  // Fastest tile of lattice i among kinds [k0, k1) and blocks of at most
+  // max_threads threads, timed on half-sweep launches.
+  auto search = [&](int i, int k0, int k1, int max_threads) {
     LatHost& h = c->lat[i];
+    const LatHost start = h;
     float best = 1e30f;
     LatHost best_h = h;
     const int zs[] = {1, 2, 4, 8, 16, 32};
-    const bool persistent = exec == XY_EXEC_PERSISTENT;
-    for (int kind = persistent ? kTileBlock : 0; kind < (persistent ? 2 : 3) && rc == XY_OK; ++kind) {
+    for (int kind = k0; kind < k1 && rc == XY_OK; ++kind) {
       for (int ty = 1; ty <= h.L && rc == XY_OK; ++ty) {
         if (h.L % ty != 0) continue;
         for (int tz : zs) {
           if (tz > h.L || h.L % tz != 0) continue;
-          LatHost cand = h;
+          LatHost cand = start;
           cand.kind = kind;
           cand.ty = ty;
           cand.tz = tz;
           if (kind != kTileBlock && tz < 2) continue;  // a march covers two planes or more
-          if (cand.threads() > c->max_block || cand.threads() < 32) continue;
-          if (persistent && cand.threads() > kPersistentBlockThreads) continue;
+          if (cand.threads() > max_threads || cand.threads() < 32) continue;
           if (cand.nyt() * cand.nzt() > h.part_cap || cand.smem() > 200 * 1024) continue;
           h = cand;
           if ((rc = sync_lats(c)) != XY_OK) break;
@@ -1218,12 +1220,14 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
             return r2;
           };
           if ((rc = run(1)) != XY_OK) break;
-          XY_TRY(c, cudaEventRecord(e0, c->stream));
+          if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = fail_cuda(c, cudaGetLastError(), "autotune"); break; }
           if ((rc = run(3)) != XY_OK) break;
-          XY_TRY(c, cudaEventRecord(e1, c->stream));
-          XY_TRY(c, cudaEventSynchronize(e1));
           float ms = 0.f;
-          XY_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+          if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+              cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+            rc = fail_cuda(c, cudaGetLastError(), "autotune");
+            break;
+          }
           if (ms < best) {
             best = ms;
             best_h = h;
@@ -1232,6 +1236,47 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
       }
     }
     h = best_h;
+  };
+  if (!persistent) {
+    for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, 0, 3, c->max_block);
+  } else {
+    // One tile kind and one block size serve every lattice of a persistent
+    // launch (the block is as wide as the widest tile): for each kind and
+    // each cap on the tile's threads (64, 128, 256), take each lattice's
+    // best tile under the cap, then time the persistent launch itself with
+    // each set and keep the fastest.
+    constexpr int kSets = 6;
+    std::vector<LatHost> sets[kSets];
+    const std::vector<LatHost> start = c->lat;
+    for (int q = 0; q < kSets && rc == XY_OK; ++q) {
+      const int kind = q < 3 ? kTileMarch : kTileBlock, cap = 64 << (q % 3);
+      c->lat = start;
+      for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, kind, kind + 1, cap);
+      sets[q] = c->lat;
+    }
+    float best = 1e30f;
+    int best_q = kSets - 1;
+    for (int q = 0; q < kSets && rc == XY_OK; ++q) {
+      c->lat = sets[q];
+      drop_graphs(c);
+      if ((rc = sync_lats(c)) != XY_OK) break;
+      if (persistent_sweeps(c, nM, nOR, 1, 0, 0) != XY_OK) {  // a set the persistent kernel cannot run
+        rc = c->sticky;
+        if (rc != XY_OK) break;
+        continue;
+      }
+      XY_TRY(c, cudaEventRecord(e0, c->stream));
+      if ((rc = persistent_sweeps(c, nM, nOR, 2, 0, 0)) != XY_OK) break;
+      XY_TRY(c, cudaEventRecord(e1, c->stream));
+      XY_TRY(c, cudaEventSynchronize(e1));
+      float ms = 0.f;
+      XY_TRY(c, cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        best_q = q;
+      }
+    }
+    if (rc == XY_OK) c->lat = sets[best_q];
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);

@@ -97,13 +97,15 @@ __device__ __forceinline__ bool due_dev(uint64_t s, int every) {
   return every > 0 && (s + 1) % static_cast<uint64_t>(every) == 0;
 }
 
-// Every lattice of a persistent launch uses tile kind KIND: the march kind
-// allows blocks of up to 512 threads; the block kind up to 256 threads with
-// at least three blocks resident per SM (its registers stay below 85).
+// Every lattice of a persistent launch uses tile kind KIND, with blocks of
+// at most 256 threads: the block kind with at least three blocks resident
+// per SM (its registers stay below 85); the march kind with its registers
+// unbounded below 255 (it holds three planes of its column and the next
+// plane's operands, and spills at 128).
 constexpr int kPersistentBlockThreads = 256;
 
 template <int KIND>
-__global__ void __launch_bounds__(KIND == kTileBlock ? kPersistentBlockThreads : 512, KIND == kTileBlock ? 3 : 1)
+__global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 3 : 1)
     k_persistent(PersistentArgs a) {
   extern __shared__ __align__(16) float sm[];
   unsigned long long nbar = 0;
