@@ -258,6 +258,20 @@ __global__ void k_mh_max_finish(int K, int nblk, const double* __restrict__ part
   kmax[k] = mx;
 }
 
+// Grid step (beta'_K-1 - beta'_0) / (K - 1), and whether the couplings of the
+// thread group starting at k0 sit on it to a few ulps (then the group steps
+// its weights by a per-sample factor instead of one exp per pair).
+__device__ __forceinline__ double grid_step(int K, const double* betap) {
+  return K > 1 ? (betap[K - 1] - betap[0]) / (K - 1) : 0.0;
+}
+__device__ __forceinline__ bool group_on_grid(int k0, int K, const double* betap, double step) {
+  if (step == 0.0 || k0 + 1 >= K) return false;
+  bool even = true;
+  for (int i = 1; i < kKT && k0 + i < K; ++i)
+    even = even && fabs(betap[k0 + i] - (betap[k0] + i * step)) <= 8.0 * 2.220446049250313e-16 * fabs(betap[k0 + i]);
+  return even;
+}
+
 // Sums pass: chunk partial sums of w x_j, w = exp(x_kt - max_k), x_j in
 // {1, e, e^2, m2, m2 e, m4, m4 e, c, c e, s2, s2 e}, e = E - Ebar (Ebar =
 // stats[0], the record mean); each thread owns kKT consecutive k.
@@ -267,11 +281,17 @@ __global__ void __launch_bounds__(kBlock) k_mh_sums(int64_t T, int64_t t_per_chu
                                                     const float* __restrict__ s2, int K,
                                                     const double* __restrict__ betap, const double* __restrict__ kmax,
                                                     const double* __restrict__ stats, double* __restrict__ sums) {
-  __shared__ double s_E[kChunk], s_l[kChunk], s_m2[kChunk], s_m4[kChunk], s_c[kChunk], s_s2[kChunk];
+  __shared__ double s_E[kChunk], s_l[kChunk], s_m2[kChunk], s_m4[kChunk], s_c[kChunk], s_s2[kChunk], s_rho[kChunk];
   const int chunk = blockIdx.y;
   const int64_t t0 = chunk * t_per_chunk, t1 = (t0 + t_per_chunk < T) ? t0 + t_per_chunk : T;
   const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * kKT;
   const double Ebar = stats[0];
+  // On the grid, coupling k0+i uses the shift max_k0 - i step Ebar, so that
+  // its weight is the first one times rho_t^i, rho_t = exp(-step (E_t -
+  // Ebar)) (evaluated once per sample by the block); the exponent stays
+  // below kKT |step| max |E - Ebar|.
+  const double step = grid_step(K, betap);
+  const bool even = k0 < K && group_on_grid(k0, K, betap, step);
   double b[kKT], mx[kKT];
   int nk = 0;
 #pragma unroll
@@ -297,15 +317,18 @@ __global__ void __launch_bounds__(kBlock) k_mh_sums(int64_t T, int64_t t_per_chu
       s_m4[j] = static_cast<double>(m4[t]);
       s_c[j] = static_cast<double>(c[t]) + static_cast<double>(c[T + t]) + static_cast<double>(c[2 * T + t]);
       s_s2[j] = static_cast<double>(s2[t]) + static_cast<double>(s2[T + t]) + static_cast<double>(s2[2 * T + t]);
+      s_rho[j] = exp(-step * (s_E[j] - Ebar));
     }
     __syncthreads();
     if (nk > 0) {
       for (int j = 0; j < n; ++j) {
         const double Et = s_E[j], e = Et - Ebar, lD = s_l[j];
         const double x2 = s_m2[j], x4 = s_m4[j], xc = s_c[j], xs = s_s2[j];
+        double w = exp(fma(-b[0], Et, -lD) - mx[0]);
+        const double rho = s_rho[j];
 #pragma unroll
         for (int i = 0; i < kKT; ++i) {
-          const double w = exp(fma(-b[i], Et, -lD) - mx[i]);
+          if (i > 0) w = even ? w * rho : exp(fma(-b[i], Et, -lD) - mx[i]);
           const double we = w * e;
           S[i][0] += w;
           S[i][1] += we;
@@ -365,7 +388,11 @@ __global__ void k_mh_finish(int K, int n_tchunks, const double* __restrict__ bet
   const double inv = 1.0 / S[0];
   const double me = S[1] * inv, mm2 = S[3] * inv, mm4 = S[5] * inv, mc = S[7] * inv, ms2 = S[9] * inv;
   const double bp = betap[k];
-  out[0 * K + k] = log(S[0]) + kmax[k];
+  // the shift the sums pass used for k (see k_mh_sums)
+  const int g0 = (k / kKT) * kKT;
+  const double step = grid_step(K, betap);
+  const double shift = group_on_grid(g0, K, betap, step) ? kmax[g0] - (k - g0) * step * stats[0] : kmax[k];
+  out[0 * K + k] = log(S[0]) + shift;
   out[1 * K + k] = stats[0] + me;
   out[2 * K + k] = mm2;
   out[3 * K + k] = mm4;
