@@ -494,10 +494,12 @@ def run_gpu(args):
     half = L_MAIN ** 3 // 2
     hbm, src = measured_peaks()
     ach = BYTES_PER_UPDATE * half / (ms_or * 1e-3) / 1e9
-    # DRAM bytes per launch from the committed ncu capture, valid only for the
-    # tile that capture used (the kernel is otherwise the same code)
+    # DRAM bytes per launch from the committed ncu capture of this tile's
+    # over-relaxation kernel (valid only for the tile that capture used)
     traffic, traffic_note = None, "no ncu capture for this tile"
-    prof = os.path.join(ROOT, "profiles", "overrelax_L160_march8x8_traffic.txt")
+    kind_names = {0: "march", 1: "block", 2: "stream", 3: "direct"}
+    tile_name = f"{kind_names.get(tile[2], tile[2])}{tile[0]}x{tile[1]}"
+    prof = os.path.join(ROOT, "profiles", f"overrelax_L160_{tile_name}_traffic.txt")
     if os.path.exists(prof):
         kv = {}
         with open(prof) as f:
@@ -507,12 +509,13 @@ def run_gpu(args):
                     kv[k.strip()] = v.strip()
         if kv.get("tile") == ",".join(str(v) for v in tile):
             traffic = int(kv["dram_bytes_per_launch"])
-            traffic_note = ("cold-cache ncu capture (profiles/overrelax_L160_march8x8_ncu.md): the whole "
+            traffic_note = (f"cold-cache ncu capture (profiles/overrelax_L160_{tile_name}_ncu.md): the whole "
                             "(cos, sin) state read once, 8 B per site against the 4 B per site of the "
                             "12 B/update angle figure")
     roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
                 "traffic": traffic, "traffic_note": traffic_note,
-                "kernel": "k_half<over-relaxation>, 160^3 half-sweep",
+                "kernel": ("k_half_direct" if tile[2] == 3 else "k_half") + "<over-relaxation>, 160^3 half-sweep, "
+                          f"{tile_name} tile",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
                 "note": "12 B/update algorithmic; lattice state (cos, sin) is L2-resident (32.8 MB < 126 MB)"}
     kernels = {"overrelax_half_ms": ms_or, "metropolis_half_ms": ms_met,

@@ -237,18 +237,24 @@ int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
  * the tile reads (the other colour's rows with their y halo, the own
  * colour's rows) copied ahead into a ring of shared-memory stages by bulk
  * asynchronous copies (TMA); not run by XY_EXEC_PERSISTENT, whose blocks
- * write planes other blocks read within one launch.  xy_set_tile checks 1 <= ty, tz <= L, the block size against
- * the kernels' limit (512 threads at their register use on sm_103a), tz <=
- * 64 for kind 1, and that the tile count fits the partial-sum area
- * (ceil(L/ty) ceil(L/tz) <= L^2/4).  Spins do not depend on the tile (the
- * lattice sums only through FP64 summation order). */
+ * write planes other blocks read within one launch.  kind 3 (direct): the
+ * march's thread layout and plane march without shared memory or block
+ * barriers: each thread loads its y-neighbour rows and x-halo element
+ * itself through the L1 cache, one plane ahead; not run by
+ * XY_EXEC_PERSISTENT either (L1 does not see writes made within the same
+ * launch).  xy_set_tile checks 1 <= ty, tz <= L, the block size against
+ * the kernels' limit (512 threads at their register use on sm_103a; 240
+ * for kind 3), tz <= 64 for kind 1, and that the tile count fits the
+ * partial-sum area (ceil(L/ty) ceil(L/tz) <= L^2/4).  Spins do not depend
+ * on the tile (the lattice sums only through FP64 summation order). */
 int xy_set_tile(xy_ctx *ctx, int lattice, int kind, int ty, int tz);
 int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
 
 /* Picks each lattice's tile (kind and shape) by timing the candidates on
  * the device for sweeps of `n_metropolis` + `n_overrelax` passes (the spins,
  * counters and accept counts are saved and restored); the choice stays in
- * the context.  In XY_EXEC_PERSISTENT mode one tile kind serves every
+ * the context.  Outside XY_EXEC_PERSISTENT every kind (0-3) is a
+ * candidate.  In XY_EXEC_PERSISTENT mode one tile kind serves every
  * lattice (xy_sweep returns XY_ERR_ARG otherwise) and the block is as wide
  * as the widest tile: for the march and the block kind and for tiles of at
  * most 64, 128 and 256 threads, each lattice's best tile is found as above,

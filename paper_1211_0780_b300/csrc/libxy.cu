@@ -30,7 +30,7 @@ int conv_blocks(long long n) { return static_cast<int>(std::min<long long>((n + 
 
 struct LatHost {
   int L, R, slot0;
-  int kind;  // kTileMarch, kTileBlock or kTileStream
+  int kind;  // kTileMarch, kTileBlock, kTileStream or kTileDirect
   int ty, tz;
   size_t spin_off;  // floats from the spin base (2N per slot)
   int part0;         // first partial slot
@@ -175,6 +175,12 @@ namespace {
 
 thread_local char g_last_cuda_error[256] = {0};
 
+// Threads a tile of this kind may have: the kTileDirect kernels are compiled
+// for smaller blocks than the others.
+int kind_max_threads(const xy_ctx* c, int kind) {
+  return kind == kTileDirect ? std::min(c->max_block, kDirectMaxThreads) : c->max_block;
+}
+
 int fail_cuda(xy_ctx* c, cudaError_t e, const char* what) {
   std::snprintf(g_last_cuda_error, sizeof g_last_cuda_error, "%s: %s", what, cudaGetErrorString(e));
   if (c) c->sticky = XY_ERR_CUDA;
@@ -265,6 +271,11 @@ cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st
                                            : dim3(h.L / 8, h.ty);
   const int smem = h.smem();
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
+  if (KIND == kTileDirect) {
+    if (MODE == kMeasureOnly) return launch_chained(k_half_direct<kMeasureOnly, true>, grid, block, smem, st, d, colour, pp);
+    if (pp.measure && colour == 1) return launch_chained(k_half_direct<M, true>, grid, block, smem, st, d, colour, pp);
+    return launch_chained(k_half_direct<M, false>, grid, block, smem, st, d, colour, pp);
+  }
   if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);
   if (pp.measure && colour == 1) return launch_chained(k_half<M, true, KIND>, grid, block, smem, st, d, colour, pp);
   return launch_chained(k_half<M, false, KIND>, grid, block, smem, st, d, colour, pp);
@@ -276,6 +287,7 @@ int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams&
   const Lattice d = c->dev_lat(i);
   const cudaError_t e = h.kind == kTileBlock    ? launch_half_kind<MODE, kTileBlock>(h, d, st, colour, pp)
                        : h.kind == kTileStream ? launch_half_kind<MODE, kTileStream>(h, d, st, colour, pp)
+                       : h.kind == kTileDirect ? launch_half_kind<MODE, kTileDirect>(h, d, st, colour, pp)
                                                : launch_half_kind<MODE, kTileMarch>(h, d, st, colour, pp);
   XY_TRY(c, e);
   return XY_OK;
@@ -545,6 +557,20 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncGetAttributes"));
     c->max_block = std::min(c->max_block, fa.maxThreadsPerBlock);
+  }
+  // The kTileDirect kernels: their own block limit (kDirectMaxThreads), no
+  // tile in shared memory.
+  const void* direct_kernels[5] = {
+      reinterpret_cast<const void*>(k_half_direct<kMetropolis, false>),
+      reinterpret_cast<const void*>(k_half_direct<kMetropolis, true>),
+      reinterpret_cast<const void*>(k_half_direct<kOverrelax, false>),
+      reinterpret_cast<const void*>(k_half_direct<kOverrelax, true>),
+      reinterpret_cast<const void*>(k_half_direct<kMeasureOnly, true>)};
+  for (const void* fn : direct_kernels) {
+    cudaFuncAttributes fa{};
+    e = cudaFuncGetAttributes(&fa, fn);
+    if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncGetAttributes"));
+    if (fa.maxThreadsPerBlock < kDirectMaxThreads) return bail(XY_ERR_CUDA);
   }
   for (LatHost& h : c->lat)
     while (h.threads() > c->max_block && (h.ty > 1 || h.tz > 1)) {
@@ -924,12 +950,12 @@ int xy_debug_draws(xy_ctx* c, int slot, int colour, int tag, uint64_t count, uin
 int xy_set_tile(xy_ctx* c, int lattice, int kind, int ty, int tz) {
   XY_ENTER(c);
   if (lattice < 0 || lattice >= c->n_lat) return XY_ERR_ARG;
-  if (kind != kTileMarch && kind != kTileBlock && kind != kTileStream) return XY_ERR_ARG;
+  if (kind != kTileMarch && kind != kTileBlock && kind != kTileStream && kind != kTileDirect) return XY_ERR_ARG;
   LatHost h = c->lat[lattice];
   h.kind = kind;
   h.ty = ty;
   h.tz = tz;
-  if (ty < 1 || tz < 1 || ty > h.L || tz > h.L || h.threads() > c->max_block) return XY_ERR_ARG;
+  if (ty < 1 || tz < 1 || ty > h.L || tz > h.L || h.threads() > kind_max_threads(c, kind)) return XY_ERR_ARG;
   if (kind == kTileBlock && tz > 64) return XY_ERR_ARG;  // block z extent
   if (h.nyt() * h.nzt() > h.part_cap) return XY_ERR_ARG;
   if (h.smem() > 200 * 1024) return XY_ERR_ARG;
@@ -972,7 +998,7 @@ int build_plan(xy_ctx* c) {
     if (h.kind != kind) return XY_ERR_ARG;  // one tile kind per persistent launch
     // stream tiles copy planes with TMA, which does not see what other blocks
     // of the same launch wrote
-    if (h.kind == kTileStream) return XY_ERR_ARG;
+    if (h.kind == kTileStream || h.kind == kTileDirect) return XY_ERR_ARG;
     B = std::max(B, h.threads());
     smem = std::max(smem, h.smem());
   }
@@ -1206,7 +1232,7 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
           cand.ty = ty;
           cand.tz = tz;
           if (kind != kTileBlock && tz < 2) continue;  // a march covers two planes or more
-          if (cand.threads() > max_threads || cand.threads() < 32) continue;
+          if (cand.threads() > std::min(max_threads, kind_max_threads(c, kind)) || cand.threads() < 32) continue;
           if (cand.nyt() * cand.nzt() > h.part_cap || cand.smem() > 200 * 1024) continue;
           h = cand;
           if ((rc = sync_lats(c)) != XY_OK) break;
@@ -1238,7 +1264,7 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
     h = best_h;
   };
   if (!persistent) {
-    for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, 0, 3, c->max_block);
+    for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, 0, 4, c->max_block);
   } else {
     // One tile kind and one block size serve every lattice of a persistent
     // launch (the block is as wide as the widest tile): for each kind and

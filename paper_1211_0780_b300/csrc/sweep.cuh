@@ -61,7 +61,19 @@ enum Mode : int { kMetropolis = 0, kOverrelax = 1, kMeasureOnly = 2 };
 // brought into a ring of shared-memory stages by bulk asynchronous copies
 // (TMA) that run ahead of the computation; threads only read shared memory
 // and store their results.
-enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2 };
+// kTileDirect: the march of kTileMarch without shared memory and without a
+// block barrier: each thread loads its y-neighbour rows and its x-halo
+// element itself, through the L1 cache (the rows it reads are the rows its
+// neighbouring threads load for their own columns), one plane ahead, so
+// every warp marches on its own.  Per-launch only (the persistent kernel's
+// blocks write within one launch, which L1 does not see).
+enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2, kTileDirect = 3 };
+
+// Threads of a kTileDirect block at most, and the registers a thread of its
+// kernel may use: three blocks of 160 threads (a 160^3 tile of 8 rows) stay
+// resident per SM.
+constexpr int kDirectMaxThreads = 240;
+constexpr int kDirectMaxRegs = 136;
 
 // Stages of the kTileStream ring: planes z-1, z, z+1 in use, the rest in
 // flight.
@@ -127,9 +139,12 @@ __host__ __device__ inline int tile_threads(int kind, int L, int ty, int tz) {
          : kind == kTileStream ? 32 * (stream_compute_warps(L, ty) + 1)
                                : (L / 8) * ty;
 }
+// kTileDirect keeps no tile in shared memory (only the reduction area).
 __host__ __device__ inline int tile_floats(int kind, int L, int ty, int tz) {
-  return kind == kTileBlock ? block_tile_floats(L, ty, tz)
-                            : (kind == kTileStream ? stream_tile_floats(L, ty) : tile_plane_floats(L, ty));
+  return kind == kTileBlock    ? block_tile_floats(L, ty, tz)
+         : kind == kTileStream ? stream_tile_floats(L, ty)
+         : kind == kTileDirect ? 0
+                               : tile_plane_floats(L, ty);
 }
 __host__ __device__ inline int tile_bytes(int kind, int L, int ty, int tz) {
   return tile_floats(kind, L, ty, tz) * 4 + kReduceBytes;
@@ -461,6 +476,125 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
     step(IC<1>{}, pb, pc, pa, i + 1);
     if (i + 2 >= TZa) break;
     step(IC<2>{}, pc, pa, pb, i + 2);
+  }
+  if (MEAS) sums.export_to(acc_out);
+}
+
+// The 4 spins of one thread's row segment through L1 (other-colour reads of
+// kTileDirect).  The other colour is not written during a half-sweep
+// launch, and a launch starts reading only after its predecessor has
+// completed and its writes are visible (griddepcontrol.wait), so no cached
+// line is stale.
+__device__ __forceinline__ Spins4 ld_spins_l1(const float* p, uint32_t half) {
+  Spins4 v;
+  v.c = __ldca(reinterpret_cast<const float4*>(p));
+  v.s = __ldca(reinterpret_cast<const float4*>(p + half));
+  return v;
+}
+
+// One tile of one half-sweep, kTileDirect: the thread layout and the plane
+// march of tile_pass (planes z-1, z, z+1 of the thread's column rotate
+// through registers), but the y-neighbour rows (y-1, y+1) and the x-halo
+// element of plane z are loaded by the thread itself, through L1, while it
+// updates plane z-1, and nothing is shared through shared memory: no block
+// barrier, every warp marches at its own pace.  Threads with ty >= the
+// tile's rows return at once.  acc_out / n_acc as tile_pass.
+template <int MODE, bool MEAS>
+__device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, int zt, int colour, int tx,
+                                            int ty, const PassParams& pp, float* acc_out, uint32_t& n_acc) {
+  static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
+  const int L = lat.L;
+  const int H = L >> 1;
+  const uint32_t PS = static_cast<uint32_t>(H) * static_cast<uint32_t>(L);  // plane stride
+  const uint32_t half = PS * static_cast<uint32_t>(L);                       // N / 2
+  const int y0 = yt * lat.ty, z0 = zt * lat.tz;
+  const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
+  if (ty >= TYa) return;
+  const int y = y0 + ty;
+  float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  float* const own = slot + colour * (2 * half);  // cos; sin at + half
+  const float* const oth = slot + (colour ^ 1) * (2 * half);
+  const int ym = (y == 0 ? L : y) - 1;  // periodic y neighbours of this row
+  const int yp = (y + 1 == L) ? 0 : y + 1;
+  const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
+  const uint32_t offym = static_cast<uint32_t>(H * ym + 4 * tx);
+  const uint32_t offyp = static_cast<uint32_t>(H * yp + 4 * tx);
+  // x-halo element of this thread's row: k = 4 tx - 1 (s = 0) or 4 tx + 4 (s = 1)
+  const uint32_t offh0 = static_cast<uint32_t>(H * y + ((tx == 0) ? H - 1 : 4 * tx - 1));
+  const uint32_t offh1 = static_cast<uint32_t>(H * y + ((4 * tx + 4 == H) ? 0 : 4 * tx + 4));
+
+  float beta = 0.f;
+  uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
+  if (MODE == kMetropolis) {
+    beta = __ldcg(pp.beta_slot + lat.slot0 + r);
+    tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) |
+           kTagMet;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    mlo = static_cast<uint32_t>(mp);
+    mhi = static_cast<uint32_t>(mp >> 32);
+  }
+  SumAcc<MEAS> sums;
+
+  // Registers: planes z-1, z, z+1 of the column (rotating), and the operands
+  // of the next plane, loaded one plane ahead.
+  Spins4 pa, pb, pc{}, nx_oth, nx_own, nx_ym, nx_yp;
+  float nx_hc, nx_hs;
+  {
+    const uint32_t zb = static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS;
+    const uint32_t zz = static_cast<uint32_t>(z0) * PS;
+    const uint32_t z1 = static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS;
+    pa = ld_spins_l1(oth + offy + zb, half);
+    pb = ld_spins_l1(oth + offy + zz, half);
+    nx_oth = ld_spins_l1(oth + offy + z1, half);
+    nx_own = ld_spins(own + offy + zz, half);
+    nx_ym = ld_spins_l1(oth + offym + zz, half);
+    nx_yp = ld_spins_l1(oth + offyp + zz, half);
+    const uint32_t oh = (((y + z0 + colour) & 1) ? offh1 : offh0) + zz;
+    nx_hc = __ldca(oth + oh);
+    nx_hs = __ldca(oth + oh + half);
+  }
+
+  // One plane: zm, zc = planes z-1, z; zn receives plane z+1.
+  auto step = [&](Spins4& zm, Spins4& zc, Spins4& zn, int i) {
+    const int z = z0 + i;
+    const Spins4 t_own = nx_own, ysm = nx_ym, ysp = nx_yp;
+    const float hc = nx_hc, hs = nx_hs;
+    zn = nx_oth;
+    if (i + 1 < TZa) {
+      // the next plane's operands
+      const uint32_t pz1 = static_cast<uint32_t>(z + 1) * PS;
+      const uint32_t pz2 = static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS;
+      nx_oth = ld_spins_l1(oth + offy + pz2, half);
+      nx_own = ld_spins(own + offy + pz1, half);
+      nx_ym = ld_spins_l1(oth + offym + pz1, half);
+      nx_yp = ld_spins_l1(oth + offyp + pz1, half);
+      const uint32_t oh = (((y + z + 1 + colour) & 1) ? offh1 : offh0) + pz1;
+      nx_hc = __ldca(oth + oh);
+      nx_hs = __ldca(oth + oh + half);
+    }
+    const int s = (y + z + colour) & 1;
+    const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
+    uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+    if (MODE == kMetropolis) {
+      const uint32_t q0 = offz >> 1;
+      w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+      w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+    }
+    float stepv[kNumSums];
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
+    Spins4 nw;
+    update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
+    if (MEAS) sums.add_plane(stepv);
+    if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+  };
+
+  for (int i = 0; i < TZa; i += 3) {
+    step(pa, pb, pc, i);
+    if (i + 1 >= TZa) break;
+    step(pb, pc, pa, i + 1);
+    if (i + 2 >= TZa) break;
+    step(pc, pa, pb, i + 2);
   }
   if (MEAS) sums.export_to(acc_out);
 }

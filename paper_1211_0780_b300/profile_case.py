@@ -21,7 +21,8 @@ def main():
     ap.add_argument("--R", type=int, default=1)
     ap.add_argument("--ty", type=int, default=0)
     ap.add_argument("--tz", type=int, default=0)
-    ap.add_argument("--kind", type=int, default=1, help="0 = march tile, 1 = block tile")
+    ap.add_argument("--kind", type=int, default=1,
+                    help="0 = march, 1 = block, 2 = stream, 3 = direct tile")
     ap.add_argument("--mode", default="or", choices=["or", "met", "meas", "sweep", "reweight"])
     ap.add_argument("--T", type=int, default=200000, help="samples of the reweight mode's series")
     ap.add_argument("--K", type=int, default=4096, help="couplings of the reweight mode")

@@ -21,7 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libxy.so")
 XY_OK, XY_ERR_ARG, XY_ERR_CUDA, XY_ERR_TIMEOUT, XY_ERR_STATE, XY_ERR_NOMEM = 0, -1, -2, -3, -4, -5
 EXEC_PLAIN, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2
 TAG_INIT, TAG_MET, TAG_PT = 1, 2, 3
-TILE_MARCH, TILE_BLOCK, TILE_STREAM = 0, 1, 2
+TILE_MARCH, TILE_BLOCK, TILE_STREAM, TILE_DIRECT = 0, 1, 2, 3
 
 
 class XYError(RuntimeError):

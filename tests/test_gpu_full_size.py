@@ -58,19 +58,20 @@ def check_met_half(before32, after32, beta, slot, mpass, colour):
     return int(close.sum())
 
 
-def test_L160_march_tile_graph():
-    """160^3, tile 8 x 8 march, CUDA graph, 1 + 5 passes: the graph's sweep
-    equals the same half-sweeps issued one by one, and each kind of
-    half-sweep and the lattice sums agree with the oracle on the full
-    lattice."""
+@pytest.mark.parametrize("kind", [0, 3])
+def test_L160_tile_graph(kind):
+    """160^3, tile 8 x 8 (march, and direct: the bench's launch shape),
+    CUDA graph, 1 + 5 passes: the graph's sweep equals the same half-sweeps
+    issued one by one, and each kind of half-sweep and the lattice sums
+    agree with the oracle on the full lattice."""
     from paper_1211_0780_b300 import xy
     L, beta = 160, 0.4542
     a = xy.Simulation(L, 1, [beta], SEED, series_capacity=16)
-    a.set_tile(0, 8, 8, 0)
+    a.set_tile(0, 8, 8, kind)
     a.set_exec(xy.EXEC_GRAPH)
     a.sweep(1, 5, 2, measure_every=1)
     b = xy.Simulation(L, 1, [beta], SEED, series_capacity=16)
-    b.set_tile(0, 8, 8, 0)
+    b.set_tile(0, 8, 8, kind)
     _, perm, ctr = a.get_state()
     b.set_packed(a.get_packed())
     b.set_state(None, perm, ctr)

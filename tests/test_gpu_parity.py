@@ -100,13 +100,14 @@ def test_state_roundtrip_and_layout():
 
 # ---------------------------------------------------------------- half-sweeps
 
-MARCH, BLOCK, STREAM = 0, 1, 2
+MARCH, BLOCK, STREAM, DIRECT = 0, 1, 2, 3
 
 
 @pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (40, (3, 16, MARCH)),
                                     (32, (32, 32, MARCH)), (24, (3, 5, BLOCK)), (40, (8, 4, BLOCK)),
                                     (16, (16, 16, BLOCK)), (24, (5, 7, STREAM)), (40, (3, 16, STREAM)),
-                                    (16, (16, 16, STREAM)), (8, (1, 8, STREAM))])
+                                    (16, (16, 16, STREAM)), (8, (1, 8, STREAM)), (24, (5, 7, DIRECT)),
+                                    (40, (3, 16, DIRECT)), (16, (16, 16, DIRECT)), (8, (1, 8, DIRECT))])
 def test_metropolis_half_parity(L, tile):
     """One Metropolis half-sweep of each colour from the same FP32 state."""
     beta = 0.4542
@@ -148,7 +149,7 @@ OR_A, OR_B = 1.5e-5, 2e-6
 
 @pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (40, (3, 16, MARCH)),
                                     (24, (5, 7, BLOCK)), (40, (8, 3, BLOCK)), (24, (5, 7, STREAM)),
-                                    (40, (8, 40, STREAM))])
+                                    (40, (8, 40, STREAM)), (24, (5, 7, DIRECT)), (40, (8, 40, DIRECT))])
 def test_overrelax_half_parity(L, tile):
     """One over-relaxation half-sweep (Eq. 2) of each colour from the same
     FP32 state: every site within the conditioning bound A/|h| + B (no
@@ -229,7 +230,8 @@ def test_measure_plane_wave_closed_form():
 
 
 @pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (48, (7, 9, MARCH)),
-                                    (24, (5, 7, BLOCK)), (48, (6, 5, BLOCK)), (48, (7, 9, STREAM))])
+                                    (24, (5, 7, BLOCK)), (48, (6, 5, BLOCK)), (48, (7, 9, STREAM)),
+                                    (48, (7, 9, DIRECT))])
 def test_measure_parity(L, tile):
     s = sim(L, 2, [0.40, 0.4542])
     if tile:
@@ -293,6 +295,7 @@ def test_one_sweep_from_shared_state(nM, nOR):
     and a two-Metropolis variant, half-sweep by half-sweep."""
     check_sweep_by_half_sweeps(16, 0.4542, nM, nOR)
     check_sweep_by_half_sweeps(16, 0.4542, nM, nOR, tile=(4, 8, MARCH))
+    check_sweep_by_half_sweeps(16, 0.4542, nM, nOR, tile=(4, 8, DIRECT))
 
 
 def test_counters_and_series_records():
@@ -338,7 +341,8 @@ def test_tile_shapes_give_identical_angles():
     res = []
     for tile in ((16, 16, MARCH), (4, 8, MARCH), (5, 3, MARCH), (2, 4, MARCH), (8, 8, BLOCK),
                  (5, 4, BLOCK), (40, 1, BLOCK), (1, 40, BLOCK), (8, 8, STREAM), (5, 3, STREAM),
-                 (40, 2, STREAM), (1, 40, STREAM)):
+                 (40, 2, STREAM), (1, 40, STREAM), (8, 8, DIRECT), (5, 3, DIRECT), (40, 2, DIRECT),
+                 (1, 40, DIRECT)):
         s = sim(40, 1, [0.4542])
         s.set_tile(0, *tile)
         s.sweep(1, 3, 4)
@@ -377,6 +381,39 @@ def test_pt_swap_parity():
             decided += 1
         s.sweep(1, 1, 2)
     assert decided >= 10
+
+
+def test_direct_tile_matches_march_tile_bit_for_bit():
+    """The direct tile (neighbours through L1, no block barrier) and the
+    march tile of the same shape give the same angles, permutations,
+    records and accept counts, bit for bit, over many chained launches of
+    plain and graph execution (a stale L1 line would show here), and the
+    persistent launch refuses the direct tile."""
+    from paper_1211_0780_b300 import xy
+    Ls, Rs = [16, 24], [4, 3]
+    betas = [0.40, 0.43, 0.46, 0.49, 0.44, 0.45, 0.46]
+    outs = []
+    for kind, mode in ((MARCH, xy.EXEC_PLAIN), (DIRECT, xy.EXEC_PLAIN), (DIRECT, xy.EXEC_GRAPH)):
+        s = sim(Ls, Rs, betas, series_capacity=64)
+        s.set_tile(0, 4, 6, kind)
+        s.set_tile(1, 3, 8, kind)
+        s.set_exec(mode)
+        s.sweep(1, 2, 9, measure_every=3, pt_swap_every=1)
+        s.sweep(2, 1, 7, measure_every=3, pt_swap_every=2)
+        a, p, c = s.get_state()
+        outs.append((a, p, c, s.read_series(), s.accepts(), s.get_packed()))
+    for other in outs[1:]:
+        assert np.array_equal(outs[0][5], other[5])
+        assert np.array_equal(outs[0][1], other[1])
+        assert np.array_equal(outs[0][2], other[2])
+        assert np.array_equal(outs[0][3], other[3])
+        assert np.array_equal(outs[0][4][0], other[4][0])
+        assert np.array_equal(outs[0][4][1], other[4][1])
+    s = sim(16, 2, [0.40, 0.45])
+    s.set_tile(0, 4, 4, DIRECT)
+    s.set_exec(xy.EXEC_PERSISTENT)
+    with pytest.raises(xy.XYError):
+        s.sweep(1, 1, 1)
 
 
 def test_barrier_timeout_reports_status_without_hanging():
@@ -445,7 +482,7 @@ def test_checkpoint_resume_is_bit_exact():
     assert np.array_equal(back[1], perm) and np.array_equal(back[2], ctr)
 
 
-@pytest.mark.parametrize("tile", [(8, 8, MARCH), (4, 2, BLOCK), (8, 4, STREAM)])
+@pytest.mark.parametrize("tile", [(8, 8, MARCH), (4, 2, BLOCK), (8, 4, STREAM), (8, 8, DIRECT)])
 def test_zero_field_degenerate_case(tile):
     """Where the six neighbours cancel exactly (h = 0: opposite unit vectors
     (1, 0) and (-1, 0) along each axis, written into the device state
