@@ -71,7 +71,8 @@ enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2, kTileDire
 
 // Threads of a kTileDirect block at most, and the registers a thread of its
 // kernel may use: three blocks of 160 threads (a 160^3 tile of 8 rows) stay
-// resident per SM.
+// resident per SM.  (The measuring variants spill a few words at this
+// limit; measured on B300 that is still faster than two blocks per SM.)
 constexpr int kDirectMaxThreads = 240;
 constexpr int kDirectMaxRegs = 136;
 
@@ -493,11 +494,11 @@ __device__ __forceinline__ Spins4 ld_spins_l1(const float* p, uint32_t half) {
 }
 
 // One tile of one half-sweep, kTileDirect: the thread layout and the plane
-// march of tile_pass (planes z-1, z, z+1 of the thread's column rotate
-// through registers), but the y-neighbour rows (y-1, y+1) and the x-halo
-// element of plane z are loaded by the thread itself, through L1, while it
-// updates plane z-1, and nothing is shared through shared memory: no block
-// barrier, every warp marches at its own pace.  Threads with ty >= the
+// march of tile_pass (planes of the thread's column rotate through
+// registers), but the y-neighbour rows (y-1, y+1) and the x-halo element of
+// plane z are loaded by the thread itself, through L1, while it updates
+// plane z-1, and nothing is shared through shared memory: no block barrier,
+// every warp marches at its own pace.  Threads with ty >= the
 // tile's rows return at once.  acc_out / n_acc as tile_pass.
 template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, int zt, int colour, int tx,
@@ -535,42 +536,40 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   }
   SumAcc<MEAS> sums;
 
-  // Registers: planes z-1, z, z+1 of the column (rotating), and the operands
-  // of the next plane, loaded one plane ahead.
-  Spins4 pa, pb, pc{}, nx_oth, nx_own, nx_ym, nx_yp;
-  float nx_hc, nx_hs;
+  // Registers: four other-colour planes of the column rotate (z-1, z, z+1 in
+  // use, z+2 being loaded), and two sets of the other operands alternate
+  // (this plane's, the next plane's, loaded one plane ahead); the plane loop
+  // is unrolled four times so that every load lands in a free register and
+  // nothing is copied.
+  struct Operands {
+    Spins4 own, ym, yp;  // own spins; other colour's rows y-1, y+1
+    float hc, hs;        // x-halo element
+  };
+  Spins4 P0, P1, P2, P3{};
+  Operands A, B;
+  auto load_operands = [&](Operands& o, int z, uint32_t pz) {
+    o.own = ld_spins(own + offy + pz, half);
+    o.ym = ld_spins_l1(oth + offym + pz, half);
+    o.yp = ld_spins_l1(oth + offyp + pz, half);
+    const uint32_t oh = (((y + z + colour) & 1) ? offh1 : offh0) + pz;
+    o.hc = __ldca(oth + oh);
+    o.hs = __ldca(oth + oh + half);
+  };
   {
-    const uint32_t zb = static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS;
     const uint32_t zz = static_cast<uint32_t>(z0) * PS;
-    const uint32_t z1 = static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS;
-    pa = ld_spins_l1(oth + offy + zb, half);
-    pb = ld_spins_l1(oth + offy + zz, half);
-    nx_oth = ld_spins_l1(oth + offy + z1, half);
-    nx_own = ld_spins(own + offy + zz, half);
-    nx_ym = ld_spins_l1(oth + offym + zz, half);
-    nx_yp = ld_spins_l1(oth + offyp + zz, half);
-    const uint32_t oh = (((y + z0 + colour) & 1) ? offh1 : offh0) + zz;
-    nx_hc = __ldca(oth + oh);
-    nx_hs = __ldca(oth + oh + half);
+    P3 = ld_spins_l1(oth + offy + static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS, half);
+    P0 = ld_spins_l1(oth + offy + zz, half);
+    P1 = ld_spins_l1(oth + offy + static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS, half);
+    load_operands(A, z0, zz);
   }
 
-  // One plane: zm, zc = planes z-1, z; zn receives plane z+1.
-  auto step = [&](Spins4& zm, Spins4& zc, Spins4& zn, int i) {
+  // One plane: zm, zc, zn = planes z-1, z, z+1; zf receives plane z+2; cur
+  // holds this plane's operands, nxt receives the next plane's.
+  auto step = [&](Spins4& zm, Spins4& zc, Spins4& zn, Spins4& zf, Operands& cur, Operands& nxt, int i) {
     const int z = z0 + i;
-    const Spins4 t_own = nx_own, ysm = nx_ym, ysp = nx_yp;
-    const float hc = nx_hc, hs = nx_hs;
-    zn = nx_oth;
     if (i + 1 < TZa) {
-      // the next plane's operands
-      const uint32_t pz1 = static_cast<uint32_t>(z + 1) * PS;
-      const uint32_t pz2 = static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS;
-      nx_oth = ld_spins_l1(oth + offy + pz2, half);
-      nx_own = ld_spins(own + offy + pz1, half);
-      nx_ym = ld_spins_l1(oth + offym + pz1, half);
-      nx_yp = ld_spins_l1(oth + offyp + pz1, half);
-      const uint32_t oh = (((y + z + 1 + colour) & 1) ? offh1 : offh0) + pz1;
-      nx_hc = __ldca(oth + oh);
-      nx_hs = __ldca(oth + oh + half);
+      zf = ld_spins_l1(oth + offy + static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS, half);
+      load_operands(nxt, z + 1, static_cast<uint32_t>(z + 1) * PS);
     }
     const int s = (y + z + colour) & 1;
     const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
@@ -584,17 +583,19 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
 #pragma unroll
     for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
     Spins4 nw;
-    update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
+    update4<MODE, MEAS>(zc, cur.hc, cur.hs, s, cur.ym, cur.yp, zm, zn, cur.own, w0, w1, beta, nw, n_acc, stepv);
     if (MEAS) sums.add_plane(stepv);
     if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
   };
 
-  for (int i = 0; i < TZa; i += 3) {
-    step(pa, pb, pc, i);
+  for (int i = 0; i < TZa; i += 4) {
+    step(P3, P0, P1, P2, A, B, i);
     if (i + 1 >= TZa) break;
-    step(pb, pc, pa, i + 1);
+    step(P0, P1, P2, P3, B, A, i + 1);
     if (i + 2 >= TZa) break;
-    step(pc, pa, pb, i + 2);
+    step(P1, P2, P3, P0, A, B, i + 2);
+    if (i + 3 >= TZa) break;
+    step(P2, P3, P0, P1, B, A, i + 3);
   }
   if (MEAS) sums.export_to(acc_out);
 }
