@@ -70,11 +70,14 @@ enum Mode : int { kMetropolis = 0, kOverrelax = 1, kMeasureOnly = 2 };
 enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2, kTileDirect = 3 };
 
 // Threads of a kTileDirect block at most, and the registers a thread of its
-// kernel may use: three blocks of 160 threads (a 160^3 tile of 8 rows) stay
-// resident per SM.  (The measuring variants spill a few words at this
-// limit; measured on B300 that is still faster than two blocks per SM.)
+// kernel may use.  Each of an SM's four schedulers holds 16K registers, so
+// at 128 registers a thread it keeps four warps and three blocks of 160
+// threads (a 160^3 tile of 8 rows) stay resident per SM; at 129-136 only
+// three warps per scheduler and two blocks fit.  (The measuring variants
+// spill some words at this limit; measured on B300 that is faster than two
+// blocks per SM.)
 constexpr int kDirectMaxThreads = 240;
-constexpr int kDirectMaxRegs = 136;
+constexpr int kDirectMaxRegs = 128;
 
 // Stages of the kTileStream ring: planes z-1, z, z+1 in use, the rest in
 // flight.
