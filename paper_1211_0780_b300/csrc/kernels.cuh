@@ -101,7 +101,7 @@ __global__ void __launch_bounds__(512) k_half(Lattice lat, int colour, PassParam
 // slot, R), block (L/8, ty); shared memory only for the reduction of the
 // measuring variant.
 template <int MODE, bool MEAS>
-__global__ void __maxnreg__(kDirectMaxRegs) k_half_direct(Lattice lat, int colour, PassParams pp) {
+__global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDirectMaxRegs) k_half_direct(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   chain_wait_and_release();
   const int r = blockIdx.y;
