@@ -152,6 +152,18 @@ def oracle_rate(seconds: float, threads: int | None = None):
     return upd / (elapsed * 1e9), n, done
 
 
+def cpu_model() -> str:
+    """The host CPU's model name (Linux /proc/cpuinfo), or "unknown"."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def run_reference(args):
     world, rank, _ = dist_env()
     if rank != 0:
@@ -176,11 +188,12 @@ def run_reference(args):
     sample = f"{args.steps} sweeps (1 Metropolis + 5 over-relaxation passes) of the 160^3 lattice, one per step"
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
-        "device": f"host CPU, {n} threads (the FP64 oracle; rank 0 only)",
+        "device": f"host CPU ({cpu_model()}), {n} threads (the FP64 oracle; rank 0 only)",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD + " (reference step = 1 sweep)"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample,
+                         "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line))
@@ -558,8 +571,11 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, done = oracle_rate(args.cpu_seconds)
+        v1, _, done1 = oracle_rate(min(4.0, args.cpu_seconds), threads=1)
         cpu = {"value": v, "unit": UNIT, "cores": n, "kind": "oracle",
-               "sample": f"{done} sweeps (1+5 passes) of the 160^3 lattice, FP64, OpenMP over sites"}
+               "sample": f"{done} sweeps (1+5 passes) of the 160^3 lattice, FP64, OpenMP over sites",
+               "cpu_model": cpu_model(),
+               "single_thread": {"value": v1, "unit": UNIT, "sample": f"{done1} sweeps on one thread"}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
