@@ -271,14 +271,15 @@ cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st
                                            : dim3(h.L / 8, h.ty);
   const int smem = h.smem();
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
-  if (KIND == kTileDirect) {
+  if constexpr (KIND == kTileDirect) {
     if (MODE == kMeasureOnly) return launch_chained(k_half_direct<kMeasureOnly, true>, grid, block, smem, st, d, colour, pp);
     if (pp.measure && colour == 1) return launch_chained(k_half_direct<M, true>, grid, block, smem, st, d, colour, pp);
     return launch_chained(k_half_direct<M, false>, grid, block, smem, st, d, colour, pp);
+  } else {
+    if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);
+    if (pp.measure && colour == 1) return launch_chained(k_half<M, true, KIND>, grid, block, smem, st, d, colour, pp);
+    return launch_chained(k_half<M, false, KIND>, grid, block, smem, st, d, colour, pp);
   }
-  if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);
-  if (pp.measure && colour == 1) return launch_chained(k_half<M, true, KIND>, grid, block, smem, st, d, colour, pp);
-  return launch_chained(k_half<M, false, KIND>, grid, block, smem, st, d, colour, pp);
 }
 
 template <int MODE>
