@@ -99,8 +99,8 @@ __global__ void __launch_bounds__(512) k_half(Lattice lat, int colour, PassParam
 
 // One half-sweep of one lattice with the kTileDirect tile: grid (tiles per
 // slot, R), block (L/8, ty); shared memory only for the reduction of the
-// measuring variant.
-template <int MODE, bool MEAS>
+// measuring variant.  LC: the lattice size fixed at compile time, or 0.
+template <int MODE, bool MEAS, int LC>
 __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDirectMaxRegs) k_half_direct(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   chain_wait_and_release();
@@ -111,7 +111,7 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDi
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
-  tile_direct<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
+  tile_direct<MODE, MEAS, LC>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nth = blockDim.x * blockDim.y;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);

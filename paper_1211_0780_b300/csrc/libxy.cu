@@ -262,6 +262,17 @@ cudaError_t launch_chained(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t
   return cudaLaunchKernelEx(&cfg, kern, args...);
 }
 
+// kTileDirect half-sweep, the kernel compiled for lattice size LC (0: any).
+template <int MODE, int LC>
+cudaError_t launch_direct(dim3 grid, dim3 block, int smem, cudaStream_t st, const Lattice& d, int colour,
+                          const PassParams& pp) {
+  static_assert(sizeof(kDirectSizes) / sizeof(kDirectSizes[0]) == 5, "one case per fixed size");
+  constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
+  if (MODE == kMeasureOnly) return launch_chained(k_half_direct<kMeasureOnly, true, LC>, grid, block, smem, st, d, colour, pp);
+  if (pp.measure && colour == 1) return launch_chained(k_half_direct<M, true, LC>, grid, block, smem, st, d, colour, pp);
+  return launch_chained(k_half_direct<M, false, LC>, grid, block, smem, st, d, colour, pp);
+}
+
 template <int MODE, int KIND>
 cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st, int colour,
                              const PassParams& pp) {
@@ -272,9 +283,14 @@ cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st
   const int smem = h.smem();
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
   if constexpr (KIND == kTileDirect) {
-    if (MODE == kMeasureOnly) return launch_chained(k_half_direct<kMeasureOnly, true>, grid, block, smem, st, d, colour, pp);
-    if (pp.measure && colour == 1) return launch_chained(k_half_direct<M, true>, grid, block, smem, st, d, colour, pp);
-    return launch_chained(k_half_direct<M, false>, grid, block, smem, st, d, colour, pp);
+    switch (h.L) {
+      case kDirectSizes[0]: return launch_direct<MODE, kDirectSizes[0]>(grid, block, smem, st, d, colour, pp);
+      case kDirectSizes[1]: return launch_direct<MODE, kDirectSizes[1]>(grid, block, smem, st, d, colour, pp);
+      case kDirectSizes[2]: return launch_direct<MODE, kDirectSizes[2]>(grid, block, smem, st, d, colour, pp);
+      case kDirectSizes[3]: return launch_direct<MODE, kDirectSizes[3]>(grid, block, smem, st, d, colour, pp);
+      case kDirectSizes[4]: return launch_direct<MODE, kDirectSizes[4]>(grid, block, smem, st, d, colour, pp);
+      default: return launch_direct<MODE, 0>(grid, block, smem, st, d, colour, pp);
+    }
   } else {
     if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);
     if (pp.measure && colour == 1) return launch_chained(k_half<M, true, KIND>, grid, block, smem, st, d, colour, pp);
@@ -562,11 +578,11 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
   // The kTileDirect kernels: their own block limit (kDirectMaxThreads), no
   // tile in shared memory.
   const void* direct_kernels[5] = {
-      reinterpret_cast<const void*>(k_half_direct<kMetropolis, false>),
-      reinterpret_cast<const void*>(k_half_direct<kMetropolis, true>),
-      reinterpret_cast<const void*>(k_half_direct<kOverrelax, false>),
-      reinterpret_cast<const void*>(k_half_direct<kOverrelax, true>),
-      reinterpret_cast<const void*>(k_half_direct<kMeasureOnly, true>)};
+      reinterpret_cast<const void*>(k_half_direct<kMetropolis, false, 0>),
+      reinterpret_cast<const void*>(k_half_direct<kMetropolis, true, 0>),
+      reinterpret_cast<const void*>(k_half_direct<kOverrelax, false, 0>),
+      reinterpret_cast<const void*>(k_half_direct<kOverrelax, true, 0>),
+      reinterpret_cast<const void*>(k_half_direct<kMeasureOnly, true, 0>)};
   for (const void* fn : direct_kernels) {
     cudaFuncAttributes fa{};
     e = cudaFuncGetAttributes(&fa, fn);

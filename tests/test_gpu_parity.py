@@ -416,6 +416,22 @@ def test_direct_tile_matches_march_tile_bit_for_bit():
         s.sweep(1, 1, 1)
 
 
+@pytest.mark.parametrize("L", [64, 80, 96, 128])
+def test_direct_tile_fixed_sizes_match_march(L):
+    """The direct-tile kernels compiled for the paper's lattice sizes (L
+    fixed at compile time) give the march tile's spins and lattice sums bit
+    for bit."""
+    outs = []
+    for kind in (MARCH, DIRECT):
+        s = sim(L, 2, [0.44, 0.4542], series_capacity=8)
+        s.set_tile(0, 8, 8, kind)
+        s.sweep(1, 2, 3, measure_every=1, pt_swap_every=1)
+        outs.append((s.get_packed(), s.read_series(), s.accepts()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2][0], outs[1][2][0])
+
+
 def test_barrier_timeout_reports_status_without_hanging():
     """The persistent kernel's grid barrier gives up after its budget and
     reports XY_ERR_TIMEOUT through the status word; the context stays usable."""
