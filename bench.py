@@ -575,7 +575,8 @@ def run_gpu(args):
         cpu = {"value": v, "unit": UNIT, "cores": n, "kind": "oracle",
                "sample": f"{done} sweeps (1+5 passes) of the 160^3 lattice, FP64, OpenMP over sites",
                "cpu_model": cpu_model(),
-               "single_thread": {"value": v1, "unit": UNIT, "sample": f"{done1} sweeps on one thread"}}
+               "single_thread": {"value": v1, "unit": UNIT,
+                                 "sample": f"{done1} sweep{'s' if done1 > 1 else ''} on one thread"}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
