@@ -498,12 +498,13 @@ def run_gpu(args):
     launches_per_step = SWEEPS_PER_STEP * (NM_MAIN + NOR_MAIN) * 2 + 2  # half-sweeps + finish + advance
 
     # --- per-kernel durations (CUDA events on the launching stream) ----------
-    # Graph-captured runs of one pass type: 6 sweeps of 0 + 5 passes = 60
-    # over-relaxation half-sweeps; 32 sweeps of 1 + 0 = 64 Metropolis ones
-    # (plus one counter-advance kernel each).  Average per half-sweep,
-    # including the kernel-to-kernel gaps of the graph.
-    ms_or = time_kernel(lambda: sim.sweep(0, 5, 6), st, 5) / 60
-    ms_met = time_kernel(lambda: sim.sweep(1, 0, 32), st, 5) / 64
+    # Graph-captured runs of one pass type, each one CUDA graph (the library
+    # captures up to 16 sweeps per graph): 16 sweeps of 0 + 5 passes = 160
+    # over-relaxation half-sweeps, 16 sweeps of 1 + 0 = 32 Metropolis ones
+    # (plus one counter-advance kernel each), replayed back to back.  Average
+    # per half-sweep, including the kernel-to-kernel gaps of the graph.
+    ms_or = time_kernel(lambda: sim.sweep(0, 5, 16), st, 5) / 160
+    ms_met = time_kernel(lambda: sim.sweep(1, 0, 16), st, 20) / 32
     half = L_MAIN ** 3 // 2
     hbm, src = measured_peaks()
     ach = BYTES_PER_UPDATE * half / (ms_or * 1e-3) / 1e9
@@ -530,7 +531,9 @@ def run_gpu(args):
                 "kernel": ("k_half_direct" if tile[2] == 3 else "k_half") + "<over-relaxation>, 160^3 half-sweep, "
                           f"{tile_name} tile",
                 "peak_source": f"MEASURED_PEAKS.json hbm_gbs ({src})",
-                "note": "12 B/update algorithmic; lattice state (cos, sin) is L2-resident (32.8 MB < 126 MB)"}
+                "note": ("12 B/update algorithmic; lattice state (cos, sin) is L2-resident (32.8 MB < 126 MB); "
+                         "duration = CUDA-event average over 5 back-to-back replays of a graph of 160 "
+                         "chained over-relaxation half-sweeps (+1 counter kernel)")}
     kernels = {"overrelax_half_ms": ms_or, "metropolis_half_ms": ms_met,
                "overrelax_updates_per_ns": half / (ms_or * 1e6), "metropolis_updates_per_ns": half / (ms_met * 1e6)}
 
