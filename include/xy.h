@@ -240,9 +240,9 @@ int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
  * write planes other blocks read within one launch.  kind 3 (direct): the
  * march's thread layout and plane march without shared memory or block
  * barriers: each thread loads its y-neighbour rows and x-halo element
- * itself through the L1 cache, one plane ahead; not run by
- * XY_EXEC_PERSISTENT either (L1 does not see writes made within the same
- * launch).  xy_set_tile checks 1 <= ty, tz <= L, the block size against
+ * itself through the L1 cache, one plane ahead (in XY_EXEC_PERSISTENT the
+ * grid barrier between half-sweeps orders those loads after the previous
+ * half-sweep's writes).  xy_set_tile checks 1 <= ty, tz <= L, the block size against
  * the kernels' limit (512 threads at their register use on sm_103a; 240
  * for kind 3), tz <= 64 for kind 1, and that the tile count fits the
  * partial-sum area (ceil(L/ty) ceil(L/tz) <= L^2/4).  Spins do not depend
@@ -256,10 +256,10 @@ int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
  * the context.  Outside XY_EXEC_PERSISTENT every kind (0-3) is a
  * candidate.  In XY_EXEC_PERSISTENT mode one tile kind serves every
  * lattice (xy_sweep returns XY_ERR_ARG otherwise) and the block is as wide
- * as the widest tile: for the march and the block kind and for tiles of at
- * most 64, 128 and 256 threads, each lattice's best tile is found as above,
- * and the six sets are timed in the persistent launch itself; the fastest
- * is kept. */
+ * as the widest tile: for the march, the block and the direct kind and for
+ * tiles of at most 64, 128 and 256 threads, each lattice's best tile is
+ * found as above, and the nine sets are timed in the persistent launch
+ * itself; the fastest is kept. */
 int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
 
 /* Device-side status word of the last persistent launch (0 = fine). */

@@ -1015,13 +1015,14 @@ int build_plan(xy_ctx* c) {
     if (h.kind != kind) return XY_ERR_ARG;  // one tile kind per persistent launch
     // stream tiles copy planes with TMA, which does not see what other blocks
     // of the same launch wrote
-    if (h.kind == kTileStream || h.kind == kTileDirect) return XY_ERR_ARG;
+    if (h.kind == kTileStream) return XY_ERR_ARG;
     B = std::max(B, h.threads());
     smem = std::max(smem, h.smem());
   }
   B = (B + 31) / 32 * 32;
-  const void* fn = kind == kTileBlock ? reinterpret_cast<const void*>(k_persistent<kTileBlock>)
-                                      : reinterpret_cast<const void*>(k_persistent<kTileMarch>);
+  const void* fn = kind == kTileBlock    ? reinterpret_cast<const void*>(k_persistent<kTileBlock>)
+                   : kind == kTileDirect ? reinterpret_cast<const void*>(k_persistent<kTileDirect>)
+                                         : reinterpret_cast<const void*>(k_persistent<kTileMarch>);
   cudaFuncAttributes fa{};
   XY_TRY(c, cudaFuncGetAttributes(&fa, fn));
   if (B > fa.maxThreadsPerBlock) return XY_ERR_ARG;  // a tile wider than one persistent block
@@ -1102,8 +1103,9 @@ cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return c->plan.kind == kTileBlock ? cudaLaunchKernelEx(&cfg, k_persistent<kTileBlock>, a)
-                                    : cudaLaunchKernelEx(&cfg, k_persistent<kTileMarch>, a);
+  return c->plan.kind == kTileBlock    ? cudaLaunchKernelEx(&cfg, k_persistent<kTileBlock>, a)
+         : c->plan.kind == kTileDirect ? cudaLaunchKernelEx(&cfg, k_persistent<kTileDirect>, a)
+                                       : cudaLaunchKernelEx(&cfg, k_persistent<kTileMarch>, a);
 }
 
 // Records the persistent block: barrier reset, the cooperative kernel, the
@@ -1295,11 +1297,11 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
     // each cap on the tile's threads (64, 128, 256), take each lattice's
     // best tile under the cap, then time the persistent launch itself with
     // each set and keep the fastest.
-    constexpr int kSets = 6;
+    constexpr int kSets = 9;
     std::vector<LatHost> sets[kSets];
     const std::vector<LatHost> start = c->lat;
     for (int q = 0; q < kSets && rc == XY_OK; ++q) {
-      const int kind = q < 3 ? kTileMarch : kTileBlock, cap = 64 << (q % 3);
+      const int kind = q < 3 ? kTileMarch : (q < 6 ? kTileBlock : kTileDirect), cap = 64 << (q % 3);
       c->lat = start;
       for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, kind, kind + 1, cap);
       sets[q] = c->lat;

@@ -101,7 +101,12 @@ __device__ __forceinline__ bool due_dev(uint64_t s, int every) {
 // at most 256 threads: the block kind with at least three blocks resident
 // per SM (its registers stay below 85); the march kind with its registers
 // unbounded below 255 (it holds three planes of its column and the next
-// plane's operands, and spills at 128).
+// plane's operands, and spills at 128); the direct kind likewise (at 128
+// it spilled 2.7 KB and ran 30% slower).  The direct kind's other-colour
+// loads go through L1: every half-sweep starts after a grid barrier whose
+// acquire (by one thread, then the block barrier) orders the block's later
+// loads after every block's writes of the previous half-sweep, as the
+// launch boundary does for the per-launch kernels.
 constexpr int kPersistentBlockThreads = 256;
 
 template <int KIND>
@@ -150,6 +155,19 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
                 tile_block<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
               else
                 tile_block<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
+            }
+          } else if (KIND == kTileDirect) {
+            const int ty = rest;  // threads beyond the tile's rows return at once
+            if (is_met) {
+              if (pp.measure)
+                tile_direct<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
+              else
+                tile_direct<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
+            } else {
+              if (pp.measure)
+                tile_direct<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
+              else
+                tile_direct<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
             }
           } else {
             const int ty = rest;

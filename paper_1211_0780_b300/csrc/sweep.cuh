@@ -65,8 +65,9 @@ enum Mode : int { kMetropolis = 0, kOverrelax = 1, kMeasureOnly = 2 };
 // block barrier: each thread loads its y-neighbour rows and its x-halo
 // element itself, through the L1 cache (the rows it reads are the rows its
 // neighbouring threads load for their own columns), one plane ahead, so
-// every warp marches on its own.  Per-launch only (the persistent kernel's
-// blocks write within one launch, which L1 does not see).
+// every warp marches on its own.  In the persistent kernel the grid
+// barrier between half-sweeps (an acquire, then the block barrier) orders
+// these loads after the previous half-sweep's writes.
 enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2, kTileDirect = 3 };
 
 // Threads of a kTileDirect block at most, and the registers a thread of its
