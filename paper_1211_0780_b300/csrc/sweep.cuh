@@ -980,9 +980,22 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
   __syncthreads();
 }
 
+// Error-free sum of two floats (Knuth's TwoSum): s + e equals a + b
+// exactly, s = fl(a + b).
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  const float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
 // Fixed-order block reduction of the FP32 partials into FP64 (a deterministic
-// tree: warp shuffles, then warp totals in order).  Thread 0..kNumSums-1 write
-// out[j].  `red` must hold kReduceBytes.  Every thread of the block calls it.
+// tree: warp shuffles, then warp totals in order).  Within a warp the tree
+// carries each value as an unevaluated FP32 sum s + c, every addition split
+// exactly by TwoSum (FP64 arithmetic is a small fraction of the FP32 rate on
+// sm_103a, and eight five-level FP64 trees per warp cost as much as the
+// half-sweep's update work); lane 0 adds s and c in FP64 and the warp totals
+// are summed in FP64.  Thread 0..kNumSums-1 write out[j].  `red` must hold
+// kReduceBytes.  Every thread of the block calls it.
 __device__ __forceinline__ void block_sums_to(double* out, const float acc[kNumSums], int tid,
                                               int nthreads, double* red) {
   const int lane = tid & 31, warp = tid >> 5;
@@ -991,13 +1004,17 @@ __device__ __forceinline__ void block_sums_to(double* out, const float acc[kNumS
   const unsigned mask = wn == 32 ? 0xffffffffu : ((1u << wn) - 1u);
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) {
-    double v = static_cast<double>(acc[j]);
+    float v = acc[j], c = 0.f;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
-      const double o = __shfl_down_sync(mask, v, off);
-      if (lane + off < wn) v += o;
+      const float ov = __shfl_down_sync(mask, v, off), oc = __shfl_down_sync(mask, c, off);
+      if (lane + off < wn) {
+        float e;
+        two_sum(v, ov, v, e);
+        c += oc + e;
+      }
     }
-    if (lane == 0) red[j * 32 + warp] = v;
+    if (lane == 0) red[j * 32 + warp] = static_cast<double>(v) + static_cast<double>(c);
   }
   __syncthreads();
   if (tid < kNumSums) {
