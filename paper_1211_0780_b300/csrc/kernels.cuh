@@ -142,90 +142,124 @@ struct FinishParams {
   unsigned long long* acc_swap; // [slots]
   uint64_t seed;
   int* n_swapped;               // nullable
+  int* done;                    // [lattices]: slots of the current event finished
+                                // (k_finish), back to 0 after the exchange
 };
 
-// Finishing step of one lattice, run by one whole block: fixed-order FP64
-// sum of the tile partials of each slot (lane-strided sequential sums, then
-// a fixed shuffle tree), the record, then the exchange of Eq. (3) on the
-// ladder by one thread.  Partials are read through L2 because the
-// persistent kernel's other blocks wrote them in the same launch.
-__device__ void finish_lattice(const Lattice& lat, int l, const FinishParams& fp) {
+// Sums of slot r of lattice lat, by one warp: fixed-order FP64 sum of the
+// slot's tile partials (lane-strided sequential sums, then a fixed shuffle
+// tree); lane 0 writes the slot's sums, its energy and, when recording, its
+// record.  Partials are read through L2 because the persistent kernel's
+// other blocks wrote them in the same launch.
+__device__ void finish_slot(const Lattice& lat, int r, const FinishParams& fp, int lane) {
   const int ntile = lat.nyt * lat.nzt;
+  const double* P = fp.partials + (static_cast<long long>(lat.part0) + static_cast<long long>(r) * ntile) * kNumSums;
+  double v[kNumSums];
+#pragma unroll
+  for (int j = 0; j < kNumSums; ++j) v[j] = 0.0;
+  for (int t = lane; t < ntile; t += 32) {
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) v[j] += __ldcg(P + t * kNumSums + j);
+  }
+#pragma unroll
+  for (int j = 0; j < kNumSums; ++j) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
+  }
+  if (lane == 0) {
+    const int g = lat.slot0 + r;
+    for (int j = 0; j < kNumSums; ++j) fp.sums_slot[g * kNumSums + j] = v[j];
+    const double E = -(v[2] + v[3] + v[4]);
+    fp.E_slot[g] = E;
+    if (fp.record) {
+      const uint64_t ev = fp.ctr[kCtrSeries] + fp.series_off;
+      xy_record rec;
+      rec.E = E;
+      rec.Mx = v[0];
+      rec.My = v[1];
+      for (int mu = 0; mu < 3; ++mu) {
+        rec.C[mu] = v[2 + mu];
+        rec.S[mu] = v[5 + mu];
+      }
+      rec.beta = fp.beta_slot64[g];
+      rec.slot = g;
+      rec.beta_index = fp.bidx_slot[g];
+      rec.sweep = fp.ctr[kCtrSweep] + fp.sweep_off;
+      fp.series[ev * fp.n_slots + g] = rec;
+    }
+  }
+}
+
+// The exchange of Eq. (3) on ladder l.  The pairs (k, k+1) with k of the
+// event's parity are disjoint, so thread t of nt decides the pairs
+// k = par + 2t, par + 2(t + nt), ...; the outcome does not depend on nt.
+// Energies are read through L2 (other warps wrote them).
+__device__ void exchange_ladder(const Lattice& lat, int l, const FinishParams& fp, int t, int nt) {
+  const uint64_t n = fp.ctr[kCtrSwap] + fp.swap_off;
+  const int par = fp.parity < 0 ? static_cast<int>(n & 1ull) : (fp.parity & 1);
+  const PhiloxKey key = philox_key(fp.seed);
+  const uint32_t tagw = (static_cast<uint32_t>(l) << 4) | kTagPt;
+  const int s0 = lat.slot0;
+  int count = 0;
+  for (int k = par + 2 * t; k + 1 < lat.R; k += 2 * nt) {
+    const int a = fp.perm[s0 + k], b = fp.perm[s0 + k + 1];
+    const double bk = fp.ladder_beta[s0 + k], bk1 = fp.ladder_beta[s0 + k + 1];
+    const double expo = (bk - bk1) * (__ldcg(fp.E_slot + s0 + a) - __ldcg(fp.E_slot + s0 + b));
+    const uint4 w = philox4x32_10(
+        make_uint4(static_cast<uint32_t>(k), static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32), tagw), key);
+    const double thr = expo >= 0.0 ? 1.0 : exp(expo);
+    if (u24d(w.x) < thr) {
+      fp.perm[s0 + k] = b;
+      fp.perm[s0 + k + 1] = a;
+      fp.beta_slot[s0 + b] = static_cast<float>(bk);
+      fp.beta_slot64[s0 + b] = bk;
+      fp.bidx_slot[s0 + b] = k;
+      fp.beta_slot[s0 + a] = static_cast<float>(bk1);
+      fp.beta_slot64[s0 + a] = bk1;
+      fp.bidx_slot[s0 + a] = k + 1;
+      fp.acc_swap[s0 + k] += 1ull;
+      ++count;
+    }
+  }
+  if (fp.n_swapped && count) atomicAdd(fp.n_swapped, count);
+}
+
+// Finishing step of one lattice, run by one whole block (the persistent
+// kernel): every slot's sums and record (a warp per slot), then the
+// exchange with the block's threads over the ladder's pairs.
+__device__ void finish_lattice(const Lattice& lat, int l, const FinishParams& fp) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < lat.R; r += nw) {
-    const double* P = fp.partials + (static_cast<long long>(lat.part0) + static_cast<long long>(r) * ntile) * kNumSums;
-    double v[kNumSums];
-#pragma unroll
-    for (int j = 0; j < kNumSums; ++j) v[j] = 0.0;
-    for (int t = lane; t < ntile; t += 32) {
-#pragma unroll
-      for (int j = 0; j < kNumSums; ++j) v[j] += __ldcg(P + t * kNumSums + j);
-    }
-#pragma unroll
-    for (int j = 0; j < kNumSums; ++j) {
-#pragma unroll
-      for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_down_sync(0xffffffffu, v[j], off);
-    }
-    if (lane == 0) {
-      const int g = lat.slot0 + r;
-      for (int j = 0; j < kNumSums; ++j) fp.sums_slot[g * kNumSums + j] = v[j];
-      const double E = -(v[2] + v[3] + v[4]);
-      fp.E_slot[g] = E;
-      if (fp.record) {
-        const uint64_t ev = fp.ctr[kCtrSeries] + fp.series_off;
-        xy_record rec;
-        rec.E = E;
-        rec.Mx = v[0];
-        rec.My = v[1];
-        for (int mu = 0; mu < 3; ++mu) {
-          rec.C[mu] = v[2 + mu];
-          rec.S[mu] = v[5 + mu];
-        }
-        rec.beta = fp.beta_slot64[g];
-        rec.slot = g;
-        rec.beta_index = fp.bidx_slot[g];
-        rec.sweep = fp.ctr[kCtrSweep] + fp.sweep_off;
-        fp.series[ev * fp.n_slots + g] = rec;
-      }
-    }
-  }
+  for (int r = warp; r < lat.R; r += nw) finish_slot(lat, r, fp, lane);
   __syncthreads();
-  if (fp.swap && threadIdx.x == 0) {
-    const uint64_t n = fp.ctr[kCtrSwap] + fp.swap_off;
-    const int par = fp.parity < 0 ? static_cast<int>(n & 1ull) : (fp.parity & 1);
-    const PhiloxKey key = philox_key(fp.seed);
-    const uint32_t tagw = (static_cast<uint32_t>(l) << 4) | kTagPt;
-    const int s0 = lat.slot0;
-    int count = 0;
-    for (int k = par; k + 1 < lat.R; k += 2) {
-      const int a = fp.perm[s0 + k], b = fp.perm[s0 + k + 1];
-      const double bk = fp.ladder_beta[s0 + k], bk1 = fp.ladder_beta[s0 + k + 1];
-      const double expo = (bk - bk1) * (fp.E_slot[s0 + a] - fp.E_slot[s0 + b]);
-      const uint4 w = philox4x32_10(
-          make_uint4(static_cast<uint32_t>(k), static_cast<uint32_t>(n), static_cast<uint32_t>(n >> 32), tagw), key);
-      const double thr = expo >= 0.0 ? 1.0 : exp(expo);
-      if (u24d(w.x) < thr) {
-        fp.perm[s0 + k] = b;
-        fp.perm[s0 + k + 1] = a;
-        fp.beta_slot[s0 + b] = static_cast<float>(bk);
-        fp.beta_slot64[s0 + b] = bk;
-        fp.bidx_slot[s0 + b] = k;
-        fp.beta_slot[s0 + a] = static_cast<float>(bk1);
-        fp.beta_slot64[s0 + a] = bk1;
-        fp.bidx_slot[s0 + a] = k + 1;
-        fp.acc_swap[s0 + k] += 1ull;
-        ++count;
-      }
-    }
-    if (fp.n_swapped) atomicAdd(fp.n_swapped, count);
-  }
+  if (fp.swap) exchange_ladder(lat, l, fp, threadIdx.x, blockDim.x);
   __syncthreads();
 }
 
-// One block per lattice.
-__global__ void k_finish(const Lattice* lats, FinishParams fp) {
+// Per-launch finishing step: one warp (block of 32 threads) per slot of
+// every lattice, so the FP64 sums of all slots run on as many SMs.  A
+// lattice's slots are counted on fp.done[l] as they finish (after a fence);
+// the warp that finishes the last one runs the lattice's exchange and resets
+// the count.  No warp waits for another.
+__global__ void k_finish(const Lattice* lats, int n_lat, FinishParams fp) {
   chain_wait_and_release();
-  finish_lattice(lats[blockIdx.x], blockIdx.x, fp);
+  const int g = blockIdx.x, lane = threadIdx.x & 31;
+  int lo = 0, hi = n_lat - 1;  // the lattice of slot g: the last with slot0 <= g
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (lats[mid].slot0 <= g) lo = mid;
+    else hi = mid - 1;
+  }
+  const Lattice lat = lats[lo];
+  finish_slot(lat, g - lat.slot0, fp, lane);
+  if (!fp.swap) return;
+  __threadfence();
+  int last = 0;
+  if (lane == 0) last = (atomicAdd(fp.done + lo, 1) == lat.R - 1) ? 1 : 0;
+  last = __shfl_sync(0xffffffffu, last, 0);
+  if (!last) return;
+  __threadfence();
+  exchange_ladder(lat, lo, fp, lane, 32);
+  if (lane == 0) fp.done[lo] = 0;
 }
 
 __global__ void k_advance(uint64_t* ctr, uint64_t d_mpass, uint64_t d_sweep, uint64_t d_swap,

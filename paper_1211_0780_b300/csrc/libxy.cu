@@ -47,7 +47,7 @@ int part_cap_for(int L) { return std::max(1, (L * L) / 4); }
 
 struct Layout {
   size_t spins, ladder_beta, perm, beta_slot, beta_slot64, bidx_slot, E_slot, sums_slot, partials,
-      acc_met, acc_swap, ctr, status, barrier, nswapped, lats, staging, plan_items, plan_offs,
+      acc_met, acc_swap, ctr, status, barrier, nswapped, fin_done, lats, staging, plan_items, plan_offs,
       series, total;
 };
 
@@ -94,6 +94,7 @@ Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
   o.status = take(64);
   o.barrier = take((kBarGroups + 1) * kBarStride * 8);
   o.nswapped = take(64);
+  o.fin_done = take(static_cast<size_t>(n) * 4);
   o.lats = take(static_cast<size_t>(n) * sizeof(Lattice));
   o.staging = take(static_cast<size_t>(maxN) * 4);
   o.plan_items = take(static_cast<size_t>(parts) * sizeof(int4));
@@ -336,12 +337,13 @@ FinishParams finish_params(xy_ctx* c) {
   f.acc_swap = c->at<unsigned long long>(c->lay.acc_swap);
   f.seed = c->seed;
   f.n_swapped = nullptr;
+  f.done = c->at<int>(c->lay.fin_done);
   return f;
 }
 
 int launch_finish(xy_ctx* c, cudaStream_t st, const FinishParams& f) {
-  XY_TRY(c, launch_chained(k_finish, dim3(c->n_lat), dim3(256), 0, st,
-                           static_cast<const Lattice*>(c->at<Lattice>(c->lay.lats)), f));
+  XY_TRY(c, launch_chained(k_finish, dim3(c->n_slots), dim3(32), 0, st,
+                           static_cast<const Lattice*>(c->at<Lattice>(c->lay.lats)), c->n_lat, f));
   return XY_OK;
 }
 
@@ -617,7 +619,8 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
   if ((e = cudaMemsetAsync(c->ws + lay.acc_met, 0, slot * 8, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->ws + lay.acc_swap, 0, slot * 8, st)) != cudaSuccess ||
       (e = cudaMemsetAsync(c->ws + lay.ctr, 0, kNumCounters * 8, st)) != cudaSuccess ||
-      (e = cudaMemsetAsync(c->ws + lay.status, 0, 64, st)) != cudaSuccess)
+      (e = cudaMemsetAsync(c->ws + lay.status, 0, 64, st)) != cudaSuccess ||
+      (e = cudaMemsetAsync(c->ws + lay.fin_done, 0, static_cast<size_t>(n_lattices) * 4, st)) != cudaSuccess)
     return bail(fail_cuda(nullptr, e, "cudaMemsetAsync"));
   int rc = sync_lats(c);
   if (rc != XY_OK) return bail(rc);
