@@ -224,17 +224,6 @@ __device__ void exchange_ladder(const Lattice& lat, int l, const FinishParams& f
   if (fp.n_swapped && count) atomicAdd(fp.n_swapped, count);
 }
 
-// Finishing step of one lattice, run by one whole block (the persistent
-// kernel): every slot's sums and record (a warp per slot), then the
-// exchange with the block's threads over the ladder's pairs.
-__device__ void finish_lattice(const Lattice& lat, int l, const FinishParams& fp) {
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  for (int r = warp; r < lat.R; r += nw) finish_slot(lat, r, fp, lane);
-  __syncthreads();
-  if (fp.swap) exchange_ladder(lat, l, fp, threadIdx.x, blockDim.x);
-  __syncthreads();
-}
-
 // Per-launch finishing step: one warp (block of 32 threads) per slot of
 // every lattice, so the FP64 sums of all slots run on as many SMs.  A
 // lattice's slots are counted on fp.done[l] as they finish (after a fence);

@@ -201,7 +201,22 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
       fp.swap_off = n_swp;
       fp.record = meas ? 1 : 0;
       fp.swap = swp ? 1 : 0;
-      for (int l = blockIdx.x; l < a.n_lat; l += gridDim.x) finish_lattice(a.lats[l], l, fp);
+      // every slot's sums and record on its own warp, spread over the grid,
+      // then (after a barrier) each ladder's exchange on one block
+      const int lane = tid & 31, nwb = B >> 5;
+      for (int g = blockIdx.x * nwb + (tid >> 5); g < fp.n_slots; g += gridDim.x * nwb) {
+        int lo = 0, hi = a.n_lat - 1;  // the lattice of slot g
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (a.lats[mid].slot0 <= g) lo = mid;
+          else hi = mid - 1;
+        }
+        finish_slot(a.lats[lo], g - a.lats[lo].slot0, fp, lane);
+      }
+      if (swp) {
+        if (!grid_barrier(a, nbar++)) return;
+        for (int l = blockIdx.x; l < a.n_lat; l += gridDim.x) exchange_ladder(a.lats[l], l, fp, tid, B);
+      }
       n_rec += meas ? 1 : 0;
       n_swp += swp ? 1 : 0;
       if (!grid_barrier(a, nbar++)) return;
