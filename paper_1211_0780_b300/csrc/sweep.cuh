@@ -20,14 +20,16 @@
 //               neighbouring float4, with periodic wrap along the row);
 //   y+-1, z+-1 -> the other colour's rows (y+-1, z), (y, z+-1) at the same k.
 //
-// Tile.  A thread block covers full rows in x, `ty` rows in y and marches
-// over `tz` planes in z.  A thread loads its own row of the other colour's
-// plane z+1 and keeps planes z-1, z, z+1 of its own column in registers;
-// planes are shared through three shared-memory buffers (one barrier per
-// plane) for the y neighbours and the x halo element.  The thread rows at the
-// tile's y edges also load the halo rows y0-1 and y0+ty.  The plane loop is
-// unrolled three times so the register planes and the buffer indices rotate
-// without copies.
+// Tile (the march, kTileMarch).  A thread block covers full rows in x, `ty`
+// rows in y and marches over `tz` planes in z.  A thread loads its own row
+// of the other colour's plane z+1 and keeps planes z-1, z, z+1 of its own
+// column in registers; planes are shared through three shared-memory
+// buffers (one barrier per plane) for the y neighbours and the x halo
+// element.  The thread rows at the tile's y edges also load the halo rows
+// y0-1 and y0+ty.  The plane loop is unrolled three times so the register
+// planes and the buffer indices rotate without copies.  The other tile kinds
+// (block, stream, direct; see TileKind) keep this thread layout or this
+// update and change how neighbour rows reach the thread.
 //
 // Accuracy.  The reflection renormalises its result with one Newton step
 // towards |S| = 1, so stored vectors stay within a few ulp of the unit
