@@ -99,10 +99,10 @@ __device__ __forceinline__ bool due_dev(uint64_t s, int every) {
 
 // Every lattice of a persistent launch uses tile kind KIND, with blocks of
 // at most 256 threads: the block kind with at least three blocks resident
-// per SM (its registers stay below 85); the march kind with its registers
-// unbounded below 255 (it holds three planes of its column and the next
-// plane's operands, and spills at 128); the direct kind likewise (at 128
-// it spilled 2.7 KB and ran 30% slower).  The direct kind's other-colour
+// per SM (80 registers); the march kind with two (128 registers; it spills
+// 272 bytes there, and ran 19% faster on a 64^3 x 32 ladder than with its
+// 217 registers unbounded); the direct kind with its registers unbounded
+// (246; at 128 it spilled 1.2 KB and ran 10% slower).  The direct kind's other-colour
 // loads go through L1: every half-sweep starts after a grid barrier whose
 // acquire (by one thread, then the block barrier) orders the block's later
 // loads after every block's writes of the previous half-sweep, as the
@@ -110,7 +110,7 @@ __device__ __forceinline__ bool due_dev(uint64_t s, int every) {
 constexpr int kPersistentBlockThreads = 256;
 
 template <int KIND>
-__global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 3 : 1)
+__global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 3 : (KIND == kTileMarch ? 2 : 1))
     k_persistent(PersistentArgs a) {
   extern __shared__ __align__(16) float sm[];
   unsigned long long nbar = 0;
@@ -123,6 +123,43 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
   const int n_pass = a.nM + a.nOR;
   const int i0 = a.offs[blockIdx.x], i1 = a.offs[blockIdx.x + 1];
   uint64_t n_rec = 0, n_swp = 0;
+  // One pass of colour `colour` over this block's tile items.  The update
+  // passes never measure: the lattice sums of a measured sweep come from a
+  // measure-only pass after its last half-sweep, which forms the same
+  // per-thread sums in the same order as the per-launch path's fused pass
+  // (the white sites' stored spins are the updated ones), so the records
+  // are identical; keeping the measuring update variants out of this kernel
+  // lets the march kind keep two blocks per SM.
+  auto tile_items = [&](auto mode, int colour, const PassParams& pp) {
+    constexpr int MODE = decltype(mode)::value;
+    constexpr bool MEAS = MODE == kMeasureOnly;
+    for (int it = i0; it < i1; ++it) {
+      const int4 w = a.items[it];
+      const Lattice lat = a.lats[w.x];
+      const int TX = lat.L >> 3;
+      const int tx = tid % TX, rest = tid / TX;
+      const int yt = w.z % lat.nyt, zt = w.z / lat.nyt;
+      float acc[kNumSums];
+#pragma unroll
+      for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
+      uint32_t n_acc = 0u;
+      if (KIND == kTileBlock) {
+        const int ty = rest % lat.ty, tz = rest / lat.ty;
+        tile_block<MODE, MEAS>(lat, w.y, yt, zt, colour, tx, ty, tz, tz < lat.tz, pp, sm, acc, n_acc);
+      } else if (KIND == kTileDirect) {
+        // threads beyond the tile's rows return at once
+        tile_direct<MODE, MEAS>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc);
+      } else {
+        tile_pass<MODE, MEAS>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc);
+      }
+      if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + w.y, n_acc, tid, B);
+      if (MEAS) {
+        double* red = reinterpret_cast<double*>(sm + tile_floats(lat.kind, lat.L, lat.ty, lat.tz));
+        const long long part = lat.part0 + static_cast<long long>(w.y) * lat.nyt * lat.nzt + w.z;
+        block_sums_to(pp.partials + part * kNumSums, acc, tid, B, red);
+      }
+    }
+  };
   for (int s = 0; s < a.n_sweeps; ++s) {
     const uint64_t sw = s_base + s;
     const bool meas = due_dev(sw, a.me), swp = due_dev(sw, a.se);
@@ -131,68 +168,19 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
       for (int colour = 0; colour < 2; ++colour) {
         PassParams pp = a.pp;
         pp.mpass_off = is_met ? static_cast<uint64_t>(s) * a.nM + p : 0ull;
-        pp.measure = ((meas || swp) && p == n_pass - 1 && colour == 1) ? 1 : 0;
-        for (int it = i0; it < i1; ++it) {
-          const int4 w = a.items[it];
-          const Lattice lat = a.lats[w.x];
-          const int TX = lat.L >> 3;
-          const int tx = tid % TX, rest = tid / TX;
-          const int yt = w.z % lat.nyt, zt = w.z / lat.nyt;
-          float acc[kNumSums];
-#pragma unroll
-          for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
-          uint32_t n_acc = 0u;
-          if (KIND == kTileBlock) {
-            const int ty = rest % lat.ty, tz = rest / lat.ty;
-            const bool inb = tz < lat.tz;
-            if (is_met) {
-              if (pp.measure)
-                tile_block<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
-              else
-                tile_block<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
-            } else {
-              if (pp.measure)
-                tile_block<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
-              else
-                tile_block<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, tz, inb, pp, sm, acc, n_acc);
-            }
-          } else if (KIND == kTileDirect) {
-            const int ty = rest;  // threads beyond the tile's rows return at once
-            if (is_met) {
-              if (pp.measure)
-                tile_direct<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
-              else
-                tile_direct<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
-            } else {
-              if (pp.measure)
-                tile_direct<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
-              else
-                tile_direct<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, pp, acc, n_acc);
-            }
-          } else {
-            const int ty = rest;
-            const bool inb = ty < lat.ty;
-            if (is_met) {
-              if (pp.measure)
-                tile_pass<kMetropolis, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
-              else
-                tile_pass<kMetropolis, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
-            } else {
-              if (pp.measure)
-                tile_pass<kOverrelax, true>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
-              else
-                tile_pass<kOverrelax, false>(lat, w.y, yt, zt, colour, tx, ty, inb, pp, sm, acc, n_acc);
-            }
-          }
-          if (is_met) block_count_to(pp.acc_met + lat.slot0 + w.y, n_acc, tid, B);
-          if (pp.measure) {
-            double* red = reinterpret_cast<double*>(sm + tile_floats(lat.kind, lat.L, lat.ty, lat.tz));
-            const long long part = lat.part0 + static_cast<long long>(w.y) * lat.nyt * lat.nzt + w.z;
-            block_sums_to(pp.partials + part * kNumSums, acc, tid, B, red);
-          }
-        }
+        pp.measure = 0;
+        if (is_met)
+          tile_items(IC<kMetropolis>{}, colour, pp);
+        else
+          tile_items(IC<kOverrelax>{}, colour, pp);
         if (!grid_barrier(a, nbar++)) return;
       }
+    }
+    if (meas || swp) {
+      PassParams pp = a.pp;
+      pp.measure = 1;
+      tile_items(IC<kMeasureOnly>{}, 1, pp);
+      if (!grid_barrier(a, nbar++)) return;
     }
     if (meas || swp) {
       FinishParams fp = a.fp;
