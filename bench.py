@@ -66,53 +66,99 @@ def measured_peaks():
 
 
 class ClockSampler:
-    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+    """SM clocks and throttle reasons sampled during the timed region: NVML
+    polled every 2 ms from a background thread (the timed region of a short
+    run lasts milliseconds), else nvidia-smi at its 200 ms minimum."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
 
     def __init__(self, index: int):
         self.index = index
         self.proc = None
         self.path = None
+        self.thread = None
+        self.samples = []
+        self.source = None
+
+    # NVML (nvml.h): NVML_CLOCK_SM and the clock-event reason bits
+    NVML_CLOCK_SM = 1
+    BITS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40), ("sw_thermal_slowdown", 0x20),
+            ("sw_power_cap", 0x4))
+
+    def _nvml_loop(self, lib, handle, reasons_fn):
+        import ctypes
+        sm, mx, mask = ctypes.c_uint(), ctypes.c_uint(), ctypes.c_ulonglong()
+        while not self.stop_flag.is_set():
+            if (lib.nvmlDeviceGetClockInfo(handle, self.NVML_CLOCK_SM, ctypes.byref(sm)) != 0
+                    or lib.nvmlDeviceGetMaxClockInfo(handle, self.NVML_CLOCK_SM, ctypes.byref(mx)) != 0
+                    or reasons_fn(handle, ctypes.byref(mask)) != 0):
+                break
+            self.samples.append((float(sm.value), float(mx.value), [n for n, bit in self.BITS if mask.value & bit]))
+            time.sleep(0.002)
 
     def start(self):
+        try:
+            import ctypes
+            import threading
+            lib = ctypes.CDLL("libnvidia-ml.so.1")
+            handle = ctypes.c_void_p()
+            if lib.nvmlInit_v2() != 0 or lib.nvmlDeviceGetHandleByIndex_v2(self.index, ctypes.byref(handle)) != 0:
+                raise OSError("nvml")
+            reasons_fn = getattr(lib, "nvmlDeviceGetCurrentClocksEventReasons", None) or \
+                lib.nvmlDeviceGetCurrentClocksThrottleReasons
+            self.stop_flag = threading.Event()
+            self.thread = threading.Thread(target=self._nvml_loop, args=(lib, handle, reasons_fn), daemon=True)
+            self.thread.start()
+            self.source = "nvml, 2 ms"
+            return
+        except (OSError, AttributeError):
+            self.thread = None
         fd, self.path = tempfile.mkstemp(suffix=".csv")
         os.close(fd)
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
                  "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+            self.source = "nvidia-smi, 200 ms"
         except OSError:
             self.proc = None
 
     def stop(self):
-        if self.proc is None:
-            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
-        self.proc.terminate()
-        try:
-            self.proc.wait(timeout=5)
-        except subprocess.TimeoutExpired:
-            self.proc.kill()
         sm, mx, reasons = [], [], set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        with open(self.path) as f:
-            for line in f:
-                parts = [p.strip() for p in line.split(",")]
-                if len(parts) < 9:
-                    continue
-                try:
-                    sm.append(float(parts[1]))
-                    mx.append(float(parts[2]))
-                except ValueError:
-                    continue
-                for name, v in zip(names, parts[5:9]):
-                    if v.lower() == "active":
-                        reasons.add(name)
-        os.unlink(self.path)
+        if self.thread is not None:
+            self.stop_flag.set()
+            self.thread.join(timeout=5)
+            for a, b, r in self.samples:
+                sm.append(a)
+                mx.append(b)
+                reasons.update(r)
+        elif self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            with open(self.path) as f:
+                for line in f:
+                    parts = [p.strip() for p in line.split(",")]
+                    if len(parts) < 9:
+                        continue
+                    try:
+                        sm.append(float(parts[1]))
+                        mx.append(float(parts[2]))
+                    except ValueError:
+                        continue
+                    for name, v in zip(self.NAMES, parts[5:9]):
+                        if v.lower() == "active":
+                            reasons.add(name)
+            os.unlink(self.path)
+        else:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no clock source"], "samples": 0}
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm), "source": self.source}
 
 
 def allreduce_max(value: float, world: int) -> float:
@@ -481,7 +527,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     clocks = ClockSampler(dev)
     clocks.start()
-    time.sleep(0.3)
+    if clocks.source and clocks.source.startswith("nvidia-smi"):
+        time.sleep(0.3)  # let nvidia-smi start sampling
     for a, b in evs:
         flush.zero_()
         a.record(st)
