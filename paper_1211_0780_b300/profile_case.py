@@ -4,7 +4,9 @@ python -m paper_1211_0780_b300.profile_case --L 160 --ty 8 --tz 2 --kind 1 --mod
 
 Creates one lattice (seeded hot start), runs a few warm-up sweeps, then
 issues `--launches` half-sweeps of the chosen kernel (or = over-relaxation,
-met = Metropolis, meas = measurement-only) and synchronises; reweight =
+met = Metropolis, meas = measurement-only; sweep = 1 + 5 sweeps; pt = sweeps of
+1 + 3 passes with sums and an exchange, the ladder spaced on [0.450, 0.458])
+and synchronises; reweight =
 `--launches` forward reweightings of one synthetic series of `--T` samples to
 `--K` couplings.  No autotuning,
 so the launch list is short and deterministic.
@@ -23,7 +25,7 @@ def main():
     ap.add_argument("--tz", type=int, default=0)
     ap.add_argument("--kind", type=int, default=1,
                     help="0 = march, 1 = block, 2 = stream, 3 = direct tile")
-    ap.add_argument("--mode", default="or", choices=["or", "met", "meas", "sweep", "reweight"])
+    ap.add_argument("--mode", default="or", choices=["or", "met", "meas", "sweep", "pt", "reweight"])
     ap.add_argument("--T", type=int, default=200000, help="samples of the reweight mode's series")
     ap.add_argument("--K", type=int, default=4096, help="couplings of the reweight mode")
     ap.add_argument("--launches", type=int, default=5)
@@ -42,7 +44,8 @@ def main():
         torch.cuda.synchronize()
         print("reweight done")
         return
-    betas = np.linspace(0.4542, 0.4560, args.R) if args.R > 1 else [0.4542]
+    betas = (np.linspace(0.450, 0.458, args.R) if args.mode == "pt" else np.linspace(0.4542, 0.4560, args.R)) \
+        if args.R > 1 else [0.4542]
     sim = xy.Simulation(args.L, args.R, betas, 0x5EED2012)
     if args.ty and args.tz:
         sim.set_tile(0, args.ty, args.tz, args.kind)
@@ -54,6 +57,9 @@ def main():
             sim.metropolis_half(i & 1, 1000 + i)
         elif args.mode == "meas":
             sim.measure()
+        elif args.mode == "pt":
+            # one sweep of 1 + 3 passes with the sums and an exchange (the PT workload)
+            sim.sweep(1, 3, 1, measure_every=1, pt_swap_every=1)
         else:
             sim.sweep(1, 5, 1)
     torch.cuda.synchronize()
