@@ -229,26 +229,32 @@ struct SumAcc {
 };
 template <>
 struct SumAcc<true> {
-  float acc[kNumSums];
-  float err[kNumSums];
+  float2 acc[kNumSums / 2];
+  float2 err[kNumSums / 2];
   __device__ __forceinline__ SumAcc() {
 #pragma unroll
-    for (int j = 0; j < kNumSums; ++j) acc[j] = err[j] = 0.f;
+    for (int j = 0; j < kNumSums / 2; ++j) acc[j] = err[j] = make_float2(0.f, 0.f);
   }
   // Compensated (Kahan) accumulation of one plane's terms, so the per-thread
-  // FP32 sums stay within a few roundings of the terms whatever the depth.
+  // FP32 sums stay within a few roundings of the terms whatever the depth;
+  // two sums at a time in the paired FP32 instructions (each lane rounds as
+  // the scalar instruction would).
   __device__ __forceinline__ void add_plane(const float* step) {
 #pragma unroll
-    for (int j = 0; j < kNumSums; ++j) {
-      const float yv = step[j] - err[j];
-      const float t = acc[j] + yv;
-      err[j] = (t - acc[j]) - yv;
+    for (int j = 0; j < kNumSums / 2; ++j) {
+      const float2 yv = __fadd2_rn(make_float2(step[2 * j], step[2 * j + 1]),
+                                   make_float2(-err[j].x, -err[j].y));
+      const float2 t = __fadd2_rn(acc[j], yv);
+      err[j] = __fadd2_rn(__fadd2_rn(t, make_float2(-acc[j].x, -acc[j].y)), make_float2(-yv.x, -yv.y));
       acc[j] = t;
     }
   }
   __device__ __forceinline__ void export_to(float* out) const {
 #pragma unroll
-    for (int j = 0; j < kNumSums; ++j) out[j] = acc[j];
+    for (int j = 0; j < kNumSums / 2; ++j) {
+      out[2 * j] = acc[j].x;
+      out[2 * j + 1] = acc[j].y;
+    }
   }
 };
 
