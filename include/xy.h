@@ -17,8 +17,9 @@
  *   - Work is ordered on the stream given to xy_init (a cudaStream_t passed
  *     as void*; NULL = the legacy default stream).  Calls that return host
  *     data synchronise that stream.
- *   - Errors are sticky per context: after XY_ERR_CUDA or XY_ERR_TIMEOUT
- *     every call on the context returns XY_ERR_STATE until xy_destroy.
+ *   - Errors are sticky per context: after XY_ERR_CUDA, XY_ERR_TIMEOUT or
+ *     XY_ERR_BOUNDS every call on the context returns XY_ERR_STATE until
+ *     xy_destroy.
  *   - A spin is stored on the device as its unit vector (cos theta,
  *     sin theta) in FP32.  Angles exchanged with the host (xy_get_state /
  *     xy_set_state) are FP32 radians in [0, 2 pi).
@@ -63,7 +64,9 @@ enum {
   XY_ERR_CUDA = -2,    /* a CUDA call failed; the context is now unusable */
   XY_ERR_TIMEOUT = -3, /* a bounded device-side wait ran out (grid barrier) */
   XY_ERR_STATE = -4,   /* the context is in a sticky error state          */
-  XY_ERR_NOMEM = -5    /* workspace or series buffer too small            */
+  XY_ERR_NOMEM = -5,   /* workspace or series buffer too small            */
+  XY_ERR_BOUNDS = -6   /* bounds-checked build (XY_BOUNDS_CHECK, libxy_check)
+                          only: a kernel skipped an access outside its buffer */
 };
 
 /* Execution modes of xy_sweep. */

@@ -6,6 +6,7 @@
 // keep host mirrors of the device counters, and marshal state between the
 // natural host layout and the packed device layout.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <cmath>
@@ -196,6 +197,15 @@ int fail_cuda(xy_ctx* c, cudaError_t e, const char* what) {
 
 #define XY_CHECK_LAUNCH(c) XY_TRY(c, cudaGetLastError())
 
+// An NVTX range over one C-ABI call (host-side timeline markers for
+// profilers; header-only, a no-op unless a tool is attached).
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
 #define XY_ENTER(c)                                          \
   do {                                                       \
     if (!(c)) return XY_ERR_ARG;                             \
@@ -212,8 +222,8 @@ int sync_checked(xy_ctx* c) {
   XY_TRY(c, cudaMemcpyAsync(&st, c->ws + c->lay.status, 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
   if (st != 0) {
-    c->sticky = XY_ERR_TIMEOUT;
-    return XY_ERR_TIMEOUT;
+    c->sticky = st == XY_ERR_BOUNDS ? XY_ERR_BOUNDS : XY_ERR_TIMEOUT;
+    return c->sticky;
   }
   return XY_OK;
 }
@@ -468,6 +478,7 @@ const char* xy_strerror(int status) {
     case XY_ERR_TIMEOUT: return "device-side wait timed out";
     case XY_ERR_STATE: return "context is in an error state";
     case XY_ERR_NOMEM: return "buffer too small";
+    case XY_ERR_BOUNDS: return "out-of-bounds access skipped (bounds-checked build)";
     default: return "unknown status";
   }
 }
@@ -658,6 +669,7 @@ int xy_set_exec(xy_ctx* c, int mode) {
 }
 
 int xy_sweep(xy_ctx* c, int nM, int nOR, int n_sweeps, int me, int se) {
+  const NvtxRange nvtx_range("xy_sweep");
   XY_ENTER(c);
   if (nM < 0 || nOR < 0 || n_sweeps < 0 || me < 0 || se < 0) return XY_ERR_ARG;
   if (n_sweeps == 0) return XY_OK;
@@ -726,6 +738,7 @@ static int measure_now(xy_ctx* c, int swap, int parity) {
 }
 
 int xy_measure(xy_ctx* c, xy_record* out) {
+  const NvtxRange nvtx_range("xy_measure");
   XY_ENTER(c);
   if (!out) return XY_ERR_ARG;
   int rc = measure_now(c, 0, 0);
@@ -757,6 +770,7 @@ int xy_measure(xy_ctx* c, xy_record* out) {
 }
 
 int xy_pt_swap(xy_ctx* c, int parity, int* n_accepted_out) {
+  const NvtxRange nvtx_range("xy_pt_swap");
   XY_ENTER(c);
   if (parity != 0 && parity != 1) return XY_ERR_ARG;
   XY_TRY(c, cudaMemsetAsync(c->ws + c->lay.nswapped, 0, 4, c->stream));
@@ -1217,6 +1231,7 @@ int xy_debug_stream_timeout(xy_ctx* c, int budget_us, int* status_out) {
 }
 
 int xy_autotune(xy_ctx* c, int nM, int nOR) {
+  const NvtxRange nvtx_range("xy_autotune");
   XY_ENTER(c);
   if (nM < 0 || nOR < 0 || nM + nOR == 0) return XY_ERR_ARG;
   // Save what trial sweeps change: spins, counters, Metropolis accepts.

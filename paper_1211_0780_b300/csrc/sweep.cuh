@@ -185,6 +185,37 @@ struct Spins4 {
   float4 c, s;
 };
 
+// Bounds of the spin accesses of one tile pass: the slot's 2N floats.  In a
+// build with XY_BOUNDS_CHECK defined (the debug library, in place of
+// compute-sanitizer) every global spin access is checked against them; one
+// outside is skipped (loads read zeros) and the status word is set to
+// XY_ERR_BOUNDS, so the host reports it and nothing faults.  Otherwise the
+// guard is empty and the checks compile away.
+struct SpinGuard {
+#ifdef XY_BOUNDS_CHECK
+  const float* lo;
+  const float* hi;
+  int* status;
+  __device__ __forceinline__ bool ok(const float* p, int n) const {
+    if (p >= lo && p + n <= hi) return true;
+    atomicCAS(status, 0, XY_ERR_BOUNDS);
+    return false;
+  }
+#else
+  __device__ __forceinline__ bool ok(const float*, int) const { return true; }
+#endif
+};
+__device__ __forceinline__ SpinGuard spin_guard(const float* slot, size_t n_floats, int* status) {
+#ifdef XY_BOUNDS_CHECK
+  return SpinGuard{slot, slot + n_floats, status};
+#else
+  (void)slot;
+  (void)n_floats;
+  (void)status;
+  return SpinGuard{};
+#endif
+}
+
 // Spin loads and stores go through L2 (.cg): the persistent kernel reads
 // values other blocks wrote earlier in the same launch.
 __device__ __forceinline__ float4 ld4(const float* p) {
@@ -195,15 +226,20 @@ __device__ __forceinline__ void st4(float* p, float4 v) {
 }
 
 // The 4 spins of one thread's row segment: cos at p, sin at p + half.
-__device__ __forceinline__ Spins4 ld_spins(const float* p, uint32_t half) {
-  Spins4 v;
-  v.c = ld4(p);
-  v.s = ld4(p + half);
+__device__ __forceinline__ Spins4 ld_spins(const SpinGuard& g, const float* p, uint32_t half) {
+  Spins4 v{};
+  if (g.ok(p, 4) && g.ok(p + half, 4)) {
+    v.c = ld4(p);
+    v.s = ld4(p + half);
+  }
   return v;
 }
-__device__ __forceinline__ void st_spins(float* p, uint32_t half, const float4& c, const float4& s) {
-  st4(p, c);
-  st4(p + half, s);
+__device__ __forceinline__ void st_spins(const SpinGuard& g, float* p, uint32_t half, const float4& c,
+                                         const float4& s) {
+  if (g.ok(p, 4) && g.ok(p + half, 4)) {
+    st4(p, c);
+    st4(p + half, s);
+  }
 }
 
 __device__ __forceinline__ void put_row(float* row, int H, int tx, const Spins4& v) {
@@ -393,6 +429,7 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
   const bool act = in_block && ty < TYa;
   const int y = y0 + ty;
   float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  const SpinGuard sg = spin_guard(slot, 4 * static_cast<size_t>(half), pp.status);
   float* const own = slot + colour * (2 * half);            // cos; sin at + half
   const float* const oth = slot + (colour ^ 1) * (2 * half);
   const int rows = lat.ty + 2;
@@ -426,16 +463,16 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
     const uint32_t zb = static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS;
     const uint32_t zz = static_cast<uint32_t>(z0) * PS;
     const uint32_t z1 = static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS;
-    pa = ld_spins(oth + offy + zb, half);
-    pb = ld_spins(oth + offy + zz, half);
+    pa = ld_spins(sg, oth + offy + zb, half);
+    pb = ld_spins(sg, oth + offy + zz, half);
     put_row(row_ptr(0, ty + 1), H, tx, pb);
-    if (top) put_row(row_ptr(0, 0), H, tx, ld_spins(oth + offym + zz, half));
-    if (bot) put_row(row_ptr(0, TYa + 1), H, tx, ld_spins(oth + offyp + zz, half));
-    nx_oth = ld_spins(oth + offy + z1, half);
-    nx_own = ld_spins(own + offy + zz, half);
+    if (top) put_row(row_ptr(0, 0), H, tx, ld_spins(sg, oth + offym + zz, half));
+    if (bot) put_row(row_ptr(0, TYa + 1), H, tx, ld_spins(sg, oth + offyp + zz, half));
+    nx_oth = ld_spins(sg, oth + offy + z1, half);
+    nx_own = ld_spins(sg, own + offy + zz, half);
     if (TZa > 1) {
-      if (top) nx_h0 = ld_spins(oth + offym + z1, half);
-      if (bot) nx_h1 = ld_spins(oth + offyp + z1, half);
+      if (top) nx_h0 = ld_spins(sg, oth + offym + z1, half);
+      if (bot) nx_h1 = ld_spins(sg, oth + offyp + z1, half);
     }
   }
   __syncthreads();
@@ -455,11 +492,11 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
         // prefetch the next plane's operands
         const uint32_t pz1 = static_cast<uint32_t>(z + 1) * PS;
         const uint32_t pz2 = static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS;
-        nx_oth = ld_spins(oth + offy + pz2, half);
-        nx_own = ld_spins(own + offy + pz1, half);
+        nx_oth = ld_spins(sg, oth + offy + pz2, half);
+        nx_own = ld_spins(sg, own + offy + pz1, half);
         if (i + 2 < TZa) {
-          if (top) nx_h0 = ld_spins(oth + offym + pz2, half);
-          if (bot) nx_h1 = ld_spins(oth + offyp + pz2, half);
+          if (top) nx_h0 = ld_spins(sg, oth + offym + pz2, half);
+          if (bot) nx_h1 = ld_spins(sg, oth + offyp + pz2, half);
         }
       }
       const float* rm = row_ptr(b0, ty);
@@ -486,7 +523,7 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
       Spins4 nw;
       update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
       if (MEAS) sums.add_plane(stepv);
-      if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+      if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
     }
     __syncthreads();
   };
@@ -506,11 +543,16 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
 // launch, and a launch starts reading only after its predecessor has
 // completed and its writes are visible (griddepcontrol.wait), so no cached
 // line is stale.
-__device__ __forceinline__ Spins4 ld_spins_l1(const float* p, uint32_t half) {
-  Spins4 v;
-  v.c = __ldca(reinterpret_cast<const float4*>(p));
-  v.s = __ldca(reinterpret_cast<const float4*>(p + half));
+__device__ __forceinline__ Spins4 ld_spins_l1(const SpinGuard& g, const float* p, uint32_t half) {
+  Spins4 v{};
+  if (g.ok(p, 4) && g.ok(p + half, 4)) {
+    v.c = __ldca(reinterpret_cast<const float4*>(p));
+    v.s = __ldca(reinterpret_cast<const float4*>(p + half));
+  }
   return v;
+}
+__device__ __forceinline__ float ld1_l1(const SpinGuard& g, const float* p) {
+  return g.ok(p, 1) ? __ldca(p) : 0.f;
 }
 
 // One tile of one half-sweep, kTileDirect: the thread layout and the plane
@@ -536,6 +578,7 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   if (ty >= TYa) return;
   const int y = y0 + ty;
   float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  const SpinGuard sg = spin_guard(slot, 4 * static_cast<size_t>(half), pp.status);
   float* const own = slot + colour * (2 * half);  // cos; sin at + half
   const float* const oth = slot + (colour ^ 1) * (2 * half);
   const int ym = (y == 0 ? L : y) - 1;  // periodic y neighbours of this row
@@ -571,18 +614,18 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   Spins4 P0, P1, P2, P3{};
   Operands A, B;
   auto load_operands = [&](Operands& o, int z, uint32_t pz) {
-    o.own = ld_spins(own + offy + pz, half);
-    o.ym = ld_spins_l1(oth + offym + pz, half);
-    o.yp = ld_spins_l1(oth + offyp + pz, half);
+    o.own = ld_spins(sg, own + offy + pz, half);
+    o.ym = ld_spins_l1(sg, oth + offym + pz, half);
+    o.yp = ld_spins_l1(sg, oth + offyp + pz, half);
     const uint32_t oh = (((y + z + colour) & 1) ? offh1 : offh0) + pz;
-    o.hc = __ldca(oth + oh);
-    o.hs = __ldca(oth + oh + half);
+    o.hc = ld1_l1(sg, oth + oh);
+    o.hs = ld1_l1(sg, oth + oh + half);
   };
   {
     const uint32_t zz = static_cast<uint32_t>(z0) * PS;
-    P3 = ld_spins_l1(oth + offy + static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS, half);
-    P0 = ld_spins_l1(oth + offy + zz, half);
-    P1 = ld_spins_l1(oth + offy + static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS, half);
+    P3 = ld_spins_l1(sg, oth + offy + static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS, half);
+    P0 = ld_spins_l1(sg, oth + offy + zz, half);
+    P1 = ld_spins_l1(sg, oth + offy + static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS, half);
     load_operands(A, z0, zz);
   }
 
@@ -591,7 +634,7 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   auto step = [&](Spins4& zm, Spins4& zc, Spins4& zn, Spins4& zf, Operands& cur, Operands& nxt, int i) {
     const int z = z0 + i;
     if (i + 1 < TZa) {
-      zf = ld_spins_l1(oth + offy + static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS, half);
+      zf = ld_spins_l1(sg, oth + offy + static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS, half);
       load_operands(nxt, z + 1, static_cast<uint32_t>(z + 1) * PS);
     }
     const int s = (y + z + colour) & 1;
@@ -608,7 +651,7 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
     Spins4 nw;
     update4<MODE, MEAS>(zc, cur.hc, cur.hs, s, cur.ym, cur.yp, zm, zn, cur.own, w0, w1, beta, nw, n_acc, stepv);
     if (MEAS) sums.add_plane(stepv);
-    if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+    if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
   };
 
   for (int i = 0; i < TZa; i += 4) {
@@ -717,6 +760,7 @@ __device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, i
   const bool act = tid < NC && ty < TYa;
   const int y = y0 + ty;
   float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  const SpinGuard sg = spin_guard(slot, 4 * static_cast<size_t>(half), pp.status);
   float* const own = slot + colour * (2 * half);
   const float* const oth = slot + (colour ^ 1) * (2 * half);
   const int SF = stream_stage_floats(L, lat.ty);
@@ -780,12 +824,13 @@ __device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, i
               const int srow = part == 0 ? 0 : (part == 1 ? 1 : TYa + 1);
               const int nrow = merged ? TYa + 2 : (part == 1 ? TYa : 1);
               const float* src = oth + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(yrow);
-              bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs * OS + srow * H), src, row * nrow, bar);
+              if (sg.ok(src, H * nrow))
+                bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs * OS + srow * H), src, row * nrow, bar);
             }
           } else if (has_own) {
             const int cs = lane - 6;
             const float* src = own + cs * half + zoff + static_cast<uint32_t>(H) * static_cast<uint32_t>(y0);
-            bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs ? WS : WC), src, row * TYa, bar);
+            if (sg.ok(src, H * TYa)) bulk_copy_g2s(dst0 + 4u * static_cast<uint32_t>(cs ? WS : WC), src, row * TYa, bar);
           }
         }
       }
@@ -868,7 +913,7 @@ __device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, i
         Spins4 nw;
         update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
         if (MEAS) sums.add_plane(stepv);
-        if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+        if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
       }
       release(i + 1);
       s1 = s2;
@@ -910,6 +955,7 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
   const bool act = in_block && ty < TYa && tz < TZa;
   const int y = y0 + ty, z = z0 + tz;
   float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  const SpinGuard sg = spin_guard(slot, 4 * static_cast<size_t>(half), pp.status);
   float* const own = slot + colour * (2 * half);            // cos; sin at + half
   const float* const oth = slot + (colour ^ 1) * (2 * half);
   const int stride_z = lat.ty + 2;  // rows per plane in shared memory
@@ -932,18 +978,18 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
 
   Spins4 t_own{};
   if (act) {
-    t_own = ld_spins(own + offz, half);
+    t_own = ld_spins(sg, own + offz, half);
     const bool zlo = tz == 0, zhi = tz == TZa - 1, ylo = ty == 0, yhi = ty == TYa - 1;
     const uint32_t pzm = static_cast<uint32_t>(z == 0 ? L - 1 : z - 1) * PS;
     const uint32_t pzp = static_cast<uint32_t>(z + 1 == L ? 0 : z + 1) * PS;
     const uint32_t oym = static_cast<uint32_t>(H * (y == 0 ? L - 1 : y - 1) + 4 * tx);
     const uint32_t oyp = static_cast<uint32_t>(H * (y + 1 == L ? 0 : y + 1) + 4 * tx);
-    const Spins4 a0 = ld_spins(oth + offz, half);
+    const Spins4 a0 = ld_spins(sg, oth + offz, half);
     Spins4 a1 = a0, a2 = a0, a3 = a0, a4 = a0;
-    if (zlo) a1 = ld_spins(oth + offy + pzm, half);
-    if (zhi) a2 = ld_spins(oth + offy + pzp, half);
-    if (ylo) a3 = ld_spins(oth + oym + static_cast<uint32_t>(z) * PS, half);
-    if (yhi) a4 = ld_spins(oth + oyp + static_cast<uint32_t>(z) * PS, half);
+    if (zlo) a1 = ld_spins(sg, oth + offy + pzm, half);
+    if (zhi) a2 = ld_spins(sg, oth + offy + pzp, half);
+    if (ylo) a3 = ld_spins(sg, oth + oym + static_cast<uint32_t>(z) * PS, half);
+    if (yhi) a4 = ld_spins(sg, oth + oyp + static_cast<uint32_t>(z) * PS, half);
     put_row(row_ptr(ty + 1, tz + 1), H, tx, a0);
     if (zlo) put_row(row_ptr(ty + 1, 0), H, tx, a1);
     if (zhi) put_row(row_ptr(ty + 1, TZa + 1), H, tx, a2);
@@ -982,7 +1028,7 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
 #pragma unroll
       for (int j = 0; j < kNumSums; ++j) acc_out[j] = stepv[j];
     }
-    if (MODE != kMeasureOnly) st_spins(own + offz, half, nw.c, nw.s);
+    if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
   }
   // The shared rows may be overwritten by the caller's next tile.
   __syncthreads();

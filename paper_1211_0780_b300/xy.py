@@ -10,15 +10,19 @@ device is missing, the calls raise.
 from __future__ import annotations
 
 import ctypes
+import json
 import os
 from typing import Sequence
 
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libxy.so")
+# The library: libxy.so, or the bounds-checked debug build (libxy_check.so,
+# compiled with XY_BOUNDS_CHECK) when XY_LIBRARY names it.
+LIB_PATH = os.environ.get("XY_LIBRARY") or os.path.join(_HERE, "libxy.so")
+CHECK_LIB_PATH = os.path.join(_HERE, "libxy_check.so")
 
-XY_OK, XY_ERR_ARG, XY_ERR_CUDA, XY_ERR_TIMEOUT, XY_ERR_STATE, XY_ERR_NOMEM = 0, -1, -2, -3, -4, -5
+XY_OK, XY_ERR_ARG, XY_ERR_CUDA, XY_ERR_TIMEOUT, XY_ERR_STATE, XY_ERR_NOMEM, XY_ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6
 EXEC_PLAIN, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2
 TAG_INIT, TAG_MET, TAG_PT = 1, 2, 3
 TILE_MARCH, TILE_BLOCK, TILE_STREAM, TILE_DIRECT = 0, 1, 2, 3
@@ -136,6 +140,53 @@ def _require_cuda():
     return torch
 
 
+def _library_id() -> str:
+    """Content hash of the loaded libxy.so (a rebuilt library invalidates
+    cached tile choices)."""
+    import hashlib
+    h = hashlib.sha1()
+    with open(LIB_PATH, "rb") as f:
+        for chunk in iter(lambda: f.read(1 << 20), b""):
+            h.update(chunk)
+    return h.hexdigest()[:16]
+
+
+def autotune_cache_key(sim, n_metropolis: int, n_overrelax: int, device: str | None = None,
+                       library: str | None = None) -> str:
+    """Key of one autotune result: lattice sizes, replicas, pass counts,
+    execution mode, device name and library build."""
+    if device is None:
+        import torch
+        device = torch.cuda.get_device_name()
+    if library is None:
+        library = _library_id()
+    return json.dumps({"L": list(sim.L), "R": list(sim.R), "nM": int(n_metropolis), "nOR": int(n_overrelax),
+                       "exec": int(getattr(sim, "exec_mode", EXEC_PLAIN)), "device": device,
+                       "library": library}, sort_keys=True)
+
+
+def load_tile_cache(path: str) -> dict:
+    """The tile cache at `path` ({key: [[ty, tz, kind], ...]}), empty if the
+    file is missing or unreadable."""
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except (OSError, ValueError):
+        return {}
+    return {k: [tuple(int(x) for x in t) for t in v] for k, v in data.items()} if isinstance(data, dict) else {}
+
+
+def store_tile_cache(path: str, key: str, tiles) -> None:
+    """Adds one result to the tile cache at `path` (written through a
+    temporary file and renamed, so readers never see a partial file)."""
+    data = {k: [list(t) for t in v] for k, v in load_tile_cache(path).items()}
+    data[key] = [list(map(int, t)) for t in tiles]
+    tmp = f"{path}.{os.getpid()}.tmp"
+    with open(tmp, "w") as f:
+        json.dump(data, f, indent=1, sort_keys=True)
+    os.replace(tmp, path)
+
+
 class Simulation:
     """Replicas of periodic L^3 XY lattices on one GPU (one exchange ladder
     per lattice).  Wraps one xy_ctx over a torch-allocated workspace."""
@@ -185,6 +236,7 @@ class Simulation:
     # -- the sweep path ------------------------------------------------
     def set_exec(self, mode: int) -> None:
         _check(lib().xy_set_exec(self._ctx, int(mode)), "xy_set_exec")
+        self.exec_mode = int(mode)
 
     def sweep(self, n_metropolis: int, n_overrelax: int, n_sweeps: int = 1,
               measure_every: int = 0, pt_swap_every: int = 0) -> None:
@@ -312,9 +364,24 @@ class Simulation:
                "xy_get_tile")
         return int(ty.value), int(tz.value), int(k.value)
 
-    def autotune(self, n_metropolis: int, n_overrelax: int):
+    def autotune(self, n_metropolis: int, n_overrelax: int, cache: str | None = None):
+        """Tile search (xy_autotune); returns each lattice's (ty, tz, kind).
+        With `cache` (a JSON file path) a previous result for the same
+        lattices, replicas, pass counts, execution mode, device and library
+        build is applied with xy_set_tile instead of timing again, and a new
+        result is stored (see autotune_cache_key)."""
+        key = autotune_cache_key(self, n_metropolis, n_overrelax) if cache else None
+        if key is not None:
+            tiles = load_tile_cache(cache).get(key)
+            if tiles is not None and len(tiles) == len(self.L):
+                for i, (ty, tz, kind) in enumerate(tiles):
+                    self.set_tile(i, ty, tz, kind)
+                return [self.get_tile(i) for i in range(len(self.L))]
         _check(lib().xy_autotune(self._ctx, int(n_metropolis), int(n_overrelax)), "xy_autotune")
-        return [self.get_tile(i) for i in range(len(self.L))]
+        tiles = [self.get_tile(i) for i in range(len(self.L))]
+        if key is not None:
+            store_tile_cache(cache, key, tiles)
+        return tiles
 
     def device_status(self) -> int:
         s = ctypes.c_int(0)

@@ -78,3 +78,19 @@ def test_ladder_two_replicas_and_bad_betas():
         sim.set_betas(0, [0.40, 0.39, 0.44])
     sim.set_betas(0, [0.41, 0.42, 0.43])
     np.testing.assert_array_equal(sim.ladder(0), [0.41, 0.42, 0.43])
+
+
+def test_autotune_cache_reuses_tiles(tmp_path):
+    """A second context with the same lattices, passes and mode takes its
+    tiles from the JSON cache (xy_set_tile) and gets the first one's."""
+    from paper_1211_0780_b300 import xy
+    path = str(tmp_path / "tiles.json")
+    a = xy.Simulation(24, 2, [0.44, 0.45], 7)
+    t1 = a.autotune(1, 1, cache=path)
+    b = xy.Simulation(24, 2, [0.44, 0.45], 8)
+    t2 = b.autotune(1, 1, cache=path)
+    assert t1 == t2 == [b.get_tile(0)]
+    assert len(xy.load_tile_cache(path)) == 1
+    b.set_exec(xy.EXEC_GRAPH)
+    b.autotune(1, 1, cache=path)  # another mode: another entry
+    assert len(xy.load_tile_cache(path)) == 2
