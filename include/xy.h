@@ -199,6 +199,17 @@ int xy_set_state(xy_ctx *ctx, const float *host_angles, const int32_t *perm,
 int xy_get_packed(xy_ctx *ctx, float *host_packed);
 int xy_set_packed(xy_ctx *ctx, const float *host_packed);
 
+/* The spins as FP32 angles in the packed order (for each slot: colour 0's
+ * N/2 angles, then colour 1's, at p = (x >> 1) + (L/2)(y + L z)); a host
+ * buffer of sum over slots of L^3 floats, half the bytes of the packed
+ * vectors.  set: stream-ordered copy into the workspace and conversion on
+ * the device with sincosf (the values must be finite; they are not
+ * inspected); get: atan2 on the device, wrapped into [0, 2 pi) as
+ * xy_get_state.  Both return after the copy completes (pinned memory makes
+ * it asynchronous to the host until then). */
+int xy_set_packed_angles(xy_ctx *ctx, const float *host_angles);
+int xy_get_packed_angles(xy_ctx *ctx, float *host_angles);
+
 /* Replaces the betas of ladder `lattice` (n_replicas ascending finite
  * values) in a running context: every slot takes the new beta of its beta
  * index (the exchange permutation is kept).  Used by an adaptive ladder

@@ -65,6 +65,23 @@ __global__ void k_from_angles(const float* __restrict__ in, long long N, float* 
   }
 }
 
+// In place: the angle stored in each cos slot of n_slots slots (each 2N
+// floats: colour 0's N/2 cosines, its N/2 sines, colour 1's ...) becomes
+// the (cos, sin) pair, with sincosf as k_from_angles uses it.
+__global__ void k_angles_in_place(float* __restrict__ spins, long long N, int n_slots) {
+  const long long half = N >> 1;
+  const long long total = static_cast<long long>(n_slots) * N;  // angles
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = i / N, q = i - r * N, c = q / half, p = q - c * half;
+    float* base = spins + 2 * r * N + c * N;
+    float sn, cs;
+    sincosf(base[p], &sn, &cs);
+    base[p] = cs;
+    base[half + p] = sn;
+  }
+}
+
 // One half-sweep of one lattice: grid (tiles per slot, R); block (L/8, ty) for
 // the march kind, (L/8, ty, tz) for the block kind, 32 (ceil(L ty / 256) + 1)
 // threads in x for the stream kind.  MEAS: the variant that

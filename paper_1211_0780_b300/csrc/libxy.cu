@@ -956,6 +956,46 @@ int xy_set_packed(xy_ctx* c, const float* host_packed) {
   return XY_OK;
 }
 
+int xy_set_packed_angles(xy_ctx* c, const float* host_angles) {
+  XY_ENTER(c);
+  if (!host_angles) return XY_ERR_ARG;
+  size_t at = 0;
+  for (const LatHost& h : c->lat) {
+    const long long N = h.N();
+    float* dst = c->spins() + h.spin_off;
+    // each slot's colour 0 and colour 1 angles (N/2 each) into the two
+    // colours' cos arrays (N floats apart), then converted in place
+    XY_TRY(c, cudaMemcpy2DAsync(dst, static_cast<size_t>(N) * 4, host_angles + at, static_cast<size_t>(N / 2) * 4,
+                                static_cast<size_t>(N / 2) * 4, static_cast<size_t>(2 * h.R), cudaMemcpyHostToDevice,
+                                c->stream));
+    const long long n = N * h.R;
+    k_angles_in_place<<<static_cast<int>(std::min<long long>((n + 255) / 256, 4096)), 256, 0, c->stream>>>(dst, N, h.R);
+    XY_CHECK_LAUNCH(c);
+    at += static_cast<size_t>(n);
+  }
+  XY_TRY(c, cudaStreamSynchronize(c->stream));
+  return XY_OK;
+}
+
+int xy_get_packed_angles(xy_ctx* c, float* host_angles) {
+  XY_ENTER(c);
+  if (!host_angles) return XY_ERR_ARG;
+  size_t at = 0;
+  float* stage = c->at<float>(c->lay.staging);
+  for (const LatHost& h : c->lat) {
+    const long long N = h.N();
+    for (int r = 0; r < h.R; ++r) {
+      k_to_angles<<<conv_blocks(N), 256, 0, c->stream>>>(c->spins() + h.spin_off + 2 * r * N, N, stage);
+      XY_CHECK_LAUNCH(c);
+      XY_TRY(c, cudaMemcpyAsync(host_angles + at, stage, static_cast<size_t>(N) * 4, cudaMemcpyDeviceToHost,
+                                c->stream));
+      XY_TRY(c, cudaStreamSynchronize(c->stream));
+      at += static_cast<size_t>(N);
+    }
+  }
+  return sync_checked(c);
+}
+
 int xy_get_accepts(xy_ctx* c, uint64_t* met, uint64_t* swap) {
   XY_ENTER(c);
   if (met) XY_TRY(c, cudaMemcpyAsync(met, c->ws + c->lay.acc_met, c->n_slots * 8, cudaMemcpyDeviceToHost, c->stream));

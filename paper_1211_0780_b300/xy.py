@@ -74,6 +74,8 @@ _SIGNATURES = {
     "xy_get_accepts": (_I, [_P, _P, _P]),
     "xy_get_packed": (_I, [_P, _P]),
     "xy_set_packed": (_I, [_P, _P]),
+    "xy_get_packed_angles": (_I, [_P, _P]),
+    "xy_set_packed_angles": (_I, [_P, _P]),
     "xy_debug_draws": (_I, [_P, _I, _I, _I, _U64, _P]),
     "xy_set_tile": (_I, [_P, _I, _I, _I, _I]),
     "xy_get_tile": (_I, [_P, _I, _P, _P, _P]),
@@ -313,8 +315,30 @@ class Simulation:
         return out
 
     def set_packed(self, src) -> None:
-        ptr = src.data_ptr() if hasattr(src, "data_ptr") else _ptr(np.ascontiguousarray(src, dtype=np.float32))
+        buf = src if hasattr(src, "data_ptr") else np.ascontiguousarray(src, dtype=np.float32)
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else _ptr(buf)  # buf outlives the call
         _check(lib().xy_set_packed(self._ctx, ptr), "xy_set_packed")
+
+    def n_packed_angles(self) -> int:
+        """Floats of the state as angles: every site of every slot."""
+        return int(sum(L ** 3 * R for L, R in zip(self.L, self.R)))
+
+    def get_packed_angles(self, out=None):
+        """All spins as angles in [0, 2 pi), packed order (per slot: colour 0
+        then colour 1), into ``out`` (numpy float32 or a pinned CPU torch
+        tensor of n_packed_angles() floats)."""
+        if out is None:
+            out = np.zeros(self.n_packed_angles(), dtype=np.float32)
+        ptr = out.data_ptr() if hasattr(out, "data_ptr") else _ptr(out)
+        _check(lib().xy_get_packed_angles(self._ctx, ptr), "xy_get_packed_angles")
+        return out
+
+    def set_packed_angles(self, src) -> None:
+        """Sets every spin from finite angles in the packed order (converted
+        on the device); half the bytes of set_packed."""
+        buf = src if hasattr(src, "data_ptr") else np.ascontiguousarray(src, dtype=np.float32)
+        ptr = buf.data_ptr() if hasattr(buf, "data_ptr") else _ptr(buf)
+        _check(lib().xy_set_packed_angles(self._ctx, ptr), "xy_set_packed_angles")
 
     def counters(self) -> np.ndarray:
         """{Metropolis passes, sweeps, exchange events, records} (no state copy)."""

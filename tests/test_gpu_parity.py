@@ -98,6 +98,31 @@ def test_state_roundtrip_and_layout():
     assert np.array_equal(s.get_packed(), packed)
 
 
+def test_packed_angles_match_set_state_and_get_state():
+    """set_packed_angles converts on the device exactly as set_state does
+    (the same sincosf on the same angles), and get_packed_angles returns the
+    angles of get_state in the packed order."""
+    from paper_1211_0780_b300.inputs import random_angles
+    L, R = 24, 2
+    N, H = L ** 3, L // 2
+    z, y, x = np.meshgrid(*(np.arange(L),) * 3, indexing="ij")
+    idx = ((x + y + z) % 2) * (N // 2) + (x >> 1) + H * (y + L * z)  # natural -> packed order
+    th = [random_angles((L, L, L), 30 + r).astype(np.float32) for r in range(R)]
+    a = sim(L, R, [0.44, 0.45])
+    a.set_state(th)
+    packed = np.zeros(R * N, np.float32)
+    for r in range(R):
+        packed[r * N + idx] = th[r]
+    b = sim(L, R, [0.44, 0.45])
+    b.set_packed_angles(packed)
+    assert np.array_equal(b.get_packed(), a.get_packed())
+    b.sweep(1, 2, 2)
+    back = b.get_packed_angles()
+    natural = b.get_state()[0]
+    for r in range(R):
+        assert np.array_equal(back[r * N + idx], natural[r])
+
+
 # ---------------------------------------------------------------- half-sweeps
 
 MARCH, BLOCK, STREAM, DIRECT = 0, 1, 2, 3
