@@ -487,6 +487,8 @@ def reweight_forward(series, beta0: float, betap, L: int, scratch=None):
     res = {name: out[i] for i, name in enumerate(OUT_ROWS)}
     res["U"] = obs[0]
     res["rhoL"] = obs[1]
+    # q2 = <m^4>/<m^2>^2 = 3(1 - U_L) (Eq. 11), the ratio of the paper's collapse
+    res["q2"] = 3.0 * (1.0 - obs[0])
     for i, name in enumerate(COV_ROWS):
         res["cov_" + name] = cov[i]
     res["_out"], res["_obs"], res["_cov"] = out, obs, cov

@@ -29,6 +29,8 @@ def test_forward_backward_match_oracle(L, T, K):
     ref = _oracle(s, beta0, bp, L)
     for key, gk in (("logZ", "logZ"), ("E", "E"), ("m2", "m2"), ("m4", "m4"), ("U", "U"), ("rhoL", "rhoL")):
         np.testing.assert_allclose(f[gk].cpu().numpy(), ref[key], rtol=1e-10, err_msg=key)
+    # q2 = <m^4>/<m^2>^2 of the collapse (Eq. 11), from the oracle's moments
+    np.testing.assert_allclose(f["q2"].cpu().numpy(), ref["m4"] / ref["m2"] ** 2, rtol=1e-10)
     # Relative to each curve's scale: dU/dbeta' crosses zero inside the grid.
     for row, key in ((0, "dU"), (1, "drhoL")):
         np.testing.assert_allclose(dobs[row].cpu().numpy(), ref[key], rtol=1e-8,
