@@ -557,7 +557,7 @@ def run_gpu(args):
     ach = BYTES_PER_UPDATE * half / (ms_or * 1e-3) / 1e9
     # DRAM bytes per launch from the committed ncu capture of this tile's
     # over-relaxation kernel (valid only for the tile that capture used)
-    traffic, traffic_note = None, "no ncu capture for this tile"
+    traffic, traffic_note, l2_bytes = None, "no ncu capture for this tile", None
     kind_names = {0: "march", 1: "block", 2: "stream", 3: "direct"}
     tile_name = f"{kind_names.get(tile[2], tile[2])}{tile[0]}x{tile[1]}"
     prof = os.path.join(ROOT, "profiles", f"overrelax_L160_{tile_name}_traffic.txt")
@@ -570,6 +570,7 @@ def run_gpu(args):
                     kv[k.strip()] = v.strip()
         if kv.get("tile") == ",".join(str(v) for v in tile):
             traffic = int(kv["dram_bytes_per_launch"])
+            l2_bytes = int(kv["l2_read_bytes_per_launch"]) if "l2_read_bytes_per_launch" in kv else None
             traffic_note = (f"cold-cache ncu capture (profiles/overrelax_L160_{tile_name}_ncu.md): the whole "
                             "(cos, sin) state read once, 8 B per site against the 4 B per site of the "
                             "12 B/update angle figure")
@@ -622,6 +623,14 @@ def run_gpu(args):
                     "bound": "alu", "unit": "FP64 instr/s", "achieved": extras["reweight"]["fp64_instr_per_s"],
                     "peak": peak, "frac": extras["reweight"]["fp64_instr_per_s"] / peak,
                     "peak_source": "xy_peak_probe FP64 FMA (measured here)"}
+    # context for the L2-resident state: the kernel's L2 -> L1 read bytes (ncu,
+    # warm) over its duration, against the measured L2 read bandwidth
+    l2_peak = extras.get("units", {}).get("l2_read_bytes") if isinstance(extras.get("units"), dict) else None
+    if l2_bytes and isinstance(l2_peak, float):
+        l2_ach = l2_bytes / (ms_or * 1e-3) / 1e9
+        roofline["l2"] = {"achieved": l2_ach, "peak": l2_peak / 1e9, "unit": "GB/s", "frac": l2_ach * 1e9 / l2_peak,
+                          "source": "L2->L1 read bytes per launch from a warm ncu capture; peak: xy_peak_probe "
+                                    "L2 read (measured here)"}
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, done = oracle_rate(args.cpu_seconds)
