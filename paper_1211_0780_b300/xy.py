@@ -210,10 +210,13 @@ class Simulation:
         nbytes = lb.xy_workspace_bytes(len(Ls), _ptr(self._Ls), _ptr(self._Rs), int(series_capacity))
         if nbytes == 0:
             raise XYError(XY_ERR_ARG, "xy_workspace_bytes")
-        self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
         if stream is None:
             stream = torch.cuda.current_stream()
         self.stream = stream
+        # allocated on the context's stream, so that the caching allocator
+        # orders any later reuse of the block after that stream's work
+        with torch.cuda.stream(stream):
+            self.workspace = torch.empty(int(nbytes), dtype=torch.uint8, device="cuda")
         self._ctx = ctypes.c_void_p()
         _check(lb.xy_init(ctypes.byref(self._ctx), len(Ls), _ptr(self._Ls), _ptr(self._Rs), _ptr(b),
                           self.seed, self.workspace.data_ptr(), int(nbytes), int(series_capacity),

@@ -123,6 +123,53 @@ def test_packed_angles_match_set_state_and_get_state():
         assert np.array_equal(back[r * N + idx], natural[r])
 
 
+def test_contexts_on_separate_streams_match_one_stream():
+    """Two contexts bound to two side streams, driven in turn as the
+    pipelined end-to-end loop drives them (each step's upload overlapping
+    the other context's sweeps, the sweeps of consecutive steps ordered by
+    events), end in the same states and records, bit for bit, as the same
+    two contexts on the current stream running the same steps one after
+    another."""
+    import torch
+    from paper_1211_0780_b300.inputs import random_angles
+    L, steps = 32, 6
+    N = L ** 3
+    inputs = [random_angles((N,), 60 + k).astype(np.float32) for k in range(steps)]
+
+    def make(stream=None):
+        c = sim(L, 1, [0.4542], series_capacity=16, stream=stream)
+        c.set_tile(0, 8, 8, DIRECT)
+        c.set_exec(1)  # CUDA graph
+        return c
+
+    ref = [make(), make()]
+    want = []
+    for k in range(steps):
+        c = ref[k % 2]
+        c.set_packed_angles(inputs[k])
+        c.sweep(1, 2, 3, measure_every=3)
+        want.append(c.read_series())
+    streams = [torch.cuda.Stream(), torch.cuda.Stream()]
+    two = [make(streams[0]), make(streams[1])]
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+    got = [None] * steps
+    for k in range(steps):
+        i = k % 2
+        two[i].set_packed_angles(inputs[k])
+        if k > 0:
+            streams[i].wait_event(done[1 - i])
+        two[i].sweep(1, 2, 3, measure_every=3)
+        done[i].record(streams[i])
+        if k > 0:
+            got[k - 1] = two[1 - i].read_series()
+    got[steps - 1] = two[(steps - 1) % 2].read_series()
+    torch.cuda.synchronize()
+    for k in range(steps):
+        assert len(got[k]) == 1 and got[k].tobytes() == want[k].tobytes()
+    for i in range(2):
+        assert np.array_equal(two[i].get_packed(), ref[i].get_packed())
+
+
 # ---------------------------------------------------------------- half-sweeps
 
 MARCH, BLOCK, STREAM, DIRECT = 0, 1, 2, 3
