@@ -642,12 +642,21 @@ def run_gpu(args):
     r = sims[(e2e_steps - 1) % 2].read_series()
     t_e2e = time.perf_counter() - t0
     assert len(r) == 1 and np.all(np.isfinite(r["E"]))
+    # the upload alone (copy + on-device conversion), CUDA events on its stream
+    ua, ub = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ua.record(streams[0])
+    for _ in range(5):
+        sims[0].set_packed_angles(pinned[0])
+    ub.record(streams[0])
+    ub.synchronize()
+    ms_up = ua.elapsed_time(ub) / 5
     e2e = {"value": world * e2e_steps * UPDATES_PER_STEP / (t_e2e * 1e9), "unit": UNIT,
            "h2d_bytes_per_step": int(n_ang * 4), "d2h_bytes_per_step": int(r.nbytes),
            "input": "FP32 angles of the 160^3 lattice, packed order, pinned host memory",
            "pipelined": "two simulations on two streams take alternate steps; step k+1's upload overlaps "
                         "step k's sweeps, the sweeps of consecutive steps never overlap",
-           "serial_value": world * e2e_steps * UPDATES_PER_STEP / (t_serial * 1e9)}
+           "serial_value": world * e2e_steps * UPDATES_PER_STEP / (t_serial * 1e9),
+           "upload_ms": ms_up, "upload_gbs": n_ang * 4 / (ms_up * 1e6), "sweeps_ms": ms_total / args.steps}
     torch.cuda.synchronize()
     del sims
 

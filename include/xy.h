@@ -117,7 +117,9 @@ int xy_init(xy_ctx **out, int n_lattices, const int *L, const int *n_replicas,
             const double *betas, uint64_t seed, void *d_workspace,
             size_t ws_bytes, int64_t series_capacity, void *stream);
 
-/* Releases the context (not the workspace).  Safe on NULL. */
+/* Releases the context (not the workspace) after synchronising its stream,
+ * so the caller may free the workspace once it returns.  Safe on NULL;
+ * always returns XY_OK (a failed context's error is not reported again). */
 int xy_destroy(xy_ctx *ctx);
 
 /* Selects how xy_sweep issues its work (XY_EXEC_*).  All modes give

@@ -650,6 +650,11 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
 
 int xy_destroy(xy_ctx* c) {
   if (!c) return XY_OK;
+  // let the context's work finish before its graphs, streams and events go
+  // (and before the caller frees the workspace); a failed context's error
+  // is not reported again here
+  cudaStreamSynchronize(c->stream);
+  if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
   drop_graphs(c);
   for (cudaStream_t s : c->lat_streams)
     if (s) cudaStreamDestroy(s);

@@ -94,3 +94,32 @@ def test_autotune_cache_reuses_tiles(tmp_path):
     b.set_exec(xy.EXEC_GRAPH)
     b.autotune(1, 1, cache=path)  # another mode: another entry
     assert len(xy.load_tile_cache(path)) == 2
+
+
+def test_readme_usage_runs():
+    """The usage example of the README at a small size: ladder run, series
+    split by coupling, differentiable reweighting, checkpoint and resume."""
+    import torch
+    from paper_1211_0780_b300 import multihist, xy
+    L, R = 16, 4
+    betas = np.linspace(0.450, 0.458, R)
+    sim = xy.Simulation(L, R, betas, seed=0x5EED2012)
+    sim.autotune(1, 3)
+    sim.set_exec(xy.EXEC_GRAPH)
+    sim.sweep(1, 3, 20, measure_every=1, pt_swap_every=1)
+    rec = sim.read_series()
+    assert len(rec) == 20 * R
+    series, b = multihist.series_from_records(rec, L, R)
+    bp = torch.linspace(0.4530, 0.4555, 64, dtype=torch.float64, device="cuda", requires_grad=True)
+    U, rhoL = xy.reweight(series[2], b[2], bp, L)
+    U.sum().backward()
+    assert torch.isfinite(bp.grad).all() and torch.isfinite(rhoL).all()
+    packed = sim.get_packed()
+    _, perm, counters = sim.get_state()
+    resumed = xy.Simulation(L, R, betas, seed=0x5EED2012)
+    resumed.set_packed(packed)
+    resumed.set_state(None, perm, counters)
+    sim.sweep(1, 3, 3, measure_every=1, pt_swap_every=1)
+    resumed.sweep(1, 3, 3, measure_every=1, pt_swap_every=1)
+    assert np.array_equal(sim.get_packed(), resumed.get_packed())
+    assert sim.read_series().tobytes() == resumed.read_series().tobytes()
