@@ -545,7 +545,8 @@ def run_gpu(args):
     torch.cuda.synchronize()
     barrier(world)
     clk = clocks.stop()
-    ms_local = sum(a.elapsed_time(b) for a, b in evs)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    ms_local = sum(step_ms)
     ms_total = allreduce_max(ms_local, world)
     recs = sim.read_series()
     assert len(recs) == args.steps and np.all(np.isfinite(recs["E"]))
@@ -700,7 +701,10 @@ def run_gpu(args):
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_total / args.steps, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
+            "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms),
+                        "note": "this rank's per-step CUDA-event times"},
+            "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "L": L_MAIN, "replicas": 1, "beta": BETA_MAIN,
                        "sweeps_per_step": SWEEPS_PER_STEP, "updates_per_step": UPDATES_PER_STEP,
