@@ -373,9 +373,10 @@ def bench_reweight(reps: int):
         per_L[str(L)] = ms
         total_ms += ms
     pairs = 4 * K * T
-    # 13 FP64 instructions per (beta', sample) pair: the weight step, w*e and
-    # the 11 accumulations (2 adds + 9 fused multiply-adds)
-    fp64_ops = 13.0 * pairs
+    # 12 FP64 instructions per (beta', sample) pair: the weight step and the
+    # 11 accumulations (1 add + 10 fused multiply-adds by w; the products of
+    # e with the observables are formed once per sample and block)
+    fp64_ops = 12.0 * pairs
     return {"workload": "4 series (L=32,64,128,160) x T=1e6 samples x K=4096 beta', forward+backward, FP64",
             "pairs_per_ns": pairs / (total_ms * 1e6), "ms_total": total_ms, "ms_per_L": per_L,
             "fp64_instr_per_s": fp64_ops / (total_ms * 1e-3)}

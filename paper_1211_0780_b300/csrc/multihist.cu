@@ -282,6 +282,9 @@ __global__ void __launch_bounds__(kBlock) k_mh_sums(int64_t T, int64_t t_per_chu
                                                     const double* __restrict__ betap, const double* __restrict__ kmax,
                                                     const double* __restrict__ stats, double* __restrict__ sums) {
   __shared__ double s_E[kChunk], s_l[kChunk], s_m2[kChunk], s_m4[kChunk], s_c[kChunk], s_s2[kChunk], s_rho[kChunk];
+  // e = E - Ebar and its products with the observables, staged once per
+  // block so that every accumulation below is one fused multiply-add by w
+  __shared__ double s_e[kChunk], s_ee[kChunk], s_em2[kChunk], s_em4[kChunk], s_ec[kChunk], s_es2[kChunk];
   const int chunk = blockIdx.y;
   const int64_t t0 = chunk * t_per_chunk, t1 = (t0 + t_per_chunk < T) ? t0 + t_per_chunk : T;
   const int k0 = (blockIdx.x * blockDim.x + threadIdx.x) * kKT;
@@ -318,29 +321,36 @@ __global__ void __launch_bounds__(kBlock) k_mh_sums(int64_t T, int64_t t_per_chu
       s_c[j] = static_cast<double>(c[t]) + static_cast<double>(c[T + t]) + static_cast<double>(c[2 * T + t]);
       s_s2[j] = static_cast<double>(s2[t]) + static_cast<double>(s2[T + t]) + static_cast<double>(s2[2 * T + t]);
       s_rho[j] = exp(-step * (s_E[j] - Ebar));
+      const double e = s_E[j] - Ebar;
+      s_e[j] = e;
+      s_ee[j] = e * e;
+      s_em2[j] = e * s_m2[j];
+      s_em4[j] = e * s_m4[j];
+      s_ec[j] = e * s_c[j];
+      s_es2[j] = e * s_s2[j];
     }
     __syncthreads();
     if (nk > 0) {
       for (int j = 0; j < n; ++j) {
-        const double Et = s_E[j], e = Et - Ebar, lD = s_l[j];
+        const double Et = s_E[j], e = s_e[j], lD = s_l[j];
         const double x2 = s_m2[j], x4 = s_m4[j], xc = s_c[j], xs = s_s2[j];
+        const double ee = s_ee[j], ex2 = s_em2[j], ex4 = s_em4[j], exc = s_ec[j], exs = s_es2[j];
         double w = exp(fma(-b[0], Et, -lD) - mx[0]);
         const double rho = s_rho[j];
 #pragma unroll
         for (int i = 0; i < kKT; ++i) {
           if (i > 0) w = even ? w * rho : exp(fma(-b[i], Et, -lD) - mx[i]);
-          const double we = w * e;
           S[i][0] += w;
-          S[i][1] += we;
-          S[i][2] = fma(we, e, S[i][2]);
+          S[i][1] = fma(w, e, S[i][1]);
+          S[i][2] = fma(w, ee, S[i][2]);
           S[i][3] = fma(w, x2, S[i][3]);
-          S[i][4] = fma(we, x2, S[i][4]);
+          S[i][4] = fma(w, ex2, S[i][4]);
           S[i][5] = fma(w, x4, S[i][5]);
-          S[i][6] = fma(we, x4, S[i][6]);
+          S[i][6] = fma(w, ex4, S[i][6]);
           S[i][7] = fma(w, xc, S[i][7]);
-          S[i][8] = fma(we, xc, S[i][8]);
+          S[i][8] = fma(w, exc, S[i][8]);
           S[i][9] = fma(w, xs, S[i][9]);
-          S[i][10] = fma(we, xs, S[i][10]);
+          S[i][10] = fma(w, exs, S[i][10]);
         }
       }
     }

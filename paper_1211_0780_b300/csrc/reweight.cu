@@ -163,7 +163,10 @@ __global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chu
                                                     const float* __restrict__ s2, double beta0, int K,
                                                     const double* __restrict__ betap, const double* __restrict__ stats,
                                                     double* __restrict__ sums) {
+  // the sample's observables and their products with e, staged once per
+  // block so that every accumulation below is one fused multiply-add by w
   __shared__ double s_e[kChunk], s_m2[kChunk], s_m4[kChunk], s_c[kChunk], s_s2[kChunk], s_rho[kChunk];
+  __shared__ double s_ee[kChunk], s_em2[kChunk], s_em4[kChunk], s_ec[kChunk], s_es2[kChunk];
   const int chunk = blockIdx.y;
   int64_t t0, t1;
   chunk_range(chunk, T, t_per_chunk, n_bins, chunks_per_bin, t0, t1);
@@ -212,29 +215,34 @@ __global__ void __launch_bounds__(kBlock) k_rw_sums(int64_t T, int64_t t_per_chu
       s_c[j] = static_cast<double>(c[t]) + static_cast<double>(c[T + t]) + static_cast<double>(c[2 * T + t]);
       s_s2[j] = static_cast<double>(s2[t]) + static_cast<double>(s2[T + t]) + static_cast<double>(s2[2 * T + t]);
       s_rho[j] = exp(-step * (s_e[j] - emid));
+      s_ee[j] = s_e[j] * s_e[j];
+      s_em2[j] = s_e[j] * s_m2[j];
+      s_em4[j] = s_e[j] * s_m4[j];
+      s_ec[j] = s_e[j] * s_c[j];
+      s_es2[j] = s_e[j] * s_s2[j];
     }
     __syncthreads();
     if (nk > 0) {
       for (int j = 0; j < n; ++j) {
         const double e = s_e[j], x2 = s_m2[j], x4 = s_m4[j], xc = s_c[j], xs = s_s2[j];
+        const double ee = s_ee[j], ex2 = s_em2[j], ex4 = s_em4[j], exc = s_ec[j], exs = s_es2[j];
         const double de = e - eref;
         double w = exp(-d[0] * de);
         const double rho = even ? s_rho[j] * rho_c : 0.0;
 #pragma unroll
         for (int i = 0; i < kKT; ++i) {
           if (i > 0) w = even ? w * rho : exp(-d[i] * de);
-          const double we = w * e;
           S[i][0] += w;
-          S[i][1] += we;
-          S[i][2] = fma(we, e, S[i][2]);
+          S[i][1] = fma(w, e, S[i][1]);
+          S[i][2] = fma(w, ee, S[i][2]);
           S[i][3] = fma(w, x2, S[i][3]);
-          S[i][4] = fma(we, x2, S[i][4]);
+          S[i][4] = fma(w, ex2, S[i][4]);
           S[i][5] = fma(w, x4, S[i][5]);
-          S[i][6] = fma(we, x4, S[i][6]);
+          S[i][6] = fma(w, ex4, S[i][6]);
           S[i][7] = fma(w, xc, S[i][7]);
-          S[i][8] = fma(we, xc, S[i][8]);
+          S[i][8] = fma(w, exc, S[i][8]);
           S[i][9] = fma(w, xs, S[i][9]);
-          S[i][10] = fma(we, xs, S[i][10]);
+          S[i][10] = fma(w, exs, S[i][10]);
         }
       }
     }
