@@ -554,6 +554,24 @@ def run_gpu(args):
     value = world * args.steps * UPDATES_PER_STEP / (ms_total * 1e6)
     launches_per_step = SWEEPS_PER_STEP * (NM_MAIN + NOR_MAIN) * 2 + 2  # half-sweeps + finish + advance
 
+    # Four more runs of the same K steps (same flush, same events), after the
+    # timed region: the median of the five runs, as context beside `value`.
+    runs = [value]
+    for _ in range(4):
+        ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+        barrier(world)
+        torch.cuda.synchronize()
+        for a, b in ev2:
+            flush.zero_()
+            a.record(st)
+            step()
+            b.record(st)
+        torch.cuda.synchronize()
+        barrier(world)
+        ms_r = allreduce_max(sum(a.elapsed_time(b) for a, b in ev2), world)
+        runs.append(world * args.steps * UPDATES_PER_STEP / (ms_r * 1e6))
+        assert len(sim.read_series()) == args.steps  # one record per step, drained per run
+
     # --- per-kernel durations (CUDA events on the launching stream) ----------
     # Graph-captured runs of one pass type, each one CUDA graph (the library
     # captures up to 16 sweeps per graph): 16 sweeps of 0 + 5 passes = 160
@@ -705,6 +723,8 @@ def run_gpu(args):
             "warmup": args.warmup, "ms_per_step": ms_total / args.steps,
             "step_ms": {"median": statistics.median(step_ms), "min": min(step_ms), "max": max(step_ms),
                         "note": "this rank's per-step CUDA-event times"},
+            "runs": {"values": runs, "median": statistics.median(runs),
+                     "note": "value is the first run; four more runs of the same K steps follow it"},
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOAD, "L": L_MAIN, "replicas": 1, "beta": BETA_MAIN,
