@@ -676,7 +676,9 @@ def run_gpu(args):
            "pipelined": "two simulations on two streams take alternate steps; step k+1's upload overlaps "
                         "step k's sweeps, the sweeps of consecutive steps never overlap",
            "serial_value": world * e2e_steps * UPDATES_PER_STEP / (t_serial * 1e9),
-           "upload_ms": ms_up, "upload_gbs": n_ang * 4 / (ms_up * 1e6), "sweeps_ms": ms_total / args.steps}
+           "upload_ms": ms_up, "upload_gbs": n_ang * 4 / (ms_up * 1e6), "sweeps_ms": ms_total / args.steps,
+           "bound": "host-to-device link (the upload is longer than the sweeps)" if ms_up > ms_total / args.steps
+                    else "sweeps (the upload is hidden behind them)"}
     torch.cuda.synchronize()
     del sims
 
