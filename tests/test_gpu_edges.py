@@ -123,3 +123,38 @@ def test_readme_usage_runs():
     resumed.sweep(1, 3, 3, measure_every=1, pt_swap_every=1)
     assert np.array_equal(sim.get_packed(), resumed.get_packed())
     assert sim.read_series().tobytes() == resumed.read_series().tobytes()
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_empty_and_rejected_sweeps_change_nothing(mode):
+    """Zero sweeps is a no-op; zero passes per sweep and a series buffer
+    too small for the requested records are rejected before any work (the
+    state, counters and series stay as they were and the context stays
+    usable); a one-replica ladder with exchanges requested has no pair to
+    exchange and keeps its permutation."""
+    from paper_1211_0780_b300 import xy
+    sim = xy.Simulation([8, 16], [1, 3], [0.45, 0.44, 0.45, 0.46], seed=11, series_capacity=4)
+    sim.set_exec(mode)
+    sim.sweep(1, 2, 2, measure_every=1, pt_swap_every=1)
+    before = (sim.get_packed().copy(), sim.counters().copy(), sim.series_count())
+    _, perm0, _ = sim.get_state()
+
+    def unchanged():
+        return (np.array_equal(sim.get_packed(), before[0]) and np.array_equal(sim.counters(), before[1])
+                and sim.series_count() == before[2])
+
+    sim.sweep(1, 2, 0, measure_every=1, pt_swap_every=1)
+    assert unchanged()
+    with pytest.raises(xy.XYError) as e:
+        sim.sweep(0, 0, 3)
+    assert e.value.status == xy.XY_ERR_ARG and unchanged()
+    with pytest.raises(xy.XYError) as e:
+        sim.sweep(1, 2, 3, measure_every=1)  # 2 records buffered + 3 more > capacity 4
+    assert e.value.status == xy.XY_ERR_NOMEM and unchanged()
+    assert sim.device_status() == 0
+    sim.sweep(1, 2, 2, measure_every=1, pt_swap_every=1)  # still usable: fills the buffer
+    rec = sim.read_series()
+    assert len(rec) == 4 * 4 and np.all(np.isfinite(rec["E"]))
+    _, perm1, _ = sim.get_state()
+    assert perm1[0] == perm0[0] == 0  # the 8^3 lattice's one-replica ladder
+    assert sorted(perm1[1:]) == [0, 1, 2]
