@@ -326,9 +326,7 @@ const char *xy_strerror(int status);
  *   d_E[T] f64, d_m2[T] f32, d_m4[T] f32, d_c[3][T] f32, d_s2[3][T] f32,
  *   d_betap[K] f64.
  * Outputs (device, f64):
- *   d_out[7][K]  = rows {logZ, <E>, <m2>, <m4>, <csum>, <s2sum>, unused 0}
- *                  then the caller derives nothing: rows 5.. are documented
- *                  in the Python binding;
+ *   d_out[6][K]  = rows {logZ, <E>, <m2>, <m4>, <csum>, <s2sum>};
  *   d_obs[2][K]  = {U_L, rho_s L};
  *   d_cov[5][K]  = {var E, cov(m2,E), cov(m4,E), cov(csum,E), cov(s2sum,E)}.
  * d_scratch: xy_reweight_scratch_bytes(T, K) bytes of caller-owned device

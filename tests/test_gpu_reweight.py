@@ -78,3 +78,50 @@ def test_autograd_matches_finite_differences_and_fluctuation_formula():
     fm = xy.reweight_forward(s, 0.4542, b - h, L)
     fd = ((fp["U"] - fm["U"]) + 2.0 * (fp["rhoL"] - fm["rhoL"])).cpu().numpy() / (2 * h)
     np.testing.assert_allclose(g, fd, rtol=1e-6, atol=1e-6 * np.max(np.abs(fd)))
+
+
+@pytest.mark.parametrize("T", [2, 777])
+def test_constant_energy_series_closed_forms(T):
+    """A series whose energy never changes (the shortest series the call
+    accepts, two samples, and a longer one):
+    every weight is the same, so at any beta' the averages are the plain
+    means, log Z = log T - (beta' - beta0) E0, the covariances with E vanish,
+    dU_L/dbeta' = 0 and d(rho_s L)/dbeta' = -(L/3) <s2> (the explicit beta'
+    of Eq. 6 alone)."""
+    from paper_1211_0780_b300 import xy
+    rng = np.random.default_rng(T)
+    L, beta0, E0 = 8, 0.4542, -1234.5
+    m2 = rng.random(T).astype(np.float32)
+    s = {"E": np.full(T, E0), "m2": m2, "m4": (m2 * m2).astype(np.float32),
+         "c": rng.random((3, T)).astype(np.float32), "s2": rng.random((3, T)).astype(np.float32)}
+    bp = np.array([0.440, beta0, 0.470])
+    f = xy.reweight_forward(s, beta0, bp, L)
+    m2m = s["m2"].astype(np.float64).mean()
+    m4m = s["m4"].astype(np.float64).mean()
+    cm = s["c"].astype(np.float64).sum(axis=0).mean()
+    s2m = s["s2"].astype(np.float64).sum(axis=0).mean()
+    for k, b in enumerate(bp):
+        assert f["logZ"][k].item() == pytest.approx(np.log(T) - (b - beta0) * E0, rel=1e-12, abs=1e-9)
+        assert f["E"][k].item() == pytest.approx(E0, rel=1e-14)
+        assert f["m2"][k].item() == pytest.approx(m2m, rel=1e-12)
+        assert f["m4"][k].item() == pytest.approx(m4m, rel=1e-12)
+        assert f["csum"][k].item() == pytest.approx(cm, rel=1e-12)
+        assert f["s2sum"][k].item() == pytest.approx(s2m, rel=1e-12)
+        assert f["U"][k].item() == pytest.approx(1.0 - m4m / (3.0 * m2m * m2m), rel=1e-12)
+        assert f["rhoL"][k].item() == pytest.approx(L / 3.0 * (cm - b * s2m), rel=1e-12)
+        for name in xy.COV_ROWS:
+            assert abs(f["cov_" + name][k].item()) <= 1e-12
+    _, dobs = xy.reweight_backward(bp, L, f)
+    d = dobs.cpu().numpy()
+    np.testing.assert_allclose(d[0], 0.0, atol=1e-12)
+    np.testing.assert_allclose(d[1], -L / 3.0 * s2m, rtol=1e-12)
+
+
+def test_one_sample_series_is_rejected():
+    """T < 2 is an argument error (nothing is computed)."""
+    from paper_1211_0780_b300 import xy
+    s = {"E": np.array([-1.0]), "m2": np.ones(1, np.float32), "m4": np.ones(1, np.float32),
+         "c": np.ones((3, 1), np.float32), "s2": np.ones((3, 1), np.float32)}
+    with pytest.raises(xy.XYError) as e:
+        xy.reweight_forward(s, 0.4542, np.array([0.45]), 8)
+    assert e.value.status == xy.XY_ERR_ARG

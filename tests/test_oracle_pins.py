@@ -387,3 +387,26 @@ def test_reweight_derivative_matches_finite_difference():
     rm = oracle.reweight_observables(*args, b - h, 16)
     for key, dkey in (("U", "dU"), ("rhoL", "drhoL")):
         np.testing.assert_allclose(r0[dkey], (rp[key] - rm[key]) / (2 * h), rtol=1e-6)
+
+
+@pytest.mark.parametrize("T", [1, 777])
+def test_reweight_constant_energy_closed_forms(T):
+    """Constant energy E0: equal weights at every beta', so the averages are
+    the plain means, log Z = log T - (beta' - beta0) E0, the covariances
+    vanish, dU/dbeta' = 0 and d(rho_s L)/dbeta' = -(L/3) <s2> (Eq. 6's
+    explicit beta' alone).  A sign slip in that explicit term, or in the
+    shift of log Z, fails here."""
+    rng = np.random.default_rng(T)
+    L, beta0, E0 = 8, 0.4542, -1234.5
+    m2 = rng.random(T)
+    c, s2 = rng.random((T, 3)), rng.random((T, 3))
+    bp = np.array([0.440, beta0, 0.470])
+    r = oracle.reweight_observables(np.full(T, E0), m2, m2 * m2, c, s2, beta0, bp, L)
+    m2m, m4m, cm, s2m = m2.mean(), (m2 * m2).mean(), c.sum(1).mean(), s2.sum(1).mean()
+    np.testing.assert_allclose(r["logZ"], np.log(T) - (bp - beta0) * E0, rtol=1e-13, atol=1e-10)
+    np.testing.assert_allclose(r["E"], E0, rtol=1e-13)  # T additions of w E0: T eps at most
+    np.testing.assert_allclose(r["U"], 1.0 - m4m / (3.0 * m2m * m2m), rtol=1e-13)
+    np.testing.assert_allclose(r["rhoL"], L / 3.0 * (cm - bp * s2m), rtol=1e-13)
+    # the covariances <O E> - <O><E> cancel terms of size |E0| <O> ~ 10^3 to ~1e-12
+    np.testing.assert_allclose(r["dU"], 0.0, atol=1e-10)
+    np.testing.assert_allclose(r["drhoL"], -L / 3.0 * s2m, rtol=0, atol=1e-10)
