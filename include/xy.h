@@ -147,8 +147,9 @@ int xy_set_exec(xy_ctx *ctx, int mode);
 int xy_sweep(xy_ctx *ctx, int n_metropolis, int n_overrelax, int n_sweeps,
              int measure_every, int pt_swap_every);
 
-/* One Metropolis half-sweep of `colour` on every slot with Metropolis-pass
- * counter `mpass` (the counters of the context are not advanced). */
+/* One Metropolis half-sweep of `colour` on every slot (Sec. II, the
+ * checkerboard update of Fig. 2) with Metropolis-pass counter `mpass` (the
+ * counters of the context are not advanced). */
 int xy_metropolis_half(xy_ctx *ctx, int colour, uint64_t mpass);
 
 /* One over-relaxation half-sweep of `colour` on every slot (Eq. 2). */
@@ -166,7 +167,8 @@ int xy_measure(xy_ctx *ctx, xy_record *host_out);
  * ladders; synchronises the stream. */
 int xy_pt_swap(xy_ctx *ctx, int parity, int *n_accepted_out);
 
-/* Copies the records appended since the last read (oldest first) into
+/* The measurement series (Sec. II: the per-sweep values that are binned).
+ * Copies the records appended since the last read (oldest first) into
  * host_buf (room for `cap` records) and empties the buffer.  *n_out = the
  * number copied.  XY_ERR_NOMEM if cap is too small (nothing is copied). */
 int xy_read_series(xy_ctx *ctx, xy_record *host_buf, int64_t cap,
@@ -175,7 +177,8 @@ int xy_read_series(xy_ctx *ctx, xy_record *host_buf, int64_t cap,
 /* Number of records waiting in the series buffer. */
 int xy_series_count(xy_ctx *ctx, int64_t *n_out);
 
-/* State for parity checks and checkpoints.  host_angles: all slots
+/* The spin configuration theta_i of H = -J sum cos(theta_i - theta_j)
+ * (Sec. II), for parity checks and checkpoints.  host_angles: all slots
  * concatenated, natural layout, sum over slots of L^3 floats; get_state
  * returns atan2(sin, cos) of the stored vectors taken into [0, 2 pi),
  * set_state stores (cos, sin) of the given angles (sincosf; every angle
@@ -212,7 +215,8 @@ int xy_set_packed(xy_ctx *ctx, const float *host_packed);
 int xy_set_packed_angles(xy_ctx *ctx, const float *host_angles);
 int xy_get_packed_angles(xy_ctx *ctx, float *host_angles);
 
-/* Replaces the betas of ladder `lattice` (n_replicas ascending finite
+/* The parallel-tempering temperature set (Sec. II, Eq. 3).
+ * Replaces the betas of ladder `lattice` (n_replicas ascending finite
  * values) in a running context: every slot takes the new beta of its beta
  * index (the exchange permutation is kept).  Used by an adaptive ladder
  * (xy_ladder_update); counters, states and records are untouched. */
@@ -233,12 +237,14 @@ int xy_set_betas(xy_ctx *ctx, int lattice, const double *betas);
 int xy_ladder_update(int R, const double *betas, const double *acceptance,
                      double damping, double *new_betas);
 
-/* Accepted-move counters: met[total slots] = accepted Metropolis proposals
+/* Accepted-move counters of the Metropolis test (Sec. II) and of the
+ * exchanges (Eq. 3): met[total slots] = accepted Metropolis proposals
  * per slot; swap[total slots] = accepted exchanges per ladder pair (entry
  * slot0(l) + k for pair (k, k+1) of ladder l).  Either may be NULL. */
 int xy_get_accepts(xy_ctx *ctx, uint64_t *met, uint64_t *swap);
 
-/* Raw Philox words of every site of one colour of slot `slot` for stream
+/* Philox4x32-10 (Salmon et al., SC'11; it replaces the Warp Generator of
+ * Sec. II).  Raw words of every site of one colour of slot `slot` for stream
  * `tag` and counter `count`, natural order of those sites (x fastest), two
  * words per site, drawn on the device by the same code the sweeps use. */
 int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
