@@ -215,6 +215,16 @@ int xy_set_packed(xy_ctx *ctx, const float *host_packed);
 int xy_set_packed_angles(xy_ctx *ctx, const float *host_angles);
 int xy_get_packed_angles(xy_ctx *ctx, float *host_angles);
 
+/* Page-locked host memory for the host buffers of the calls above
+ * (cudaHostAlloc, portable to every device), so that their copies run at
+ * the full host-to-device rate: on some hosts memory pinned by other means
+ * (page by page) moved at a quarter of it.  The one allocation call of the
+ * library, on the host only; the caller frees the block with xy_host_free
+ * (NULL is a no-op).  Errors: XY_ERR_ARG (NULL out, zero bytes),
+ * XY_ERR_CUDA (the allocation failed; *out = NULL, no context is affected). */
+int xy_host_alloc(size_t bytes, void **out);
+int xy_host_free(void *p);
+
 /* The parallel-tempering temperature set (Sec. II, Eq. 3).
  * Replaces the betas of ladder `lattice` (n_replicas ascending finite
  * values) in a running context: every slot takes the new beta of its beta

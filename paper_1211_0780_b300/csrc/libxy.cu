@@ -982,6 +982,27 @@ int xy_set_packed_angles(xy_ctx* c, const float* host_angles) {
   return XY_OK;
 }
 
+int xy_host_alloc(size_t bytes, void** out) {
+  if (!out || bytes == 0) return XY_ERR_ARG;
+  *out = nullptr;
+  void* p = nullptr;
+  if (cudaHostAlloc(&p, bytes, cudaHostAllocPortable) != cudaSuccess) {
+    cudaGetLastError();  // not sticky: nothing else depends on this call
+    return XY_ERR_CUDA;
+  }
+  *out = p;
+  return XY_OK;
+}
+
+int xy_host_free(void* p) {
+  if (!p) return XY_OK;
+  if (cudaFreeHost(p) != cudaSuccess) {
+    cudaGetLastError();
+    return XY_ERR_CUDA;
+  }
+  return XY_OK;
+}
+
 int xy_get_packed_angles(xy_ctx* c, float* host_angles) {
   XY_ENTER(c);
   if (!host_angles) return XY_ERR_ARG;

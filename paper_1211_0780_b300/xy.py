@@ -76,6 +76,8 @@ _SIGNATURES = {
     "xy_set_packed": (_I, [_P, _P]),
     "xy_get_packed_angles": (_I, [_P, _P]),
     "xy_set_packed_angles": (_I, [_P, _P]),
+    "xy_host_alloc": (_I, [_SZ, _P]),
+    "xy_host_free": (_I, [_P]),
     "xy_debug_draws": (_I, [_P, _I, _I, _I, _U64, _P]),
     "xy_set_tile": (_I, [_P, _I, _I, _I, _I]),
     "xy_get_tile": (_I, [_P, _I, _P, _P, _P]),
@@ -431,6 +433,34 @@ class Simulation:
 
 PEAK_KINDS = {"sfu_sincos": 0, "sfu_ex2": 1, "fp32_fma": 2, "fp64_fma": 3, "int_mul_wide": 4,
               "l2_read_bytes": 5}
+
+
+class _HostBlock:
+    """Owner of one xy_host_alloc block; frees it when collected."""
+
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def __del__(self):
+        try:
+            lib().xy_host_free(ctypes.c_void_p(self.ptr))
+        except Exception:
+            pass
+
+
+def pinned_empty(n: int, dtype=np.float32) -> np.ndarray:
+    """A numpy array of n elements in page-locked host memory from
+    xy_host_alloc (freed with the array): the host buffer for
+    set_packed_angles / get_packed_angles / set_packed / get_packed whose
+    copies run at the full host-to-device rate."""
+    _require_cuda()
+    dt = np.dtype(dtype)
+    nbytes = max(int(n), 1) * dt.itemsize
+    p = ctypes.c_void_p()
+    _check(lib().xy_host_alloc(nbytes, ctypes.byref(p)), "xy_host_alloc")
+    raw = (ctypes.c_char * nbytes).from_address(p.value)
+    raw._owner = _HostBlock(p.value)  # the array's base keeps the block alive
+    return np.frombuffer(raw, dtype=dt, count=int(n))
 
 
 def peak_probe(kind: str) -> float:

@@ -597,3 +597,23 @@ def test_zero_field_degenerate_case(tile):
     acc0 = s.accepts()[0][0]
     s.metropolis_half(1, 4)
     assert s.accepts()[0][0] - acc0 == N // 2
+
+
+def test_pinned_host_buffers_round_trip():
+    """Arrays from xy_host_alloc serve as the host buffers of the packed
+    calls and give the same bytes as ordinary host arrays."""
+    from paper_1211_0780_b300 import xy
+    a = sim(16, 2, [0.44, 0.45])
+    a.sweep(1, 2, 3)
+    want = a.get_packed_angles()
+    buf = xy.pinned_empty(a.n_packed_angles())
+    a.get_packed_angles(buf)
+    assert np.array_equal(buf, want)
+    b, c = sim(16, 2, [0.44, 0.45]), sim(16, 2, [0.44, 0.45])
+    b.set_packed_angles(buf)
+    c.set_packed_angles(np.array(want))
+    assert np.array_equal(b.get_packed(), c.get_packed())
+    vec = xy.pinned_empty(a.n_packed())
+    a.get_packed(vec)
+    assert np.array_equal(vec, a.get_packed())
+    del buf, vec  # freed through xy_host_free
