@@ -99,6 +99,11 @@ def test_null_context_and_reweight_validation(lib):
     assert lib.xy_reweight_forward(1000, p, p, p, p, p, float("nan"), 4, p, 16, p, p, p, p, 1 << 30, None) == xy.XY_ERR_ARG
     assert lib.xy_reweight_forward(1000, p, p, p, p, p, 0.45, 4, p, 16, p, p, p, p, 16, None) == xy.XY_ERR_NOMEM
     assert lib.xy_reweight_backward(0, p, 16, p, p, p, p, p, p, None) == xy.XY_ERR_ARG
+    # host buffers: argument errors come back before any CUDA call
+    out = ctypes.c_void_p(123)
+    assert lib.xy_host_alloc(0, ctypes.byref(out)) == xy.XY_ERR_ARG
+    assert lib.xy_host_alloc(16, None) == xy.XY_ERR_ARG
+    assert lib.xy_host_free(None) == xy.XY_OK
 
 
 def test_product_path_has_no_fallback(monkeypatch):
