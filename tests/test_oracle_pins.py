@@ -65,6 +65,81 @@ def test_stream_layout_pairs_sites():
                 n += 1
 
 
+# ---------------------------------------------------------------- initial state
+
+_M0, _M1 = 0xD2511F53, 0xCD9E8D57      # Philox4x32 multipliers (SC'11, Table 2)
+_W0, _W1 = 0x9E3779B9, 0xBB67AE85      # Weyl key increments (SC'11, Sec. 3.3)
+
+
+def _philox_py(ctr, key):
+    """Philox4x32-10 in plain Python integers, written from the SC'11
+    definition independently of the oracle's C: ten rounds of
+    (c0, c1, c2, c3) -> (hi(M1 c2) ^ c1 ^ k0, lo(M1 c2), hi(M0 c0) ^ c3 ^ k1,
+    lo(M0 c0)), the key advanced by the Weyl increments between rounds."""
+    c0, c1, c2, c3 = (int(v) for v in ctr)
+    k0, k1 = (int(v) for v in key)
+    m = 0xFFFFFFFF
+    for _ in range(10):
+        p0, p1 = _M0 * c0, _M1 * c2
+        c0, c1, c2, c3 = ((p1 >> 32) ^ c1 ^ k0) & m, p1 & m, ((p0 >> 32) ^ c3 ^ k1) & m, p0 & m
+        k0, k1 = (k0 + _W0) & m, (k1 + _W1) & m
+    return c0, c1, c2, c3
+
+
+def test_init_matches_the_stream_definition():
+    """The initial state (the hot start of every workload) is theta = 2 pi u
+    with u = (w >> 8) 2^-24 from the proposal word of the INIT stream at
+    count 0: word 0 of the call with ctr0 = p >> 1 for an even packed index
+    p, word 2 for an odd one; ctr3 = slot << 4 | colour << 3 | TAG_INIT.
+    Expected angles come from a plain-Python Philox (itself checked on the
+    published known answers first), not from the oracle: catches theta =
+    pi u, the acceptance word taken for the proposal, a wrong tag, colour or
+    slot in the counter, or a swapped pairing."""
+    for ctr, key, want in load_kat():
+        assert list(_philox_py(ctr, key)) == want
+    Lx, Ly, Lz = 6, 4, 4
+    for seed, slot in ((SEED, 0), (0x0123456789ABCDEF, 5)):
+        th = oracle.init_uniform((Lx, Ly, Lz), seed, slot)
+        key = (seed & 0xFFFFFFFF, seed >> 32)
+        for z in range(Lz):
+            for y in range(Ly):
+                for x in range(Lx):
+                    colour = (x + y + z) % 2
+                    p = (x >> 1) + (Lx // 2) * (y + Ly * z)
+                    w = _philox_py((p >> 1, 0, 0, (slot << 4) | (colour << 3) | oracle.TAG_INIT), key)
+                    u = (w[2 if p & 1 else 0] >> 8) / 2.0 ** 24
+                    assert th[z, y, x] == 2 * np.pi * u, (x, y, z)
+
+
+def test_init_is_uniform_and_uncorrelated():
+    """What a hot start must be, whatever the stream: i.i.d. uniform angles
+    on [0, 2 pi).  Checked per colour and slot: chi^2 over 64 bins of
+    [0, 2 pi) (catches a half or doubled range), <cos theta> = <sin theta> =
+    0 within 4 sigma = 4/sqrt(2n), the lattice energy within 4 sigma of its
+    beta = 0 law (mean 0, variance 3N/2: the 3N bond cosines of independent
+    uniform angles are uncorrelated, each of variance 1/2; catches
+    neighbouring sites drawing the same or correlated words) and distinct
+    slots uncorrelated."""
+    L = 32
+    N = L ** 3
+    ths = [oracle.init_uniform((L, L, L), SEED, slot) for slot in range(3)]
+    z, y, x = np.meshgrid(*(np.arange(L),) * 3, indexing="ij")
+    for th in ths:
+        assert th.min() >= 0.0 and th.max() < 2 * np.pi
+        for colour in (0, 1):
+            t = th[((x + y + z) % 2) == colour]
+            n = t.size
+            h, _ = np.histogram(t, bins=64, range=(0.0, 2 * np.pi))
+            chi2 = ((h - n / 64) ** 2 / (n / 64)).sum()
+            assert stats.chi2.sf(chi2, 63) > 1e-4
+            assert abs(np.cos(t).mean()) < 4 / np.sqrt(2 * n)
+            assert abs(np.sin(t).mean()) < 4 / np.sqrt(2 * n)
+        assert abs(oracle.measure(th).E) < 4 * np.sqrt(1.5 * N)
+    for a, b in ((0, 1), (1, 2)):
+        r = np.mean(np.cos(ths[a] - ths[b]))
+        assert abs(r) < 4 / np.sqrt(2 * N)
+
+
 # ---------------------------------------------------------------- measurement
 
 def test_measure_plane_wave_closed_form():
