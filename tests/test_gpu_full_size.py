@@ -4,26 +4,23 @@ a CUDA graph, the 64^3 x 32 parallel-tempering batch with its autotuned
 tile, the ragged batch in one persistent launch, and reweighting of 10^6
 samples to 4096 couplings.  The oracle runs whole half-sweeps of these
 lattices (FP64 C), or the sampled couplings for reweighting; tolerances as
-in test_gpu_parity (Metropolis: 1e-5 rad outside accept margins < 1e-6;
-over-relaxation: the conditioning bound at every site; sums: 2e-6 per bond
-term)."""
+in test_gpu_parity (the oracle runs on the exact angles of the stored
+vectors; Metropolis: 1e-5 rad outside accept margins < 1e-6; over-relaxation:
+the conditioning bound at every site and 99.9% of the sites within 1e-5 rad;
+sums: 2e-6 per bond term)."""
 
 import numpy as np
 import pytest
 
 import oracle
-from helpers import circ_dist
+from helpers import circ_dist, stored_angles64
 
 pytestmark = pytest.mark.gpu
 
 SEED = 0x5EED2012
 TOL_RAD, MARGIN = 1e-5, 1e-6
-OR_A, OR_B = 1.5e-5, 2e-6
+OR_A, OR_B = 8.4e-6, 1e-6  # the conditioning bound of test_gpu_parity
 BOND_TOL = 2e-6
-
-
-def f64(a):
-    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
 
 
 def field_norm(theta):
@@ -38,22 +35,23 @@ def colour_mask(L, colour):
     return ((x + y + z) % 2) == colour
 
 
-def check_or_half(before32, after32, colour):
-    ref = f64(before32)
+def check_or_half(before, after, colour):
+    """before, after: exact angles of the stored vectors (stored_angles64)."""
+    ref = before.copy()
     h = field_norm(ref)
     oracle.overrelax_half(ref, colour)
-    d = circ_dist(after32, ref)
-    m = colour_mask(before32.shape[0], colour)
+    d = circ_dist(after, ref)
+    m = colour_mask(before.shape[0], colour)
     assert np.all(d[m] <= OR_A / h[m] + OR_B), float(np.max(d[m] * h[m]))
-    assert np.mean(d[m] > TOL_RAD) < 5e-3
+    assert np.quantile(d[m], 0.999) < TOL_RAD
     assert np.all(d[~m] == 0)
 
 
-def check_met_half(before32, after32, beta, slot, mpass, colour):
-    ref = f64(before32)
+def check_met_half(before, after, beta, slot, mpass, colour):
+    ref = before.copy()
     _, margin = oracle.metropolis_half(ref, beta, SEED, slot, mpass, colour, want_margin=True)
     close = margin < MARGIN
-    d = circ_dist(after32, ref)
+    d = circ_dist(after, ref)
     assert np.max(d[~close]) < TOL_RAD
     return int(close.sum())
 
@@ -86,16 +84,16 @@ def test_L160_tile_graph(kind):
     assert np.array_equal(a.get_packed(), b.get_packed())
     assert a.read_series()["E"][0] == pytest.approx(b.measure()["E"][0], rel=1e-9)
 
-    th = b.get_state()[0][0].copy()
     pk = b.get_packed()
+    th = stored_angles64(b, pk)[0]
     b.overrelax_half(0)
-    check_or_half(th, b.get_state()[0][0], 0)
+    check_or_half(th, stored_angles64(b)[0], 0)
     b.set_packed(pk)
     b.metropolis_half(1, 7)
-    excluded = check_met_half(th, b.get_state()[0][0], beta, 0, 7, 1)
+    excluded = check_met_half(th, stored_angles64(b)[0], beta, 0, 7, 1)
     assert excluded <= 1e-4 * L ** 3 / 2
     b.set_packed(pk)
-    s = oracle.measure(f64(th))
+    s = oracle.measure(th)
     assert abs(b.measure()["E"][0] - s.E) < BOND_TOL * 3 * L ** 3
 
 
@@ -110,22 +108,23 @@ def test_pt_batch_64cubed_32_replicas():
     s.set_exec(xy.EXEC_GRAPH)
     s.autotune(1, 3)
     s.sweep(1, 3, 2, measure_every=1, pt_swap_every=1)
-    angles, perm, ctr = s.get_state()
+    _, perm, ctr = s.get_state()
     beta_of_slot = np.empty(R)
     beta_of_slot[perm] = betas
     pk = s.get_packed()
+    angles = stored_angles64(s, pk)
     s.overrelax_half(1)
-    after = s.get_state()[0]
+    after = stored_angles64(s)
     for slot in range(R):
         check_or_half(angles[slot], after[slot], 1)
     s.set_packed(pk)
     s.metropolis_half(0, 5)
-    after = s.get_state()[0]
+    after = stored_angles64(s)
     excluded = sum(check_met_half(angles[slot], after[slot], beta_of_slot[slot], slot, 5, 0) for slot in range(R))
     assert excluded <= 1e-4 * R * L ** 3 / 2
     # one exchange event on the measured energies
     s.set_packed(pk)
-    E = np.array([oracle.measure(f64(a)).E for a in angles])
+    E = np.array([oracle.measure(a).E for a in angles])
     gE = s.measure()["E"]
     assert np.max(np.abs(gE - E)) < BOND_TOL * 3 * L ** 3
     parity = int(ctr[2]) & 1
@@ -162,9 +161,9 @@ def test_ragged_batch_persistent_launch():
     assert np.array_equal(runs[0][0], runs[1][0])
     assert np.array_equal(runs[0][1], runs[1][1])
     s = runs[1][2]
-    angles = s.get_state()[0]
+    angles = stored_angles64(s)
     s.overrelax_half(0)
-    after = s.get_state()[0]
+    after = stored_angles64(s)
     slot0 = np.cumsum([0] + [R] * len(Ls))[:-1]
     for i in (0, 3, 6):  # L = 16, 48, 128, first replica
         check_or_half(angles[slot0[i]], after[slot0[i]], 0)

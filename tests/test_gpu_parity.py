@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 
 import oracle
-from helpers import circ_dist
+from helpers import circ_dist, stored_angles64
 
 pytestmark = pytest.mark.gpu
 
@@ -181,42 +181,46 @@ MARCH, BLOCK, STREAM, DIRECT = 0, 1, 2, 3
                                     (16, (16, 16, STREAM)), (8, (1, 8, STREAM)), (24, (5, 7, DIRECT)),
                                     (40, (3, 16, DIRECT)), (16, (16, 16, DIRECT)), (8, (1, 8, DIRECT))])
 def test_metropolis_half_parity(L, tile):
-    """One Metropolis half-sweep of each colour from the same FP32 state."""
+    """One Metropolis half-sweep of each colour from the same stored state,
+    against the oracle applied to the exact angles of the stored vectors."""
     beta = 0.4542
     s = sim(L, 1, [beta])
     if tile:
         s.set_tile(0, *tile)
-    th32 = s.get_state()[0][0].copy()  # angles of the stored vectors
     pk = s.get_packed()
+    th = stored_angles64(s, pk)[0]
     excluded = 0
     for colour, mpass in ((0, 3), (1, 3), (0, 11)):
         s.set_packed(pk)  # the same stored state for every pass
         acc0 = s.accepts()[0][0]
         s.metropolis_half(colour, mpass)
-        g = s.get_state()[0][0]
-        ref = f64(th32)
+        pk_after = s.get_packed()
+        g = stored_angles64(s, pk_after)[0]
+        ref = th.copy()
         n_acc, margin = oracle.metropolis_half(ref, beta, SEED, 0, mpass, colour, want_margin=True)
         close = margin < MARGIN
         excluded += int(close.sum())
         d = circ_dist(g, ref)
         assert np.max(d[~close]) < TOL_RAD, (colour, np.max(d[~close]))
-        assert np.all(g[~colour_mask(L, colour)] == th32[~colour_mask(L, colour)])
+        assert np.all(g[~colour_mask(L, colour)] == th[~colour_mask(L, colour)])
         gacc = int(s.accepts()[0][0] - acc0)
         assert abs(gacc - n_acc) <= int(close.sum())
-        th32 = g.copy()
-        pk = s.get_packed()
+        th = g
+        pk = pk_after
     assert excluded <= max(2, 1e-4 * 3 * L ** 3 / 2)
 
 
 # Worst-case deviation of one over-relaxation update from the oracle's FP64
-# reflection of the read-back angles: each stored neighbour vector differs
-# from the oracle's unit vector by <= 8e-7, the six-term FP32 field sum adds
-# <= 1.2e-6 per component, so |dh| <= 6e-6 and the field direction moves by
-# <= |dh| / |h|, the reflected angle by twice that; the own spin's direction
-# (<= 3e-7), the approximate reciprocal and the FP32 products of
-# S' = k h - S (<= 1e-6 together) and the read-back of the result (<= 2.4e-7)
-# add a constant.
-OR_A, OR_B = 1.5e-5, 2e-6
+# reflection (Eq. 2) of the exact angles of the stored vectors: the oracle
+# sees every neighbour at the direction the GPU stores, so only the stored
+# vectors' lengths (|S| - 1 <= 5e-7 after a fast-sincos proposal or a
+# renormalised reflection; six of them: <= 3e-6) and the FP32 rounding of
+# the six-term field sum (<= 1.2e-6 per component) move the field, |dh| <=
+# 4.2e-6; the field direction moves by <= |dh|/|h| and the reflected angle
+# by twice that.  The approximate reciprocal and the FP32 products of
+# S' = k h - S add <= 1e-6.  Measured on B300 at L = 16 .. 160: max |d||h| =
+# 1.7e-6 (bound 8.4e-6) and a 0.999-quantile of 1.5e-6 rad.
+OR_A, OR_B = 8.4e-6, 1e-6
 
 
 @pytest.mark.parametrize("L,tile", [(16, None), (24, (5, 7, MARCH)), (40, (3, 16, MARCH)),
@@ -224,29 +228,33 @@ OR_A, OR_B = 1.5e-5, 2e-6
                                     (40, (8, 40, STREAM)), (24, (5, 7, DIRECT)), (40, (8, 40, DIRECT))])
 def test_overrelax_half_parity(L, tile):
     """One over-relaxation half-sweep (Eq. 2) of each colour from the same
-    FP32 state: every site within the conditioning bound A/|h| + B (no
-    exclusions), and fewer than 0.5% of the updated sites beyond 1e-5 rad
-    (those are sites with a weak field, |h| < A/(1e-5 - B))."""
+    stored state, against the oracle applied to the exact angles of the
+    stored vectors: every site within the conditioning bound A/|h| + B (no
+    exclusions), and at least 99.9% of the updated sites within 1e-5 rad
+    (the few beyond it have a weak field, |h| below ~0.2)."""
     s = sim(L, 1, [0.4542])
     if tile:
         s.set_tile(0, *tile)
     s.sweep(1, 1, 3)
-    th32 = s.get_state()[0][0].copy()  # angles of the stored vectors
     pk = s.get_packed()
+    th = stored_angles64(s, pk)[0]
     for colour in (0, 1):
         s.set_packed(pk)
         s.overrelax_half(colour)
-        g = s.get_state()[0][0]
-        ref = f64(th32)
+        pk_after = s.get_packed()
+        g = stored_angles64(s, pk_after)[0]
+        ref = th.copy()
         h = field_norm(ref)
         oracle.overrelax_half(ref, colour)
         m = colour_mask(L, colour)
         d = circ_dist(g, ref)
+        print(f"L={L} tile={tile} colour={colour}: beyond 1e-5 rad {np.mean(d[m] > TOL_RAD):.2e}, "
+              f"0.999-quantile {np.quantile(d[m], 0.999):.2e} rad, max |d||h| {np.max(d[m] * h[m]):.2e}")
         assert np.all(d[m] <= OR_A / h[m] + OR_B), float(np.max(d[m] * h[m]))
-        assert np.mean(d[m] > TOL_RAD) < 5e-3
+        assert np.quantile(d[m], 0.999) < TOL_RAD
         assert np.all(d[~m] == 0)
-        th32 = g.copy()
-        pk = s.get_packed()
+        th = g
+        pk = pk_after
 
 
 def test_overrelax_involution_and_energy():
@@ -326,11 +334,12 @@ def test_measure_parity(L, tile):
 def check_sweep_by_half_sweeps(L, beta, nM, nOR, tile=None, seed=SEED):
     """One xy_sweep equals the same half-sweeps issued one by one (bit for
     bit), and each half-sweep agrees with the oracle's half-sweep applied to
-    the GPU's stored FP32 state before it: Metropolis sites within 1e-5 rad
-    outside accept margins < 1e-6 (counted), over-relaxation sites within the
-    conditioning bound.  (A whole sweep cannot be compared to a pure FP64
-    chain: FP32 storage alone, amplified by the reflections, moves ~2% of
-    sites by more than 1e-5 rad in one 1 + 2 sweep.)"""
+    the exact angles of the stored vectors before it: Metropolis sites within
+    1e-5 rad outside accept margins < 1e-6 (counted), over-relaxation sites
+    within the conditioning bound.  (A whole sweep cannot be held to 1e-5 rad
+    against a pure FP64 chain: FP32 storage alone, amplified by the
+    reflections, moves 1-3% of the sites beyond it in one 1 + 2 sweep; see
+    test_one_sweep_against_the_fp64_chain and the CPU test of that floor.)"""
     a = sim(L, 1, [beta], seed=seed)
     b = sim(L, 1, [beta], seed=seed)
     if tile:
@@ -340,23 +349,23 @@ def check_sweep_by_half_sweeps(L, beta, nM, nOR, tile=None, seed=SEED):
     excluded = 0
     for m in range(nM):
         for c in (0, 1):
-            before = f64(b.get_state()[0][0])
+            before = stored_angles64(b)[0]
             b.metropolis_half(c, m)
-            g = b.get_state()[0][0]
+            g = stored_angles64(b)[0]
             _, mg = oracle.metropolis_half(before, beta, seed, 0, m, c, want_margin=True)
             close = mg < MARGIN
             excluded += int(close.sum())
             assert np.max(circ_dist(g, before)[~close]) < TOL_RAD
     for _ in range(nOR):
         for c in (0, 1):
-            before = f64(b.get_state()[0][0])
+            before = stored_angles64(b)[0]
             h = field_norm(before)
             b.overrelax_half(c)
-            g = b.get_state()[0][0]
+            g = stored_angles64(b)[0]
             oracle.overrelax_half(before, c)
             d = circ_dist(g, before)
             assert np.all(d <= OR_A / h + OR_B)
-    assert np.array_equal(a.get_state()[0][0], b.get_state()[0][0])
+    assert np.array_equal(a.get_packed(), b.get_packed())
     assert excluded <= max(2, 1e-4 * L ** 3 * nM)
     return excluded
 
@@ -368,6 +377,59 @@ def test_one_sweep_from_shared_state(nM, nOR):
     check_sweep_by_half_sweeps(16, 0.4542, nM, nOR)
     check_sweep_by_half_sweeps(16, 0.4542, nM, nOR, tile=(4, 8, MARCH))
     check_sweep_by_half_sweeps(16, 0.4542, nM, nOR, tile=(4, 8, DIRECT))
+
+
+def _fp64_sweep(th, beta, seed, mpass, nM, nOR, fp32_storage):
+    """The oracle's sweep (nM Metropolis then nOR over-relaxation passes,
+    black then white) in place; with fp32_storage every half-sweep's result
+    is rounded to FP32 angles, exact FP64 arithmetic otherwise.  Returns
+    the sites whose Metropolis accept margin is below MARGIN."""
+    close = np.zeros(th.shape, dtype=bool)
+    for m in range(nM):
+        for c in (0, 1):
+            _, mg = oracle.metropolis_half(th, beta, seed, 0, mpass + m, c, want_margin=True)
+            close |= mg < MARGIN
+            if fp32_storage:
+                th[:] = th.astype(np.float32)
+    for _ in range(nOR):
+        for c in (0, 1):
+            oracle.overrelax_half(th, c)
+            if fp32_storage:
+                th[:] = th.astype(np.float32)
+    return close
+
+
+@pytest.mark.parametrize("L,tile", [(16, None), (32, (8, 8, DIRECT)), (64, (8, 8, DIRECT))])
+def test_one_sweep_against_the_fp64_chain(L, tile):
+    """A whole 1 + 2 sweep from a shared state against the pure FP64 chain
+    (the oracle on the exact angles of the stored vectors).  The 1e-5 rad
+    criterion cannot hold here for any FP32 state: the same chain with exact
+    arithmetic and only FP32 storage of the angles between half-sweeps
+    already moves 1-3% of the sites beyond 1e-5 rad (reflections amplify a
+    neighbour's rounding by ~1/|h|).  The GPU path is held to that floor:
+    its fraction beyond 1e-5 rad and its 0.999-quantile are at most 2.5 times
+    those of the FP32-storage chain from the same state, sites with a
+    Metropolis accept margin below 1e-6 excluded (counted, < 1e-4)."""
+    beta, nM, nOR = 0.4542, 1, 2
+    s = sim(L, 1, [beta])
+    if tile:
+        s.set_tile(0, *tile)
+    s.sweep(nM, nOR, 5)
+    th = stored_angles64(s)[0]
+    mpass = int(s.get_state()[2][0])
+    s.sweep(nM, nOR, 1)
+    g = stored_angles64(s)[0]
+    exact, f32 = th.copy(), th.copy()
+    close = _fp64_sweep(exact, beta, SEED, mpass, nM, nOR, False)
+    close |= _fp64_sweep(f32, beta, SEED, mpass, nM, nOR, True)
+    assert close.sum() <= max(2, 1e-4 * L ** 3)
+    d_gpu, d_f32 = circ_dist(g, exact)[~close], circ_dist(f32, exact)[~close]
+    fg, ff = np.mean(d_gpu > TOL_RAD), np.mean(d_f32 > TOL_RAD)
+    qg, qf = np.quantile(d_gpu, 0.999), np.quantile(d_f32, 0.999)
+    print(f"L={L}: beyond 1e-5 rad GPU {fg:.4f}, FP32-storage chain {ff:.4f}; "
+          f"0.999-quantile GPU {qg:.2e}, FP32-storage chain {qf:.2e}; excluded {int(close.sum())}")
+    assert ff > 1e-3  # the floor: FP32 storage alone breaks the 1e-5 criterion
+    assert fg <= 2.5 * ff and qg <= 2.5 * qf
 
 
 def test_counters_and_series_records():
