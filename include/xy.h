@@ -260,6 +260,21 @@ int xy_get_accepts(xy_ctx *ctx, uint64_t *met, uint64_t *swap);
 int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
                    uint32_t *host_words);
 
+/* The fast-math expressions of the Metropolis update (Sec. II: proposal
+ * theta' uniform in [0, 2 pi), acceptance u < exp(-beta dE)), evaluated
+ * element by element on the device by the same device functions the sweep
+ * kernels inline, for accuracy checks against FP64.  kind 0: d_in holds n
+ * uint32 proposal words w; d_out[2i], d_out[2i+1] receive the proposal
+ * vector (cos theta', sin theta') of theta' = (w >> 8) 2 pi / 2^24 (FP32
+ * product) as the update forms it with the fast sincos.  kind 1: d_in holds
+ * n FP32 exponents x = -beta dE; d_out[i] receives the threshold exp(x) 2^24
+ * (fast exponential) that the update compares the acceptance word's
+ * (w >> 8) with.  Device pointers owned by the caller, on the current
+ * device; ordered on `stream`, which the call synchronises.  XY_ERR_ARG for
+ * another kind, n < 0 or a null pointer with n > 0. */
+int xy_debug_fast_math(int kind, int64_t n, const void *d_in, float *d_out,
+                       void *stream);
+
 /* Tile of lattice `lattice`.  kind 0 (march): a thread block of (L/8) x ty
  * threads covers full rows in x and ty rows in y and marches over tz planes
  * in z, loading each other-colour spin about once.  kind 1 (block): a
@@ -343,7 +358,7 @@ const char *xy_strerror(int status);
  *   d_betap[K] f64.
  * Outputs (device, f64):
  *   d_out[6][K]  = rows {logZ, <E>, <m2>, <m4>, <csum>, <s2sum>};
- *   d_obs[2][K]  = {U_L, rho_s L};
+ *   d_obs[3][K]  = {U_L, rho_s L, q2 = <m4>/<m2>^2 (Eq. 11) = 3 (1 - U_L)};
  *   d_cov[5][K]  = {var E, cov(m2,E), cov(m4,E), cov(csum,E), cov(s2sum,E)}.
  * d_scratch: xy_reweight_scratch_bytes(T, K) bytes of caller-owned device
  * memory.  Errors: XY_ERR_ARG (T < 2, K < 1, L < 1, NULL pointers,
@@ -368,12 +383,16 @@ int xy_reweight_forward(int64_t T, const double *d_E, const float *d_m2,
  * exits.  The number of sample chunks is capped so their partial sums fit:
  * K may be at most about 95,000 target couplings; larger K returns
  * XY_ERR_NOMEM (T is unrestricted).  The call allocates nothing.  It runs on
- * the device that owns d_out (made current) and, on its first call on a
- * device, looks up the array's device address -- make that first call
- * before any stream capture.  Every call shares the array and leaves its
- * contents behind; nothing needs clearing because each call writes every
- * word it later reads, but calls that overlap on the GPU race.  Errors as
- * for xy_reweight_forward. */
+ * the device that owns d_out (device or managed memory; made current for the
+ * call, and the caller's current device restored before it returns) and, on
+ * its first call on a device, looks up the array's device address and keeps
+ * it for the life of the process -- make that first call before any stream
+ * capture, and do not call this entry point on a device after a
+ * cudaDeviceReset of it (the kept address then belongs to the torn-down
+ * context).  Every call shares the array and leaves its contents behind;
+ * nothing needs clearing because each call writes every word it later
+ * reads, but calls that overlap on the GPU race.  Errors as for
+ * xy_reweight_forward. */
 size_t xy_reweight_noalloc_capacity_bytes(void);
 
 int xy_reweight_forward_noalloc(int64_t T, const double *d_E, const float *d_m2,
@@ -408,7 +427,7 @@ int xy_multihist_solve(int64_t T, const double *d_E, int R,
 /* Averages at K target couplings from the pooled series and solved f:
  * <O>_beta' = sum_t O_t exp(-beta' E_t - log D_t) / sum_t exp(...), with the
  * columns and outputs of xy_reweight_forward (d_out[6][K]: log of the
- * denominator sum, <E>, <m2>, <m4>, <c>, <s2>; d_obs[2][K]: U_L, rho_s L;
+ * denominator sum, <E>, <m2>, <m4>, <c>, <s2>; d_obs[3][K]: U_L, rho_s L, q2;
  * d_cov[5][K]: covariances with E, so xy_reweight_backward gives the
  * beta' derivatives). */
 int xy_multihist_forward(int64_t T, const double *d_E, const float *d_m2,
@@ -467,7 +486,8 @@ int xy_fss_crossings(int B, int K, const double *d_betap, int LA,
 /* Backward: given upstream gradients g_U[K] and g_rhoL[K] (device f64) and
  * the forward's d_out, d_cov, returns grad_betap[K] = g_U dU/dbeta' +
  * g_rhoL d(rho_s L)/dbeta' (each output depends only on its own beta'_k).
- * d_dobs[2][K] (nullable) receives {dU/dbeta', d(rho_s L)/dbeta'}. */
+ * d_dobs[3][K] (nullable) receives {dU/dbeta', d(rho_s L)/dbeta',
+ * dq2/dbeta' = -3 dU/dbeta'}. */
 int xy_reweight_backward(int K, const double *d_betap, int L,
                          const double *d_out, const double *d_cov,
                          const double *d_gU, const double *d_grhoL,

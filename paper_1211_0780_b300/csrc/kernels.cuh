@@ -280,6 +280,25 @@ __global__ void k_advance(uint64_t* ctr, uint64_t d_mpass, uint64_t d_sweep, uin
   }
 }
 
+// The fast-math expressions of the Metropolis update, evaluated one by one
+// for accuracy checks with the same device functions the sweep kernels
+// call.  kind 0: in = proposal words; out[2i], out[2i+1] = the proposal
+// vector (cos, sin) of proposal_angle(w).  kind 1: in = exponents x (FP32);
+// out[i] = accept_threshold(x).
+__global__ void k_fast_math(int kind, long long n, const void* __restrict__ in, float* __restrict__ out) {
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < n;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    if (kind == 0) {
+      float c, s;
+      spin(proposal_angle(static_cast<const uint32_t*>(in)[i]), c, s);
+      out[2 * i] = c;
+      out[2 * i + 1] = s;
+    } else {
+      out[i] = accept_threshold(static_cast<const float*>(in)[i]);
+    }
+  }
+}
+
 // Raw words of every site of one colour of local slot r, natural order of
 // those sites (x fastest), two per site.
 __global__ void k_draws(Lattice lat, int r, int colour, uint32_t tag, uint64_t count,

@@ -1047,6 +1047,17 @@ int xy_debug_draws(xy_ctx* c, int slot, int colour, int tag, uint64_t count, uin
   return XY_OK;
 }
 
+int xy_debug_fast_math(int kind, int64_t n, const void* d_in, float* d_out, void* stream) {
+  if ((kind != 0 && kind != 1) || n < 0 || (n > 0 && (!d_in || !d_out))) return XY_ERR_ARG;
+  if (n == 0) return XY_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, 16384));
+  k_fast_math<<<blocks, 256, 0, st>>>(kind, static_cast<long long>(n), d_in, d_out);
+  XY_TRY(nullptr, cudaGetLastError());
+  XY_TRY(nullptr, cudaStreamSynchronize(st));
+  return XY_OK;
+}
+
 int xy_set_tile(xy_ctx* c, int lattice, int kind, int ty, int tz) {
   XY_ENTER(c);
   if (lattice < 0 || lattice >= c->n_lat) return XY_ERR_ARG;

@@ -380,7 +380,7 @@ __global__ void k_mh_mean(int64_t T, const double* __restrict__ E, double* stats
 
 // Outputs in the layout of xy_reweight_forward: out[6][K] = {log Z (up to a
 // constant common to all k: log sum_t exp(-beta' E_t - log D_t)), <E>,
-// <m2>, <m4>, <c>, <s2>}, obs[2][K] = {U_L, rho_s L}, cov[5][K] = cov with E
+// <m2>, <m4>, <c>, <s2>}, obs[3][K] = {U_L, rho_s L, q2}, cov[5][K] = cov with E
 // of {E, m2, m4, c, s2}.
 __global__ void k_mh_finish(int K, int n_tchunks, const double* __restrict__ betap, int L,
                             const double* __restrict__ kmax, const double* __restrict__ stats,
@@ -415,6 +415,7 @@ __global__ void k_mh_finish(int K, int n_tchunks, const double* __restrict__ bet
   cov[4 * K + k] = S[10] * inv - ms2 * me;
   obs[0 * K + k] = 1.0 - mm4 / (3.0 * mm2 * mm2);
   obs[1 * K + k] = L / 3.0 * (mc - bp * ms2);
+  obs[2 * K + k] = mm4 / (mm2 * mm2);  // q2 of Eq. (11)
 }
 
 bool valid_ladder(int R, const double* betas, const int64_t* counts, int64_t T) {

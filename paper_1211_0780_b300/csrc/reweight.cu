@@ -293,6 +293,7 @@ __global__ void k_rw_finish(int K, int n_tchunks, double beta0, const double* __
   cov[4 * K + k] = S[10] * inv - ms2 * me;
   obs[0 * K + k] = 1.0 - mm4 / (3.0 * mm2 * mm2);
   obs[1 * K + k] = L / 3.0 * (mc - bp * ms2);
+  obs[2 * K + k] = mm4 / (mm2 * mm2);  // q2 of Eq. (11) = 3 (1 - U_L)
 }
 
 // Backward: d<O>/dbeta' = -cov(O, E), chain rule to U_L and rho_s L.
@@ -309,6 +310,7 @@ __global__ void k_rw_backward(int K, const double* __restrict__ betap, int L, co
   if (dobs) {
     dobs[k] = dU;
     dobs[K + k] = dR;
+    dobs[2 * K + k] = -3.0 * dU;  // d q2 / d beta', q2 = 3 (1 - U_L)
   }
   if (grad) grad[k] = (gU ? gU[k] * dU : 0.0) + (gR ? gR[k] * dR : 0.0);
 }
@@ -407,6 +409,35 @@ int static_scratch_address(int device, void** out) {
   return XY_OK;
 }
 
+// Layout inside the array: stat partials, stats, then n_tchunks x K x kNSum
+// chunk sums.
+constexpr size_t kStaticOffStats = (static_cast<size_t>(kStatBlocks) * 3 * 8 + 255) / 256 * 256;
+constexpr size_t kStaticOffSums = kStaticOffStats + 256;
+
+// The forward pass on `device` (current) out of the static array.
+int forward_on_static_scratch(int64_t T, const double* d_E, const float* d_m2, const float* d_m4, const float* d_c,
+                              const float* d_s2, double beta0, int K, const double* d_betap, int L, double* d_out,
+                              double* d_obs, double* d_cov, const Plan& p, int device, cudaStream_t st) {
+  void* base = nullptr;
+  const int rc = static_scratch_address(device, &base);
+  if (rc != XY_OK) return rc;
+  char* ws = static_cast<char*>(base);
+  double* part = reinterpret_cast<double*>(ws);
+  double* stats = reinterpret_cast<double*>(ws + kStaticOffStats);
+  double* sums = reinterpret_cast<double*>(ws + kStaticOffSums);
+  k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
+  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, K, d_betap, stats);
+  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, 0, 1, d_E, d_m2, d_m4, d_c, d_s2,
+                                                                  beta0, K, d_betap, stats, sums);
+  k_rw_finish<<<(K + 127) / 128, 128, 0, st>>>(K, p.n_tchunks, beta0, d_betap, L, stats, sums, d_out, d_obs, d_cov);
+  const cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    snprintf(g_rw_err, sizeof g_rw_err, "%s", cudaGetErrorString(e));
+    return XY_ERR_CUDA;
+  }
+  return XY_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -419,47 +450,33 @@ int xy_reweight_forward_noalloc(int64_t T, const double* d_E, const float* d_m2,
                                 void* stream) {
   if (T < 2 || K < 1 || L < 1 || !std::isfinite(beta0)) return XY_ERR_ARG;
   if (!d_E || !d_m2 || !d_m4 || !d_c || !d_s2 || !d_betap || !d_out || !d_obs || !d_cov) return XY_ERR_ARG;
-  // Layout inside the array: stat partials, stats, then n_tchunks x K x kNSum sums.
-  const size_t off_stat_part = 0;
-  const size_t off_stats = (static_cast<size_t>(kStatBlocks) * 3 * 8 + 255) / 256 * 256;
-  const size_t off_sums = off_stats + 256;
   const size_t per_chunk = static_cast<size_t>(K) * kNSum * 8;
-  if (off_sums + per_chunk > kStaticScratchBytes) return XY_ERR_NOMEM;  // K too large
+  if (kStaticOffSums + per_chunk > kStaticScratchBytes) return XY_ERR_NOMEM;  // K too large
   Plan p = plan_for(T, K);
-  const int cap = static_cast<int>((kStaticScratchBytes - off_sums) / per_chunk);
+  const int cap = static_cast<int>((kStaticScratchBytes - kStaticOffSums) / per_chunk);
   if (p.n_tchunks > cap) {
     p.n_tchunks = cap;
     p.t_per_chunk = (T + cap - 1) / cap;
   }
-  // The device of the outputs is the device to run on; the first call on a
-  // device looks the array's address up (do it before any stream capture).
+  // The device of the outputs (device or managed memory) is the device to
+  // run on; the first call on a device looks the array's address up (do it
+  // before any stream capture).  The caller's current device is restored
+  // before returning.
   cudaPointerAttributes pa{};
-  cudaError_t e = cudaPointerGetAttributes(&pa, d_out);
-  if (e != cudaSuccess || pa.type != cudaMemoryTypeDevice) {
+  const cudaError_t e = cudaPointerGetAttributes(&pa, d_out);
+  if (e != cudaSuccess || (pa.type != cudaMemoryTypeDevice && pa.type != cudaMemoryTypeManaged) || pa.device < 0) {
     cudaGetLastError();
     return XY_ERR_ARG;
   }
-  e = cudaSetDevice(pa.device);
-  if (e != cudaSuccess) return XY_ERR_CUDA;
-  void* base = nullptr;
-  const int rc = static_scratch_address(pa.device, &base);
-  if (rc != XY_OK) return rc;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  char* ws = static_cast<char*>(base);
-  double* part = reinterpret_cast<double*>(ws + off_stat_part);
-  double* stats = reinterpret_cast<double*>(ws + off_stats);
-  double* sums = reinterpret_cast<double*>(ws + off_sums);
-  k_rw_stats<<<kStatBlocks, kBlock, 0, st>>>(T, d_E, part);
-  k_rw_stats_finish<<<1, 32, 0, st>>>(T, kStatBlocks, part, K, d_betap, stats);
-  k_rw_sums<<<dim3(p.n_kblocks, p.n_tchunks), kBlock, 0, st>>>(T, p.t_per_chunk, 0, 1, d_E, d_m2, d_m4, d_c, d_s2,
-                                                                  beta0, K, d_betap, stats, sums);
-  k_rw_finish<<<(K + 127) / 128, 128, 0, st>>>(K, p.n_tchunks, beta0, d_betap, L, stats, sums, d_out, d_obs, d_cov);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) {
-    snprintf(g_rw_err, sizeof g_rw_err, "%s", cudaGetErrorString(e));
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess || (prev != pa.device && cudaSetDevice(pa.device) != cudaSuccess)) {
+    snprintf(g_rw_err, sizeof g_rw_err, "%s", cudaGetErrorString(cudaGetLastError()));
     return XY_ERR_CUDA;
   }
-  return XY_OK;
+  const int rc = forward_on_static_scratch(T, d_E, d_m2, d_m4, d_c, d_s2, beta0, K, d_betap, L, d_out, d_obs, d_cov,
+                                           p, pa.device, static_cast<cudaStream_t>(stream));
+  if (prev != pa.device) cudaSetDevice(prev);
+  return rc;
 }
 
 }  // extern "C"

@@ -181,6 +181,17 @@ __device__ __forceinline__ void spin(float th, float& c, float& s) {
   s = -sn;
 }
 
+// The Metropolis proposal angle theta' = 2 pi u0 of a proposal word: the
+// 24-bit integer (w >> 8) times 2 pi / 2^24 in FP32.
+__device__ __forceinline__ float proposal_angle(uint32_t w) {
+  return static_cast<float>(w >> 8) * kTwoPiOver2p24;
+}
+
+// The acceptance threshold of u1 < exp(x) in units of the accept word:
+// u1 < exp(x)  <=>  (w >> 8) < exp(x) 2^24 (the scaling by 2^24 is exact),
+// with the fast exponential.
+__device__ __forceinline__ float accept_threshold(float x) { return __expf(x) * 16777216.0f; }
+
 struct Spins4 {
   float4 c, s;
 };
@@ -365,17 +376,15 @@ __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int
     if (MODE == kMetropolis) {
       const uint4& w = q ? w1 : w0;
       // proposal theta' = 2 pi u0 (words 0 and 2), acceptance u1 (words 1 and 3)
-      const float2 tp = make_float2(static_cast<float>(w.x >> 8) * kTwoPiOver2p24,
-                                    static_cast<float>(w.z >> 8) * kTwoPiOver2p24);
+      const float2 tp = make_float2(proposal_angle(w.x), proposal_angle(w.z));
       float2 cp, sp;
       spin(tp.x, cp.x, sp.x);
       spin(tp.y, cp.y, sp.y);
       // -beta dE with dE = -[h_x (cos t' - cos t) + h_y (sin t' - sin t)]
       const float2 x = __fmul2_rn(make_float2(beta, beta),
                                   __ffma2_rn(hx[q], __fadd2_rn(cp, neg2(co)), __fmul2_rn(hy[q], __fadd2_rn(sp, neg2(so)))));
-      // u1 < exp(x)  <=>  (w >> 8) < exp(x) 2^24 (exact scaling)
-      const bool a0 = static_cast<float>(w.y >> 8) < __expf(x.x) * 16777216.0f;
-      const bool a1 = static_cast<float>(w.w >> 8) < __expf(x.y) * 16777216.0f;
+      const bool a0 = static_cast<float>(w.y >> 8) < accept_threshold(x.x);
+      const bool a1 = static_cast<float>(w.w >> 8) < accept_threshold(x.y);
       n_acc += (a0 ? 1u : 0u) + (a1 ? 1u : 0u);
       nc[q] = make_float2(a0 ? cp.x : co.x, a1 ? cp.y : co.y);
       ns[q] = make_float2(a0 ? sp.x : so.x, a1 ? sp.y : so.y);

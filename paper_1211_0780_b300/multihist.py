@@ -79,7 +79,7 @@ def forward(pooled, betas, counts, f, betap, L: int, scratch=None):
     if scratch is None or scratch.numel() < need:
         scratch = torch.empty(int(need), dtype=torch.uint8, device="cuda")
     out = torch.empty((6, K), dtype=torch.float64, device="cuda")
-    obs = torch.empty((2, K), dtype=torch.float64, device="cuda")
+    obs = torch.empty((3, K), dtype=torch.float64, device="cuda")
     cov = torch.empty((5, K), dtype=torch.float64, device="cuda")
     xy._check(xy.lib().xy_multihist_forward(T, E.data_ptr(), m2.data_ptr(), m4.data_ptr(), c.data_ptr(),
                                             s2.data_ptr(), R, xy._ptr(b), xy._ptr(n), xy._ptr(fv), K, bp.data_ptr(),
@@ -87,7 +87,7 @@ def forward(pooled, betas, counts, f, betap, L: int, scratch=None):
                                             scratch.data_ptr(), int(scratch.numel()),
                                             torch.cuda.current_stream().cuda_stream), "xy_multihist_forward")
     res = {name: out[i] for i, name in enumerate(xy.OUT_ROWS)}
-    res["U"], res["rhoL"] = obs[0], obs[1]
+    res["U"], res["rhoL"], res["q2"] = obs[0], obs[1], obs[2]
     for i, name in enumerate(xy.COV_ROWS):
         res["cov_" + name] = cov[i]
     res["_out"], res["_obs"], res["_cov"] = out, obs, cov

@@ -79,6 +79,7 @@ _SIGNATURES = {
     "xy_host_alloc": (_I, [_SZ, _P]),
     "xy_host_free": (_I, [_P]),
     "xy_debug_draws": (_I, [_P, _I, _I, _I, _U64, _P]),
+    "xy_debug_fast_math": (_I, [_I, _I64, _P, _P, _P]),
     "xy_set_tile": (_I, [_P, _I, _I, _I, _I]),
     "xy_get_tile": (_I, [_P, _I, _P, _P, _P]),
     "xy_autotune": (_I, [_P, _I, _I]),
@@ -473,6 +474,23 @@ def peak_probe(kind: str) -> float:
     return float(out.value)
 
 
+def fast_math(kind: str, values) -> np.ndarray:
+    """The Metropolis update's fast-math expressions on the device (see
+    xy_debug_fast_math).  kind "proposal": uint32 proposal words -> (n, 2)
+    FP32 proposal vectors (cos, sin); kind "accept": FP32 exponents x ->
+    the FP32 thresholds exp(x) 2^24."""
+    torch = _require_cuda()
+    k = {"proposal": 0, "accept": 1}[kind]
+    src = torch.as_tensor(np.ascontiguousarray(values, dtype=np.uint32 if k == 0 else np.float32).view(
+        np.int32 if k == 0 else np.float32), device="cuda")
+    n = src.numel()
+    out = torch.empty(2 * n if k == 0 else n, dtype=torch.float32, device="cuda")
+    _check(lib().xy_debug_fast_math(k, n, src.data_ptr(), out.data_ptr(),
+                                    torch.cuda.current_stream().cuda_stream), "xy_debug_fast_math")
+    res = out.cpu().numpy()
+    return res.reshape(n, 2) if k == 0 else res
+
+
 # ---------------------------------------------------------------------------
 # Single-histogram reweighting (FP64), forward and backward kernels
 # ---------------------------------------------------------------------------
@@ -510,7 +528,7 @@ def reweight_forward(series, beta0: float, betap, L: int, scratch=None):
     if scratch is None or scratch.numel() < need:
         scratch = torch.empty(int(need), dtype=torch.uint8, device="cuda")
     out = torch.empty((6, K), dtype=torch.float64, device="cuda")
-    obs = torch.empty((2, K), dtype=torch.float64, device="cuda")
+    obs = torch.empty((3, K), dtype=torch.float64, device="cuda")
     cov = torch.empty((5, K), dtype=torch.float64, device="cuda")
     st = torch.cuda.current_stream().cuda_stream
     _check(lib().xy_reweight_forward(T, E.data_ptr(), m2.data_ptr(), m4.data_ptr(), c.data_ptr(),
@@ -520,8 +538,7 @@ def reweight_forward(series, beta0: float, betap, L: int, scratch=None):
     res = {name: out[i] for i, name in enumerate(OUT_ROWS)}
     res["U"] = obs[0]
     res["rhoL"] = obs[1]
-    # q2 = <m^4>/<m^2>^2 = 3(1 - U_L) (Eq. 11), the ratio of the paper's collapse
-    res["q2"] = 3.0 * (1.0 - obs[0])
+    res["q2"] = obs[2]  # <m^4>/<m^2>^2 (Eq. 11), the ratio of the paper's collapse
     for i, name in enumerate(COV_ROWS):
         res["cov_" + name] = cov[i]
     res["_out"], res["_obs"], res["_cov"] = out, obs, cov
@@ -529,12 +546,12 @@ def reweight_forward(series, beta0: float, betap, L: int, scratch=None):
 
 
 def reweight_backward(betap, L: int, fwd, gU=None, grhoL=None):
-    """Runs the backward kernel: returns (grad_betap or None, dobs[2][K])
-    with dobs = {dU/dbeta', d(rho_s L)/dbeta'}."""
+    """Runs the backward kernel: returns (grad_betap or None, dobs[3][K])
+    with dobs = {dU/dbeta', d(rho_s L)/dbeta', dq2/dbeta'}."""
     import torch
     bp = torch.as_tensor(betap, dtype=torch.float64, device="cuda").contiguous()
     K = bp.numel()
-    dobs = torch.empty((2, K), dtype=torch.float64, device="cuda")
+    dobs = torch.empty((3, K), dtype=torch.float64, device="cuda")
     grad = torch.empty(K, dtype=torch.float64, device="cuda") if (gU is not None or grhoL is not None) else None
     # Keep the contiguous copies alive until the kernel has been enqueued on
     # this stream (the caching allocator then orders any reuse after it).

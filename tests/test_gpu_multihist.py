@@ -32,7 +32,7 @@ def _oracle_outputs(pooled, betas, counts, f, bp, L):
                   pooled["c"].astype(np.float64).sum(axis=0), pooled["s2"].astype(np.float64).sum(axis=0)], axis=1)
     mE, mO, cov = omh.averages(pooled["E"], O, betas, counts, f, bp)
     m2, m4, c, s2 = mO.T
-    return {"E": mE, "m2": m2, "m4": m4, "csum": c, "s2sum": s2, "U": 1 - m4 / (3 * m2 * m2),
+    return {"E": mE, "m2": m2, "m4": m4, "csum": c, "s2sum": s2, "U": 1 - m4 / (3 * m2 * m2), "q2": m4 / (m2 * m2),
             "rhoL": L / 3 * (c - np.asarray(bp) * s2), "cov_m2": cov[:, 0], "cov_m4": cov[:, 1]}
 
 
@@ -49,7 +49,7 @@ def test_solve_and_forward_match_oracle(R, n):
     bp = np.linspace(0.438, 0.472, 41)
     g = mh.forward(pooled, betas, counts, f, bp, L)
     ref = _oracle_outputs(pooled, betas, counts, fo, bp, L)
-    for key in ("E", "m2", "m4", "U", "rhoL"):
+    for key in ("E", "m2", "m4", "U", "rhoL", "q2"):
         np.testing.assert_allclose(g[key].cpu().numpy(), ref[key], rtol=1e-9, err_msg=key)
     np.testing.assert_allclose(g["cov_m2"].cpu().numpy(), ref["cov_m2"], rtol=1e-7,
                                atol=1e-9 * np.max(np.abs(ref["cov_m2"])))
@@ -64,7 +64,7 @@ def test_one_coupling_equals_single_histogram_kernels():
     bp = np.linspace(0.4500, 0.4590, 37)
     g = mh.forward(pooled, [0.4542], counts, f, bp, L)
     r = xy.reweight_forward(pooled, 0.4542, bp, L)
-    for key in ("E", "m2", "m4", "csum", "s2sum", "U", "rhoL"):
+    for key in ("E", "m2", "m4", "csum", "s2sum", "U", "rhoL", "q2"):
         np.testing.assert_allclose(g[key].cpu().numpy(), r[key].cpu().numpy(), rtol=1e-10, err_msg=key)
 
 

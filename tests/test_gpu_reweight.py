@@ -35,6 +35,9 @@ def test_forward_backward_match_oracle(L, T, K):
     for row, key in ((0, "dU"), (1, "drhoL")):
         np.testing.assert_allclose(dobs[row].cpu().numpy(), ref[key], rtol=1e-8,
                                    atol=1e-8 * np.max(np.abs(ref[key])))
+    # dq2/dbeta' = -3 dU/dbeta' (Eq. 11: q2 = 3 (1 - U_L))
+    np.testing.assert_allclose(dobs[2].cpu().numpy(), -3.0 * ref["dU"], rtol=1e-8,
+                               atol=3e-8 * np.max(np.abs(ref["dU"])))
 
 
 def test_non_uniform_grid_and_sign_change():

@@ -15,7 +15,7 @@ def _call_noalloc(lib, s_t, beta0, bp, L, torch):
     E, m2, m4, c, s2 = s_t
     K = bp.numel()
     out = torch.full((6, K), float("nan"), dtype=torch.float64, device="cuda")
-    obs = torch.full((2, K), float("nan"), dtype=torch.float64, device="cuda")
+    obs = torch.full((3, K), float("nan"), dtype=torch.float64, device="cuda")
     cov = torch.full((5, K), float("nan"), dtype=torch.float64, device="cuda")
     rc = lib.xy_reweight_forward_noalloc(E.numel(), E.data_ptr(), m2.data_ptr(), m4.data_ptr(), c.data_ptr(),
                                          s2.data_ptr(), float(beta0), K, bp.data_ptr(), int(L), out.data_ptr(),
