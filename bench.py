@@ -185,9 +185,28 @@ def barrier(world: int):
 
 # ---------------------------------------------------------------- CPU oracle
 
-def oracle_rate(seconds: float, threads: int | None = None):
-    """FP64 oracle on the host cores: 160^3 sweeps (1 + 5 passes) until about
-    `seconds` have passed.  Returns (updates/ns, threads, sweeps)."""
+def workload_config(world: int) -> dict:
+    """The headline workload as both arms run it (the `config` of the line)."""
+    return {"workload": WORKLOAD, "L": L_MAIN, "replicas": 1, "beta": BETA_MAIN,
+            "sweeps_per_step": SWEEPS_PER_STEP, "measure_every": SWEEPS_PER_STEP,
+            "updates_per_step": UPDATES_PER_STEP,
+            "l2": "GPU arm: flushed (256 MB write) before every timed step",
+            "parallelism": f"replicas only x{world}"}
+
+
+def oracle_step(th, mpass: int) -> int:
+    """One step of the headline workload on the FP64 oracle: SWEEPS_PER_STEP
+    sweeps of 1 + 5 passes with the lattice sums after the last one.
+    Returns the next Metropolis-pass counter."""
+    import oracle
+    oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, SWEEPS_PER_STEP, SWEEPS_PER_STEP)
+    return mpass + SWEEPS_PER_STEP * NM_MAIN
+
+
+def oracle_rate(seconds: float, threads: int | None = None, sweeps: int = SWEEPS_PER_STEP):
+    """FP64 oracle on the host cores: steps of the headline workload (or,
+    with sweeps=1, single unmeasured sweeps) until about `seconds` have
+    passed.  Returns (updates/ns, threads, sweeps done)."""
     import oracle
     n = threads or os.cpu_count() or 1
     oracle.set_threads(n)
@@ -196,10 +215,13 @@ def oracle_rate(seconds: float, threads: int | None = None):
     mpass = 0
     while elapsed < seconds or done == 0:
         t0 = time.perf_counter()
-        oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, 1, 0)
+        if sweeps == SWEEPS_PER_STEP:
+            mpass = oracle_step(th, mpass)
+        else:
+            oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, sweeps, 0)
+            mpass += sweeps * NM_MAIN
         elapsed += time.perf_counter() - t0
-        done += 1
-        mpass += NM_MAIN
+        done += sweeps
     upd = done * (NM_MAIN + NOR_MAIN) * L_MAIN ** 3
     return upd / (elapsed * 1e9), n, done
 
@@ -226,24 +248,23 @@ def run_reference(args):
     th = oracle.init_uniform((L_MAIN,) * 3, SEED, 0)
     mpass = 0
     for _ in range(args.warmup):
-        oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, 1, 0)
-        mpass += NM_MAIN
+        mpass = oracle_step(th, mpass)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        oracle.run_chain(th, BETA_MAIN, SEED, 0, mpass, NM_MAIN, NOR_MAIN, 1, 1)
+        mpass = oracle_step(th, mpass)
         times.append(time.perf_counter() - t0)
-        mpass += NM_MAIN
-    upd = (NM_MAIN + NOR_MAIN) * L_MAIN ** 3
     total = sum(times)
-    value = args.steps * upd / (total * 1e9)
-    sample = f"{args.steps} sweeps (1 Metropolis + 5 over-relaxation passes) of the 160^3 lattice, one per step"
+    value = args.steps * UPDATES_PER_STEP / (total * 1e9)
+    sample = (f"{args.steps} steps of {SWEEPS_PER_STEP} sweeps (1 Metropolis + 5 over-relaxation passes) of the "
+              f"160^3 lattice with the lattice sums after each step's last sweep: the workload's own steps")
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
         "device": f"host CPU ({cpu_model()}), {n} threads (the FP64 oracle; rank 0 only)",
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": {"workload": WORKLOAD + " (reference step = 1 sweep)"},
+        "data": "synthetic", "config": workload_config(world),
+        "exec": "FP64 oracle in C, OpenMP over the sites of each half-sweep",
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": n, "kind": "oracle", "sample": sample,
                          "cpu_model": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -610,6 +631,15 @@ def run_gpu(args):
                 "note": ("12 B/update algorithmic; lattice state (cos, sin) is L2-resident (32.8 MB < 126 MB); "
                          "duration = CUDA-event average over 5 back-to-back replays of a graph of 160 "
                          "chained over-relaxation half-sweeps (+1 counter kernel)")}
+    # the same 12 B/update basis over the Metropolis half-sweep and over the
+    # whole timed step (every kernel of the 10 sweeps, the fused sums and the
+    # finishing step, and the gaps between them)
+    ach_met = BYTES_PER_UPDATE * half / (ms_met * 1e-3) / 1e9
+    ach_step = BYTES_PER_UPDATE * UPDATES_PER_STEP / (ms_total / args.steps * 1e-3) / 1e9
+    roofline["metropolis"] = {"achieved": ach_met, "frac": ach_met / hbm, "unit": "GB/s",
+                              "kernel": "Metropolis half-sweep, same tile and timing as above"}
+    roofline["step"] = {"achieved": ach_step, "frac": ach_step / hbm, "unit": "GB/s",
+                        "note": "12 B x updates per step / ms_per_step: the whole 1 + 5 step"}
     kernels = {"overrelax_half_ms": ms_or, "metropolis_half_ms": ms_met,
                "overrelax_updates_per_ns": half / (ms_or * 1e6), "metropolis_updates_per_ns": half / (ms_met * 1e6)}
 
@@ -714,12 +744,13 @@ def run_gpu(args):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         v, n, done = oracle_rate(args.cpu_seconds)
-        v1, _, done1 = oracle_rate(min(4.0, args.cpu_seconds), threads=1)
+        v1, _, done1 = oracle_rate(min(4.0, args.cpu_seconds), threads=1, sweeps=1)
         cpu = {"value": v, "unit": UNIT, "cores": n, "kind": "oracle",
-               "sample": f"{done} sweeps (1+5 passes) of the 160^3 lattice, FP64, OpenMP over sites",
+               "sample": f"{done // SWEEPS_PER_STEP} steps ({done} sweeps of 1+5 passes, lattice sums every "
+                         f"{SWEEPS_PER_STEP}) of the 160^3 lattice, FP64, OpenMP over sites",
                "cpu_model": cpu_model(),
                "single_thread": {"value": v1, "unit": UNIT,
-                                 "sample": f"{done1} sweep{'s' if done1 > 1 else ''} on one thread"}}
+                                 "sample": f"{done1} unmeasured sweep{'s' if done1 > 1 else ''} on one thread"}}
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -730,11 +761,8 @@ def run_gpu(args):
                      "note": "value is the first run; four more runs of the same K steps follow it"},
             "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "L": L_MAIN, "replicas": 1, "beta": BETA_MAIN,
-                       "sweeps_per_step": SWEEPS_PER_STEP, "updates_per_step": UPDATES_PER_STEP,
-                       "tile": list(tile), "exec": "cuda graph of half-sweep kernels",
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas only x{world}"},
+            "config": workload_config(world),
+            "tile": list(tile), "exec": "cuda graph of half-sweep kernels",
             "roofline": roofline, "kernels": kernels, "cpu_baseline": cpu, "clocks": clk, "e2e": e2e,
             "gpu_launches": args.steps * launches_per_step,
         }
@@ -749,8 +777,8 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
-    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")

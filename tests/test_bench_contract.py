@@ -27,4 +27,7 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
-    assert d["dtype"] == "f64" and d["data"] == "synthetic" and "workload" in d["config"]
+    assert d["dtype"] == "f64" and d["data"] == "synthetic"
+    # the GPU arm's workload and schedule: 10 sweeps per step, sums every 10
+    assert d["config"] == bench.workload_config(1)
+    assert d["config"]["measure_every"] == d["config"]["sweeps_per_step"] == bench.SWEEPS_PER_STEP
