@@ -48,12 +48,11 @@ int part_cap_for(int L) { return std::max(1, (L * L) / 4); }
 
 struct Layout {
   size_t spins, ladder_beta, perm, beta_slot, beta_slot64, bidx_slot, E_slot, sums_slot, partials,
-      acc_met, acc_swap, ctr, status, barrier, nswapped, fin_done, lats, staging, plan_items, plan_offs,
-      series, total;
+      acc_met, acc_swap, ctr, status, barrier, nswapped, fin_done, lats, staging, plan_items, series, total;
 };
 
 constexpr int kMaxPlanBlocks = 8192;
-constexpr size_t kBarBytes = (kBarGroups + 1) * kBarStride * 8;
+constexpr size_t kBarBytes = static_cast<size_t>(kBarWords) * 8;
 
 bool valid_lattices(int n, const int* L, const int* R) {
   if (n <= 0 || n > 4096 || !L || !R) return false;
@@ -93,13 +92,12 @@ Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
   o.acc_swap = take(slots * 8);
   o.ctr = take(kNumCounters * 8);
   o.status = take(64);
-  o.barrier = take((kBarGroups + 1) * kBarStride * 8);
+  o.barrier = take(kBarBytes);
   o.nswapped = take(64);
   o.fin_done = take(static_cast<size_t>(n) * 4);
   o.lats = take(static_cast<size_t>(n) * sizeof(Lattice));
   o.staging = take(static_cast<size_t>(maxN) * 4);
   o.plan_items = take(static_cast<size_t>(parts) * sizeof(int4));
-  o.plan_offs = take(static_cast<size_t>(kMaxPlanBlocks + 1) * 4);
   o.series = take(static_cast<size_t>(std::max<int64_t>(series_cap, 0)) * slots * sizeof(xy_record));
   o.total = off;
   return o;
@@ -133,7 +131,7 @@ struct xy_ctx {
   int sticky = XY_OK;
   std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
   struct Plan {
-    int G = 0, B = 0, smem = 0, kind = 0;
+    int G = 0, B = 0, smem = 0, kind = 0, n_items = 0;
     bool graph_ok = true;
   } plan;
   bool plan_valid = false;
@@ -1098,9 +1096,20 @@ int xy_device_status(xy_ctx* c, int* status_out) {
 
 namespace {
 
-// Longest-processing-time-first assignment of the tile work items of one
-// half-sweep to G blocks.  Cost of a tile ~ (rows + 2)(planes + 2) x row
-// length: the sincos evaluations, which dominate, including the halos.
+// The persistent kernel of one tile kind and sweep part.
+const void* persistent_kernel(int kind, int part) {
+#define XY_PK(K) \
+  (part == kPartMetropolis   ? reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis>) \
+   : part == kPartOverrelax ? reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax>) \
+                            : reinterpret_cast<const void*>(k_persistent<K, kPartFinish>))
+  return kind == kTileBlock ? XY_PK(kTileBlock) : kind == kTileDirect ? XY_PK(kTileDirect) : XY_PK(kTileMarch);
+#undef XY_PK
+}
+
+// The tile work items of one half-sweep in decreasing order of cost (the
+// blocks take them in this order: longest-processing-time-first) and the
+// grid of the persistent launches.  Cost of a tile ~ (rows + 2)(planes + 2)
+// x row length: the update work including the halos.
 int build_plan(xy_ctx* c) {
   if (c->plan_valid) return XY_OK;
   int B = 64, smem = 0;
@@ -1114,15 +1123,19 @@ int build_plan(xy_ctx* c) {
     smem = std::max(smem, h.smem());
   }
   B = (B + 31) / 32 * 32;
-  const void* fn = kind == kTileBlock    ? reinterpret_cast<const void*>(k_persistent<kTileBlock>)
-                   : kind == kTileDirect ? reinterpret_cast<const void*>(k_persistent<kTileDirect>)
-                                         : reinterpret_cast<const void*>(k_persistent<kTileMarch>);
-  cudaFuncAttributes fa{};
-  XY_TRY(c, cudaFuncGetAttributes(&fa, fn));
-  if (B > fa.maxThreadsPerBlock) return XY_ERR_ARG;  // a tile wider than one persistent block
-  XY_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  int nb = 0;
-  XY_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, B, smem));
+  // Every part's kernel runs on the same grid and item plan: the grid is
+  // sized by the part that keeps the fewest blocks per SM.
+  int nb = 1 << 30;
+  for (int part = kPartMetropolis; part <= kPartFinish; ++part) {
+    const void* fn = persistent_kernel(kind, part);
+    cudaFuncAttributes fa{};
+    XY_TRY(c, cudaFuncGetAttributes(&fa, fn));
+    if (B > fa.maxThreadsPerBlock) return XY_ERR_ARG;  // a tile wider than one persistent block
+    XY_TRY(c, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    int n = 0;
+    XY_TRY(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, fn, B, smem));
+    nb = std::min(nb, n);
+  }
   if (nb <= 0) return XY_ERR_ARG;
   struct Item {
     int4 w;
@@ -1141,24 +1154,12 @@ int build_plan(xy_ctx* c) {
   const int G = static_cast<int>(std::min<long long>(
       std::min<long long>(static_cast<long long>(nb) * c->num_sms, kMaxPlanBlocks), std::max<size_t>(items.size(), 1)));
   std::stable_sort(items.begin(), items.end(), [](const Item& a, const Item& b) { return a.cost > b.cost; });
-  std::vector<double> load(G, 0.0);
-  std::vector<std::vector<int4>> per(G);
-  for (const Item& it : items) {
-    const int b = static_cast<int>(std::min_element(load.begin(), load.end()) - load.begin());
-    load[b] += it.cost;
-    per[b].push_back(it.w);
-  }
-  std::vector<int4> flat;
-  std::vector<int> offs(G + 1, 0);
-  for (int b = 0; b < G; ++b) {
-    offs[b] = static_cast<int>(flat.size());
-    flat.insert(flat.end(), per[b].begin(), per[b].end());
-  }
-  offs[G] = static_cast<int>(flat.size());
+  std::vector<int4> flat(items.size());
+  for (size_t i = 0; i < items.size(); ++i) flat[i] = items[i].w;
   XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.plan_items, flat.data(), flat.size() * sizeof(int4), cudaMemcpyHostToDevice, c->stream));
-  XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.plan_offs, offs.data(), offs.size() * 4, cudaMemcpyHostToDevice, c->stream));
   XY_TRY(c, cudaStreamSynchronize(c->stream));
   c->plan.G = G;
+  c->plan.n_items = static_cast<int>(items.size());
   c->plan.B = B;
   c->plan.smem = smem;
   c->plan.kind = kind;
@@ -1166,19 +1167,18 @@ int build_plan(xy_ctx* c) {
   return XY_OK;
 }
 
-PersistentArgs persistent_args(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
+PersistentArgs persistent_args(xy_ctx* c) {
   PersistentArgs a{};
   a.pp = c->pass_params(true, 0, 0);
   a.fp = finish_params(c);
   a.lats = c->at<Lattice>(c->lay.lats);
   a.items = c->at<int4>(c->lay.plan_items);
-  a.offs = c->at<int>(c->lay.plan_offs);
+  a.n_items = c->plan.n_items;
   a.n_lat = c->n_lat;
-  a.nM = nM;
-  a.nOR = nOR;
-  a.n_sweeps = ns;
-  a.me = me;
-  a.se = se;
+  a.n_pass = 0;
+  a.mpass_off = 0;
+  a.bar0 = 0;
+  a.work0 = 0;
   a.bar = c->at<unsigned long long>(c->lay.barrier);
   a.status = c->at<int>(c->lay.status);
   a.budget_ns = 2000000000ll;
@@ -1186,7 +1186,7 @@ PersistentArgs persistent_args(xy_ctx* c, int nM, int nOR, int ns, int me, int s
   return a;
 }
 
-cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a) {
+cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, int part) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(c->plan.G);
   cfg.blockDim = dim3(c->plan.B);
@@ -1197,19 +1197,45 @@ cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& 
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  return c->plan.kind == kTileBlock    ? cudaLaunchKernelEx(&cfg, k_persistent<kTileBlock>, a)
-         : c->plan.kind == kTileDirect ? cudaLaunchKernelEx(&cfg, k_persistent<kTileDirect>, a)
-                                       : cudaLaunchKernelEx(&cfg, k_persistent<kTileMarch>, a);
+  void* args[] = {const_cast<PersistentArgs*>(&a)};
+  return cudaLaunchKernelExC(&cfg, persistent_kernel(c->plan.kind, part), args);
 }
 
-// Records the persistent block: barrier reset, the cooperative kernel, the
-// counter advance.
-int issue_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, const BlockCounts& bc) {
-  XY_TRY(c, cudaMemsetAsync(a.bar, 0, kBarBytes, st));
-  XY_TRY(c, launch_persistent(c, st, a));
-  k_advance<<<1, 1, 0, st>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
-  XY_CHECK_LAUNCH(c);
-  return XY_OK;
+// Issues the persistent launches of `ns` sweeps starting at host sweep
+// index s0 on `st` -- the barrier reset, then per sweep the Metropolis part,
+// the over-relaxation part and (measured or exchanging sweeps) the finish
+// part -- followed by the counter advance.  No synchronisation.
+cudaError_t issue_persistent(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, int se, uint64_t s0,
+                             const BlockCounts& bc) {
+  PersistentArgs a = persistent_args(c);
+  cudaError_t e = cudaMemsetAsync(a.bar, 0, kBarBytes, st);
+  uint64_t n_rec = 0, n_swp = 0;
+  for (int s = 0; s < ns && e == cudaSuccess; ++s) {
+    const bool meas = due(s0 + s, me), swp = due(s0 + s, se);
+    for (int part = kPartMetropolis; part <= kPartFinish && e == cudaSuccess; ++part) {
+      const int n_pass = part == kPartMetropolis ? nM : (part == kPartOverrelax ? nOR : 0);
+      if (part == kPartFinish ? !(meas || swp) : n_pass == 0) continue;
+      a.n_pass = n_pass;
+      a.mpass_off = static_cast<uint64_t>(s) * nM;
+      a.fp.sweep_off = s;
+      a.fp.series_off = n_rec;
+      a.fp.swap_off = n_swp;
+      a.fp.record = meas ? 1 : 0;
+      a.fp.swap = swp ? 1 : 0;
+      e = launch_persistent(c, st, a, part);
+      a.bar0 += persistent_barriers(part, n_pass, a.fp.swap);
+      // half-sweeps of this launch: 2 per pass, the finish part's measure pass
+      const unsigned long long halves = part == kPartFinish ? 1ull : 2ull * n_pass;
+      a.work0 += halves * (static_cast<unsigned long long>(c->plan.n_items) + c->plan.G);
+    }
+    n_rec += meas ? 1 : 0;
+    n_swp += swp ? 1 : 0;
+  }
+  if (e == cudaSuccess) {
+    k_advance<<<1, 1, 0, st>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
+    e = cudaGetLastError();
+  }
+  return e;
 }
 
 int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
@@ -1221,11 +1247,11 @@ int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
   bc.sweeps = ns;
   bc.swaps = count_due(s0, ns, se);
   bc.records = count_due(s0, ns, me);
-  const PersistentArgs a = persistent_args(c, nM, nOR, ns, me, se);
   bool launched = false;
   if (c->plan.graph_ok) {
-    // The kernel reads the device counters; only the counter advance baked
-    // into the graph depends on the phase of s0 against the two periods.
+    // The kernels read the device counters; which sweeps measure or
+    // exchange, and the counter advance, depend on the phase of s0 against
+    // the two periods.
     const uint64_t P = static_cast<uint64_t>(lcm_int(me > 0 ? me : 1, se > 0 ? se : 1));
     const auto key = std::make_tuple(nM, nOR, ns, me, se, static_cast<int>(s0 % P), 1);
     auto it = c->graphs.find(key);
@@ -1233,12 +1259,7 @@ int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
       cudaGraph_t g = nullptr;
       cudaError_t e = cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return fail_cuda(c, e, "cudaStreamBeginCapture");
-      cudaError_t e1 = cudaMemsetAsync(a.bar, 0, kBarBytes, c->cap_stream);
-      cudaError_t e2 = e1 == cudaSuccess ? launch_persistent(c, c->cap_stream, a) : e1;
-      if (e2 == cudaSuccess) {
-        k_advance<<<1, 1, 0, c->cap_stream>>>(c->ctr(), bc.mpass, bc.sweeps, bc.swaps, bc.records, bc.records);
-        e2 = cudaGetLastError();
-      }
+      const cudaError_t e2 = issue_persistent(c, c->cap_stream, nM, nOR, ns, me, se, s0, bc);
       e = cudaStreamEndCapture(c->cap_stream, &g);
       if (e2 == cudaSuccess && e == cudaSuccess) {
         cudaGraphExec_t ex = nullptr;
@@ -1258,10 +1279,7 @@ int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
       launched = true;
     }
   }
-  if (!launched) {
-    rc = issue_persistent(c, c->stream, a, bc);
-    if (rc != XY_OK) return rc;
-  }
+  if (!launched) XY_TRY(c, issue_persistent(c, c->stream, nM, nOR, ns, me, se, s0, bc));
   mirror_advance(c, bc);
   return sync_checked(c);
 }
@@ -1275,12 +1293,12 @@ int xy_debug_barrier_timeout(xy_ctx* c, int budget_us, int* status_out) {
   if (budget_us <= 0 || budget_us > 2000000) return XY_ERR_ARG;
   int rc = build_plan(c);
   if (rc != XY_OK) return rc;
-  PersistentArgs a = persistent_args(c, 0, 0, 0, 0, 0);
+  PersistentArgs a = persistent_args(c);
   a.poison = 1;
   a.budget_ns = static_cast<long long>(budget_us) * 1000;
   XY_TRY(c, cudaMemsetAsync(a.bar, 0, kBarBytes, c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));
-  XY_TRY(c, launch_persistent(c, c->stream, a));
+  XY_TRY(c, launch_persistent(c, c->stream, a, kPartOverrelax));
   int st = 0;
   XY_TRY(c, cudaMemcpyAsync(&st, a.status, 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));

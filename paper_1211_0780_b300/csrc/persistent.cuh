@@ -1,9 +1,16 @@
-// Persistent batched sweep: one cooperative launch advances every replica of
-// every lattice (uneven L included) through n_sweeps sweeps, with the fused
-// measurement and the on-device exchange of Sec. II, Eq. (3).  Each
-// half-sweep is a list of tile work items (lattice, slot, tile) that the host
-// scheduler spreads over the blocks by longest-processing-time-first; a
-// bounded grid barrier separates half-sweeps.
+// Persistent batched sweep: cooperative launches that each advance every
+// replica of every lattice (uneven L included) through one part of a sweep
+// -- its Metropolis passes, its over-relaxation passes, or the fused
+// measurement with the on-device exchange of Sec. II, Eq. (3) -- so that each
+// part's kernel keeps its own register budget (one kernel holding every
+// variant needed 246 registers a thread for the direct tile, two warps per
+// scheduler).  Each half-sweep is one list of tile work items (lattice,
+// slot, tile), sorted by the host by decreasing cost; the blocks take items
+// from the list in that order through one atomic counter, so the longest
+// items start first and a block that finishes early takes the next one
+// (longest-processing-time-first, balanced by the actual run times); a
+// bounded grid barrier separates the half-sweeps inside a launch, and the
+// launch boundary separates the parts.
 //
 // The barrier is two levels of monotonically increasing arrival counters:
 // block b arrives on group counter b mod kBarGroups (each on its own 128-byte
@@ -11,11 +18,14 @@
 // address); the block that completes its group's count for this barrier
 // instance adds one to the top counter, which every block polls with
 // acquire loads.  Barrier instance k completes when the top counter reaches
-// (k + 1) * (number of non-empty groups).  Every wait is bounded by a
-// %globaltimer budget; when it runs out the block sets the status word to
-// XY_ERR_TIMEOUT and every block leaves at its next barrier, so a missing
-// block ends the launch with an error, never a hang.  Co-residency of all
-// blocks is guaranteed by the cooperative launch.
+// (k + 1) * (number of non-empty groups); instances are numbered across the
+// launches of one xy_sweep call (the host passes each launch the number
+// completed before it), and the counters are cleared once per call.  Every
+// wait is bounded by a %globaltimer budget; when it runs out the block sets
+// the status word to XY_ERR_TIMEOUT and every block leaves at its next
+// barrier (and later launches return at once), so a missing block ends the
+// call with an error, never a hang.  Co-residency of all blocks is
+// guaranteed by the cooperative launch.
 #pragma once
 #include <cstdint>
 
@@ -26,17 +36,26 @@ namespace xy {
 
 constexpr int kBarGroups = 16;
 constexpr int kBarStride = 16;  // 64-bit words between counters (128 bytes)
+// The work counter sits after the barrier's group and top counters.
+constexpr int kBarWords = (kBarGroups + 2) * kBarStride;
+
+// The part of a sweep one persistent launch runs.
+enum PersistentPart : int { kPartMetropolis = 0, kPartOverrelax = 1, kPartFinish = 2 };
 
 struct PersistentArgs {
   PassParams pp;            // mpass_off and measure are set per pass
-  FinishParams fp;          // offsets, record and swap are set per sweep
+  FinishParams fp;          // offsets, record and swap set by the host per sweep
   const Lattice* lats;
-  const int4* items;        // (lattice, local slot, tile, unused)
-  const int* offs;          // items of block b: offs[b] .. offs[b+1]-1
+  const int4* items;        // (lattice, local slot, tile, unused), by decreasing cost
+  int n_items;              // items of one half-sweep
   int n_lat;
-  int nM, nOR, n_sweeps, me, se;
-  unsigned long long* bar;  // kBarGroups group counters then the top counter,
-                            // kBarStride words apart, zero at launch
+  int n_pass;               // kPartMetropolis / kPartOverrelax: passes of this launch
+  uint64_t mpass_off;       // kPartMetropolis: pass counter offset of its first pass
+  unsigned long long bar0;  // barrier instances completed before this launch
+  unsigned long long work0; // work-counter value at this launch's first half-sweep
+  unsigned long long* bar;  // kBarGroups group counters, the top counter, then
+                            // the work counter, kBarStride words apart, zero at
+                            // the call's start
   int* status;              // 0, or XY_ERR_TIMEOUT
   long long budget_ns;      // bound of one barrier wait
   int poison;               // test hook: the first barrier expects one block too many
@@ -93,47 +112,57 @@ __device__ __forceinline__ bool grid_barrier(const PersistentArgs& a, unsigned l
   return ok != 0;
 }
 
-__device__ __forceinline__ bool due_dev(uint64_t s, int every) {
-  return every > 0 && (s + 1) % static_cast<uint64_t>(every) == 0;
+// Barrier instances one launch of `part` runs: one between consecutive
+// half-sweeps; the finish part, one before the slots' sums and one before
+// the exchange.
+__host__ __device__ inline unsigned long long persistent_barriers(int part, int n_pass, int swap) {
+  return part == kPartFinish ? (swap ? 2ull : 1ull) : (n_pass > 0 ? 2ull * n_pass - 1ull : 0ull);
 }
 
 // Every lattice of a persistent launch uses tile kind KIND, with blocks of
-// at most 256 threads: the block kind with at least three blocks resident
-// per SM (80 registers); the march kind with two (128 registers; it spills
-// 272 bytes there, and ran 19% faster on a 64^3 x 32 ladder than with its
-// 217 registers unbounded); the direct kind with its registers unbounded
-// (246; at 128 it spilled 1.2 KB and ran 10% slower).  The direct kind's other-colour
-// loads go through L1: every half-sweep starts after a grid barrier whose
-// acquire (by one thread, then the block barrier) orders the block's later
-// loads after every block's writes of the previous half-sweep, as the
-// launch boundary does for the per-launch kernels.
+// at most 256 threads, and each part's kernel is compiled for the blocks per
+// SM its kind keeps: the block kind three (at most 80 registers), the march
+// and the direct kinds two (at most 128).  The direct kind's other-colour
+// loads go through L1: a half-sweep starts after the launch boundary or a
+// grid barrier whose acquire (by one thread, then the block barrier) orders
+// the block's later loads after every block's writes of the previous
+// half-sweep, as the launch boundary does for the per-launch kernels.
 constexpr int kPersistentBlockThreads = 256;
 
-template <int KIND>
-__global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 3 : (KIND == kTileMarch ? 2 : 1))
+template <int KIND, int PART>
+__global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 3 : 2)
     k_persistent(PersistentArgs a) {
   extern __shared__ __align__(16) float sm[];
-  unsigned long long nbar = 0;
+  unsigned long long nbar = a.bar0;
   if (a.poison) {  // test hook: the first barrier waits for one arrival too many
     grid_barrier(a, 0);
     return;
   }
+  if (*reinterpret_cast<volatile int*>(a.status) != 0) return;  // an earlier launch failed
   const int tid = threadIdx.x, B = blockDim.x;
-  const uint64_t s_base = a.pp.ctr[kCtrSweep];
-  const int n_pass = a.nM + a.nOR;
-  const int i0 = a.offs[blockIdx.x], i1 = a.offs[blockIdx.x + 1];
-  uint64_t n_rec = 0, n_swp = 0;
+  unsigned long long* const work = a.bar + (kBarGroups + 1) * kBarStride;
+  // Every block makes one failing grab per half-sweep, so each half-sweep
+  // advances the counter by exactly n_items + gridDim.x.
+  unsigned long long base = a.work0;
+  __shared__ int s_item;
   // One pass of colour `colour` over this block's tile items.  The update
   // passes never measure: the lattice sums of a measured sweep come from a
   // measure-only pass after its last half-sweep, which forms the same
   // per-thread sums in the same order as the per-launch path's fused pass
   // (the white sites' stored spins are the updated ones), so the records
-  // are identical; keeping the measuring update variants out of this kernel
-  // lets the march kind keep two blocks per SM.
+  // are identical.
   auto tile_items = [&](auto mode, int colour, const PassParams& pp) {
     constexpr int MODE = decltype(mode)::value;
     constexpr bool MEAS = MODE == kMeasureOnly;
-    for (int it = i0; it < i1; ++it) {
+    for (;;) {
+      if (tid == 0) {
+        const unsigned long long t = atomicAdd(work, 1ull) - base;
+        s_item = t < static_cast<unsigned long long>(a.n_items) ? static_cast<int>(t) : -1;
+      }
+      __syncthreads();
+      const int it = s_item;
+      __syncthreads();  // every thread has read s_item before it is written again
+      if (it < 0) break;
       const int4 w = a.items[it];
       const Lattice lat = a.lats[w.x];
       const int TX = lat.L >> 3;
@@ -159,55 +188,45 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
         block_sums_to(pp.partials + part * kNumSums, acc, tid, B, red);
       }
     }
+    base += static_cast<unsigned long long>(a.n_items) + gridDim.x;
   };
-  for (int s = 0; s < a.n_sweeps; ++s) {
-    const uint64_t sw = s_base + s;
-    const bool meas = due_dev(sw, a.me), swp = due_dev(sw, a.se);
-    for (int p = 0; p < n_pass; ++p) {
-      const bool is_met = p < a.nM;
+  if (PART != kPartFinish) {
+    for (int p = 0; p < a.n_pass; ++p) {
       for (int colour = 0; colour < 2; ++colour) {
+        if (p > 0 || colour > 0)
+          if (!grid_barrier(a, nbar++)) return;
         PassParams pp = a.pp;
-        pp.mpass_off = is_met ? static_cast<uint64_t>(s) * a.nM + p : 0ull;
         pp.measure = 0;
-        if (is_met)
+        if (PART == kPartMetropolis) {
+          pp.mpass_off = a.mpass_off + static_cast<uint64_t>(p);
           tile_items(IC<kMetropolis>{}, colour, pp);
-        else
+        } else {
+          pp.mpass_off = 0ull;
           tile_items(IC<kOverrelax>{}, colour, pp);
-        if (!grid_barrier(a, nbar++)) return;
-      }
-    }
-    if (meas || swp) {
-      PassParams pp = a.pp;
-      pp.measure = 1;
-      tile_items(IC<kMeasureOnly>{}, 1, pp);
-      if (!grid_barrier(a, nbar++)) return;
-    }
-    if (meas || swp) {
-      FinishParams fp = a.fp;
-      fp.sweep_off = s;
-      fp.series_off = n_rec;
-      fp.swap_off = n_swp;
-      fp.record = meas ? 1 : 0;
-      fp.swap = swp ? 1 : 0;
-      // every slot's sums and record on its own warp, spread over the grid,
-      // then (after a barrier) each ladder's exchange on one block
-      const int lane = tid & 31, nwb = B >> 5;
-      for (int g = blockIdx.x * nwb + (tid >> 5); g < fp.n_slots; g += gridDim.x * nwb) {
-        int lo = 0, hi = a.n_lat - 1;  // the lattice of slot g
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (a.lats[mid].slot0 <= g) lo = mid;
-          else hi = mid - 1;
         }
-        finish_slot(a.lats[lo], g - a.lats[lo].slot0, fp, lane);
       }
-      if (swp) {
-        if (!grid_barrier(a, nbar++)) return;
-        for (int l = blockIdx.x; l < a.n_lat; l += gridDim.x) exchange_ladder(a.lats[l], l, fp, tid, B);
+    }
+  } else {
+    PassParams pp = a.pp;
+    pp.measure = 1;
+    tile_items(IC<kMeasureOnly>{}, 1, pp);
+    if (!grid_barrier(a, nbar++)) return;
+    // every slot's sums and record on its own warp, spread over the grid,
+    // then (after a barrier) each ladder's exchange on one block
+    const FinishParams& fp = a.fp;
+    const int lane = tid & 31, nwb = B >> 5;
+    for (int g = blockIdx.x * nwb + (tid >> 5); g < fp.n_slots; g += gridDim.x * nwb) {
+      int lo = 0, hi = a.n_lat - 1;  // the lattice of slot g
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (a.lats[mid].slot0 <= g) lo = mid;
+        else hi = mid - 1;
       }
-      n_rec += meas ? 1 : 0;
-      n_swp += swp ? 1 : 0;
+      finish_slot(a.lats[lo], g - a.lats[lo].slot0, fp, lane);
+    }
+    if (fp.swap) {
       if (!grid_barrier(a, nbar++)) return;
+      for (int l = blockIdx.x; l < a.n_lat; l += gridDim.x) exchange_ladder(a.lats[l], l, fp, tid, B);
     }
   }
 }

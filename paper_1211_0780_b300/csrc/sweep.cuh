@@ -599,10 +599,8 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   const uint32_t offh0 = static_cast<uint32_t>(H * y + ((tx == 0) ? H - 1 : 4 * tx - 1));
   const uint32_t offh1 = static_cast<uint32_t>(H * y + ((4 * tx + 4 == H) ? 0 : 4 * tx + 4));
 
-  float beta = 0.f;
   uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
   if (MODE == kMetropolis) {
-    beta = __ldcg(pp.beta_slot + lat.slot0 + r);
     tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) |
            kTagMet;
     const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
@@ -615,23 +613,43 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   // use, z+2 being loaded), and two sets of the other operands alternate
   // (this plane's, the next plane's, loaded one plane ahead); the plane loop
   // is unrolled four times so that every load lands in a free register and
-  // nothing is copied.
+  // nothing is copied.  The Metropolis words of a plane are drawn with its
+  // operands, one plane ahead, so that the Philox integer work of the next
+  // plane overlaps this plane's update (8.7 instead of 9.1 us at 160^3).
   struct Operands {
     Spins4 own, ym, yp;  // own spins; other colour's rows y-1, y+1
     float hc, hs;        // x-halo element
+    uint4 w0, w1;        // Metropolis words of sites (0, 1) and (2, 3)
   };
   Spins4 P0, P1, P2, P3{};
   Operands A, B;
-  auto load_operands = [&](Operands& o, int z, uint32_t pz) {
+  // The own colour's spins and the Metropolis words of one plane.
+  auto load_own = [&](Operands& o, uint32_t pz) {
     o.own = ld_spins(sg, own + offy + pz, half);
+    if (MODE == kMetropolis) {
+      const uint32_t q0 = (offy + pz) >> 1;
+      o.w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+      o.w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+    } else {
+      o.w0 = o.w1 = make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  // The other colour's operands of one plane (rows y -+ 1, x halo).
+  auto load_other = [&](Operands& o, int z, uint32_t pz) {
     o.ym = ld_spins_l1(sg, oth + offym + pz, half);
     o.yp = ld_spins_l1(sg, oth + offyp + pz, half);
     const uint32_t oh = (((y + z + colour) & 1) ? offh1 : offh0) + pz;
     o.hc = ld1_l1(sg, oth + oh);
     o.hs = ld1_l1(sg, oth + oh + half);
   };
+  auto load_operands = [&](Operands& o, int z, uint32_t pz) {
+    load_own(o, pz);
+    load_other(o, z, pz);
+  };
+  float beta = 0.f;
   {
     const uint32_t zz = static_cast<uint32_t>(z0) * PS;
+    if (MODE == kMetropolis) beta = __ldcg(pp.beta_slot + lat.slot0 + r);
     P3 = ld_spins_l1(sg, oth + offy + static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS, half);
     P0 = ld_spins_l1(sg, oth + offy + zz, half);
     P1 = ld_spins_l1(sg, oth + offy + static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS, half);
@@ -648,17 +666,12 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
     }
     const int s = (y + z + colour) & 1;
     const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
-    uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
-    if (MODE == kMetropolis) {
-      const uint32_t q0 = offz >> 1;
-      w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
-      w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
-    }
     float stepv[kNumSums];
 #pragma unroll
     for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
     Spins4 nw;
-    update4<MODE, MEAS>(zc, cur.hc, cur.hs, s, cur.ym, cur.yp, zm, zn, cur.own, w0, w1, beta, nw, n_acc, stepv);
+    update4<MODE, MEAS>(zc, cur.hc, cur.hs, s, cur.ym, cur.yp, zm, zn, cur.own, cur.w0, cur.w1, beta, nw, n_acc,
+                        stepv);
     if (MEAS) sums.add_plane(stepv);
     if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
   };
