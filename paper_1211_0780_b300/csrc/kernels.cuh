@@ -120,7 +120,7 @@ __global__ void __launch_bounds__(512) k_half(Lattice lat, int colour, PassParam
 template <int MODE, bool MEAS, int LC>
 __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDirectMaxRegs) k_half_direct(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
-  chain_wait_and_release();
+  if (!pp.own_ready) chain_wait_and_release();  // else tile_direct waits after its own-colour loads
   const int r = blockIdx.y;
   const int t = blockIdx.x;
   const int yt = t % lat.nyt, zt = t / lat.nyt;

@@ -165,6 +165,7 @@ struct xy_ctx {
     p.acc_met = at<unsigned long long>(lay.acc_met);
     p.measure = measure;
     p.poison = 0;
+    p.own_ready = 0;
     p.status = at<int>(lay.status);
     p.wait_ns = 1000000000ll;  // a copied plane lands in microseconds
     return p;
@@ -382,7 +383,10 @@ int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, in
         const bool last = (p == n_pass - 1);
         for (int colour = 0; colour < 2; ++colour) {
           const int measure = (needE && last && colour == 1) ? 1 : 0;
-          const PassParams pp = c->pass_params(true, p < nM ? mp : 0, measure);
+          PassParams pp = c->pass_params(true, p < nM ? mp : 0, measure);
+          // Every half-sweep of a sweep but the first is chained behind the
+          // other colour's half-sweep on the same stream (see tile_direct).
+          pp.own_ready = (p > 0 || colour > 0) ? 1 : 0;
           int rc;
           if (branches)
             rc = p < nM ? launch_half<kMetropolis>(c, c->lat_streams[i], i, colour, pp)

@@ -127,6 +127,9 @@ struct PassParams {
   unsigned long long* acc_met;  // accepted proposals per global slot
   int measure;                  // fuse the lattice sums (white passes only)
   int poison;                   // test hook (kTileStream): plane 2 is never copied
+  int own_ready;                // kTileDirect launches chained by the library: the
+                                // own colour and the pass counter are final before
+                                // griddepcontrol.wait (see tile_direct)
   int* status;                  // set to XY_ERR_TIMEOUT when a bounded wait runs out
   long long wait_ns;            // bound of one wait for a copied plane
 };
@@ -649,11 +652,25 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   float beta = 0.f;
   {
     const uint32_t zz = static_cast<uint32_t>(z0) * PS;
+    // A launch chained by the library behind the other colour's half-sweep
+    // (pp.own_ready) reads its own colour and draws its first plane's words
+    // before griddepcontrol.wait: its predecessor writes only the other
+    // colour, and the own colour's last writer, the launch before that, has
+    // completed once the predecessor passed its own wait, which it did
+    // before releasing this launch.  Everything the predecessor may write
+    // (the other colour, the coupling after an exchange) is read after it.
+    if (pp.own_ready) {
+      load_own(A, zz);
+      chain_wait_and_release();
+    }
     if (MODE == kMetropolis) beta = __ldcg(pp.beta_slot + lat.slot0 + r);
     P3 = ld_spins_l1(sg, oth + offy + static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS, half);
     P0 = ld_spins_l1(sg, oth + offy + zz, half);
     P1 = ld_spins_l1(sg, oth + offy + static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS, half);
-    load_operands(A, z0, zz);
+    if (pp.own_ready)
+      load_other(A, z0, zz);
+    else
+      load_operands(A, z0, zz);
   }
 
   // One plane: zm, zc, zn = planes z-1, z, z+1; zf receives plane z+2; cur
