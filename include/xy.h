@@ -21,7 +21,8 @@
  *     XY_ERR_BOUNDS every call on the context returns XY_ERR_STATE until
  *     xy_destroy.
  *   - A spin is stored on the device as its unit vector (cos theta,
- *     sin theta) in FP32.  Angles exchanged with the host (xy_get_state /
+ *     sin theta) in FP32 (as its FP32 angle on tile kind 4, see
+ *     xy_set_tile).  Angles exchanged with the host (xy_get_state /
  *     xy_set_state) are FP32 radians in [0, 2 pi).
  *
  * Lattice, colours and layout.  Site (x, y, z), 0 <= x, y, z < L, has colour
@@ -182,7 +183,8 @@ int xy_series_count(xy_ctx *ctx, int64_t *n_out);
  * concatenated, natural layout, sum over slots of L^3 floats; get_state
  * returns atan2(sin, cos) of the stored vectors taken into [0, 2 pi),
  * set_state stores (cos, sin) of the given angles (sincosf; every angle
- * must be finite).  perm: for each ladder in order, n_replicas entries
+ * must be finite); on tile kind 4 (angle storage) the stored angles are
+ * returned as they are and the given ones stored taken into [0, 2 pi).  perm: for each ladder in order, n_replicas entries
  * (beta index -> local slot).  counters[4] = {Metropolis passes, sweeps,
  * exchange events, records}.  Any pointer may be NULL to skip that part.
  * Every draw is a pure function of (seed, counters, slot, site), so
@@ -200,7 +202,10 @@ int xy_set_state(xy_ctx *ctx, const float *host_angles, const int32_t *perm,
  * workspace and a host buffer of sum over slots of 2 L^3 floats (pinned
  * memory makes the copy asynchronous; the call returns after it completes).
  * Bit-exact checkpoints and host round trips without the conversion of
- * xy_get_state / xy_set_state; set_packed takes the vectors as given. */
+ * xy_get_state / xy_set_state; set_packed takes the vectors as given.  A
+ * lattice on tile kind 4 (angle storage) holds its angles where the
+ * cosines are (the sine places are unused); a packed state is restored on a
+ * lattice of the same storage. */
 int xy_get_packed(xy_ctx *ctx, float *host_packed);
 int xy_set_packed(xy_ctx *ctx, const float *host_packed);
 
@@ -209,8 +214,9 @@ int xy_set_packed(xy_ctx *ctx, const float *host_packed);
  * buffer of sum over slots of L^3 floats, half the bytes of the packed
  * vectors.  set: stream-ordered copy into the workspace and conversion on
  * the device with sincosf (the values must be finite; they are not
- * inspected); get: atan2 on the device, wrapped into [0, 2 pi) as
- * xy_get_state.  Both return after the copy completes (pinned memory makes
+ * inspected; on tile kind 4 the angles are taken into [0, 2 pi) and kept);
+ * get: atan2 on the device, wrapped into [0, 2 pi) as xy_get_state (on
+ * tile kind 4 the stored angles themselves).  Both return after the copy completes (pinned memory makes
  * it asynchronous to the host until then). */
 int xy_set_packed_angles(xy_ctx *ctx, const float *host_angles);
 int xy_get_packed_angles(xy_ctx *ctx, float *host_angles);
@@ -289,11 +295,20 @@ int xy_debug_fast_math(int kind, int64_t n, const void *d_in, float *d_out,
  * barriers: each thread loads its y-neighbour rows and x-halo element
  * itself through the L1 cache, one plane ahead (in XY_EXEC_PERSISTENT the
  * grid barrier between half-sweeps orders those loads after the previous
- * half-sweep's writes).  xy_set_tile checks 1 <= ty, tz <= L, the block size against
+ * half-sweep's writes).  kind 4 (angle): the direct tile on a lattice kept
+ * as FP32 angles in [0, 2 pi) instead of vectors (4 instead of 8 bytes per
+ * spin; each colour's angles sit where its cosines are in the vector
+ * layout): every angle read is turned into its vector by the fast sincos
+ * and the update stores the new angle (the proposal's, or atan2 of the
+ * reflected vector).  Changing a lattice between kind 4 and another kind
+ * converts its state in place (atan2f / sincosf, within 1e-6 rad).
+ * xy_set_tile checks 1 <= ty, tz <= L, the block size against
  * the kernels' limit (512 threads at their register use on sm_103a; 240
- * for kind 3), tz <= 64 for kind 1, and that the tile count fits the
+ * for kinds 3 and 4), tz <= 64 for kind 1, and that the tile count fits the
  * partial-sum area (ceil(L/ty) ceil(L/tz) <= L^2/4).  Spins do not depend
- * on the tile (the lattice sums only through FP64 summation order). */
+ * on the tile among kinds 0-3 (the lattice sums only through FP64 summation
+ * order), nor on the shape within kind 4; kind 4 differs from the others by
+ * the fast sincos of the neighbours (a few 1e-7 per vector). */
 int xy_set_tile(xy_ctx *ctx, int lattice, int kind, int ty, int tz);
 int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
 
@@ -301,12 +316,14 @@ int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
  * the device for sweeps of `n_metropolis` + `n_overrelax` passes (the spins,
  * counters and accept counts are saved and restored); the choice stays in
  * the context.  Outside XY_EXEC_PERSISTENT every kind (0-3) is a
- * candidate.  In XY_EXEC_PERSISTENT mode one tile kind serves every
- * lattice (xy_sweep returns XY_ERR_ARG otherwise) and the block is as wide
- * as the widest tile: for the march, the block and the direct kind and for
- * tiles of at most 64, 128 and 256 threads, each lattice's best tile is
- * found as above, and the nine sets are timed in the persistent launch
- * itself; the fastest is kept. */
+ * candidate, and kind 4 too when the context's vector state is larger than
+ * the device's L2 cache (there a half-sweep is bound by HBM bytes, which
+ * angle storage halves).  In XY_EXEC_PERSISTENT mode one tile kind serves
+ * every lattice (xy_sweep returns XY_ERR_ARG otherwise) and the block is as
+ * wide as the widest tile: for the march, the block, the direct (and, as
+ * above, the angle) kind and for tiles of at most 64, 128 and 256 threads,
+ * each lattice's best tile is found as above, and the sets are timed in the
+ * persistent launch itself; the fastest is kept. */
 int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
 
 /* Device-side status word of the last persistent launch (0 = fine). */

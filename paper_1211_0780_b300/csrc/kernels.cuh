@@ -38,26 +38,37 @@ __global__ void k_init(Lattice lat, uint64_t seed) {
   }
 }
 
+// An angle taken into [0, 2 pi) (a value that rounds to 2 pi is 0).
+__device__ __forceinline__ float mod_two_pi(float t) {
+  t = fmodf(t, kTwoPi);
+  t = t < 0.f ? t + kTwoPi : t;
+  return t >= kTwoPi ? 0.f : t;
+}
+
 // Angles of one slot in the packed order (colour 0 then colour 1, N/2 each):
-// theta = atan2(sin, cos) taken into [0, 2 pi).
-__global__ void k_to_angles(const float* __restrict__ spins, long long N, float* __restrict__ out) {
+// theta = atan2(sin, cos) taken into [0, 2 pi), or the stored angle itself
+// (angle storage, kTileAngle).
+__global__ void k_to_angles(const float* __restrict__ spins, long long N, float* __restrict__ out, int angles) {
   const long long half = N >> 1;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long c = i / half, p = i - c * half;
     const float* base = spins + c * N;
-    float t = atan2f(base[p + half], base[p]);
-    t = t < 0.f ? t + kTwoPi : t;
-    out[i] = t >= kTwoPi ? 0.f : t;
+    out[i] = angles ? base[p] : wrap_angle(atan2f(base[p + half], base[p]));
   }
 }
 
-// The inverse: packed angles of one slot to stored (cos, sin) with sincosf.
-__global__ void k_from_angles(const float* __restrict__ in, long long N, float* __restrict__ spins) {
+// The inverse: packed angles of one slot to stored (cos, sin) with sincosf,
+// or (angle storage) to the stored angle taken into [0, 2 pi).
+__global__ void k_from_angles(const float* __restrict__ in, long long N, float* __restrict__ spins, int angles) {
   const long long half = N >> 1;
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < N;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long c = i / half, p = i - c * half;
+    if (angles) {
+      spins[c * N + p] = mod_two_pi(in[i]);
+      continue;
+    }
     float sn, cs;
     sincosf(in[i], &sn, &cs);
     spins[c * N + p] = cs;
@@ -65,16 +76,35 @@ __global__ void k_from_angles(const float* __restrict__ in, long long N, float* 
   }
 }
 
+// In place, for n_slots slots of 2N floats: every stored vector (cos, sin)
+// becomes its angle atan2(sin, cos) in [0, 2 pi), written where the cosine
+// was (the change to angle storage, kTileAngle).
+__global__ void k_vectors_to_angles(float* __restrict__ spins, long long N, int n_slots) {
+  const long long half = N >> 1;
+  const long long total = static_cast<long long>(n_slots) * N;
+  for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
+       i += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long r = i / N, q = i - r * N, c = q / half, p = q - c * half;
+    float* base = spins + 2 * r * N + c * N;
+    base[p] = wrap_angle(atan2f(base[half + p], base[p]));
+  }
+}
+
 // In place: the angle stored in each cos slot of n_slots slots (each 2N
 // floats: colour 0's N/2 cosines, its N/2 sines, colour 1's ...) becomes
-// the (cos, sin) pair, with sincosf as k_from_angles uses it.
-__global__ void k_angles_in_place(float* __restrict__ spins, long long N, int n_slots) {
+// the (cos, sin) pair, with sincosf as k_from_angles uses it; or, for a
+// lattice kept as angles (angles != 0), is taken into [0, 2 pi) and stays.
+__global__ void k_angles_in_place(float* __restrict__ spins, long long N, int n_slots, int angles) {
   const long long half = N >> 1;
   const long long total = static_cast<long long>(n_slots) * N;  // angles
   for (long long i = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; i < total;
        i += static_cast<long long>(gridDim.x) * blockDim.x) {
     const long long r = i / N, q = i - r * N, c = q / half, p = q - c * half;
     float* base = spins + 2 * r * N + c * N;
+    if (angles) {
+      base[p] = mod_two_pi(base[p]);
+      continue;
+    }
     float sn, cs;
     sincosf(base[p], &sn, &cs);
     base[p] = cs;
@@ -129,6 +159,29 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDi
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
   tile_direct<MODE, MEAS, LC>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
+  const int tid = threadIdx.x + blockDim.x * threadIdx.y;
+  const int nth = blockDim.x * blockDim.y;
+  if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);
+  if (MEAS) {
+    const long long part = lat.part0 + static_cast<long long>(r) * lat.nyt * lat.nzt + t;
+    block_sums_to(pp.partials + part * kNumSums, acc, tid, nth, reinterpret_cast<double*>(sm));
+  }
+}
+
+// One half-sweep of one lattice with the kTileAngle tile (angle storage):
+// grid and block as k_half_direct.
+template <int MODE, bool MEAS, int LC>
+__global__ void __maxnreg__(kDirectMaxRegs) k_half_angle(Lattice lat, int colour, PassParams pp) {
+  extern __shared__ __align__(16) float sm[];
+  if (!pp.own_ready) chain_wait_and_release();  // else tile_angle waits after its own-colour loads
+  const int r = blockIdx.y;
+  const int t = blockIdx.x;
+  const int yt = t % lat.nyt, zt = t / lat.nyt;
+  float acc[kNumSums];
+#pragma unroll
+  for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
+  uint32_t n_acc = 0u;
+  tile_angle<MODE, MEAS, LC>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nth = blockDim.x * blockDim.y;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);

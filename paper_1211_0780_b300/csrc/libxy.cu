@@ -179,7 +179,7 @@ thread_local char g_last_cuda_error[256] = {0};
 // Threads a tile of this kind may have: the kTileDirect kernels are compiled
 // for smaller blocks than the others.
 int kind_max_threads(const xy_ctx* c, int kind) {
-  return kind == kTileDirect ? std::min(c->max_block, kDirectMaxThreads) : c->max_block;
+  return (kind == kTileDirect || kind == kTileAngle) ? std::min(c->max_block, kDirectMaxThreads) : c->max_block;
 }
 
 int fail_cuda(xy_ctx* c, cudaError_t e, const char* what) {
@@ -238,6 +238,22 @@ void default_tile(LatHost& h) {
   }
 }
 
+// Converts lattice i's stored state in place between vectors and angles
+// when a change of tile kind changes its storage (kTileAngle keeps angles,
+// every other kind vectors).  Ordered on the context's stream.
+int convert_storage(xy_ctx* c, int i, bool to_angles) {
+  const LatHost& h = c->lat[i];
+  const long long N = h.N(), n = N * h.R;
+  float* dst = c->spins() + h.spin_off;
+  const int blocks = static_cast<int>(std::min<long long>((n + 255) / 256, 4096));
+  if (to_angles)
+    k_vectors_to_angles<<<blocks, 256, 0, c->stream>>>(dst, N, h.R);
+  else
+    k_angles_in_place<<<blocks, 256, 0, c->stream>>>(dst, N, h.R, 0);
+  XY_CHECK_LAUNCH(c);
+  return XY_OK;
+}
+
 int sync_lats(xy_ctx* c) {
   std::vector<Lattice> d(c->n_lat);
   for (int i = 0; i < c->n_lat; ++i) d[i] = c->dev_lat(i);
@@ -283,6 +299,16 @@ cudaError_t launch_direct(dim3 grid, dim3 block, int smem, cudaStream_t st, cons
   return launch_chained(k_half_direct<M, false, LC>, grid, block, smem, st, d, colour, pp);
 }
 
+// kTileAngle half-sweep (angle storage; L read at run time).
+template <int MODE>
+cudaError_t launch_angle(dim3 grid, dim3 block, int smem, cudaStream_t st, const Lattice& d, int colour,
+                         const PassParams& pp) {
+  constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
+  if (MODE == kMeasureOnly) return launch_chained(k_half_angle<kMeasureOnly, true, 0>, grid, block, smem, st, d, colour, pp);
+  if (pp.measure && colour == 1) return launch_chained(k_half_angle<M, true, 0>, grid, block, smem, st, d, colour, pp);
+  return launch_chained(k_half_angle<M, false, 0>, grid, block, smem, st, d, colour, pp);
+}
+
 template <int MODE, int KIND>
 cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st, int colour,
                              const PassParams& pp) {
@@ -301,6 +327,8 @@ cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st
       case kDirectSizes[4]: return launch_direct<MODE, kDirectSizes[4]>(grid, block, smem, st, d, colour, pp);
       default: return launch_direct<MODE, 0>(grid, block, smem, st, d, colour, pp);
     }
+  } else if constexpr (KIND == kTileAngle) {
+    return launch_angle<MODE>(grid, block, smem, st, d, colour, pp);
   } else {
     if (MODE == kMeasureOnly) return launch_chained(k_half<kMeasureOnly, true, KIND>, grid, block, smem, st, d, colour, pp);
     if (pp.measure && colour == 1) return launch_chained(k_half<M, true, KIND>, grid, block, smem, st, d, colour, pp);
@@ -315,6 +343,7 @@ int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams&
   const cudaError_t e = h.kind == kTileBlock    ? launch_half_kind<MODE, kTileBlock>(h, d, st, colour, pp)
                        : h.kind == kTileStream ? launch_half_kind<MODE, kTileStream>(h, d, st, colour, pp)
                        : h.kind == kTileDirect ? launch_half_kind<MODE, kTileDirect>(h, d, st, colour, pp)
+                       : h.kind == kTileAngle  ? launch_half_kind<MODE, kTileAngle>(h, d, st, colour, pp)
                                                : launch_half_kind<MODE, kTileMarch>(h, d, st, colour, pp);
   XY_TRY(c, e);
   return XY_OK;
@@ -592,12 +621,17 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
   }
   // The kTileDirect kernels: their own block limit (kDirectMaxThreads), no
   // tile in shared memory.
-  const void* direct_kernels[5] = {
+  const void* direct_kernels[10] = {
       reinterpret_cast<const void*>(k_half_direct<kMetropolis, false, 0>),
       reinterpret_cast<const void*>(k_half_direct<kMetropolis, true, 0>),
       reinterpret_cast<const void*>(k_half_direct<kOverrelax, false, 0>),
       reinterpret_cast<const void*>(k_half_direct<kOverrelax, true, 0>),
-      reinterpret_cast<const void*>(k_half_direct<kMeasureOnly, true, 0>)};
+      reinterpret_cast<const void*>(k_half_direct<kMeasureOnly, true, 0>),
+      reinterpret_cast<const void*>(k_half_angle<kMetropolis, false, 0>),
+      reinterpret_cast<const void*>(k_half_angle<kMetropolis, true, 0>),
+      reinterpret_cast<const void*>(k_half_angle<kOverrelax, false, 0>),
+      reinterpret_cast<const void*>(k_half_angle<kOverrelax, true, 0>),
+      reinterpret_cast<const void*>(k_half_angle<kMeasureOnly, true, 0>)};
   for (const void* fn : direct_kernels) {
     cudaFuncAttributes fa{};
     e = cudaFuncGetAttributes(&fa, fn);
@@ -827,7 +861,8 @@ int xy_get_state(xy_ctx* c, float* host_angles, int32_t* perm, uint64_t* counter
       std::vector<float> packed(static_cast<size_t>(N));
       for (int r = 0; r < h.R; ++r) {
         float* stage = c->at<float>(c->lay.staging);
-        k_to_angles<<<conv_blocks(N), 256, 0, c->stream>>>(c->spins() + h.spin_off + 2 * r * N, N, stage);
+        k_to_angles<<<conv_blocks(N), 256, 0, c->stream>>>(c->spins() + h.spin_off + 2 * r * N, N, stage,
+                                                           angle_storage(h.kind) ? 1 : 0);
         XY_CHECK_LAUNCH(c);
         XY_TRY(c, cudaMemcpyAsync(packed.data(), stage, N * 4, cudaMemcpyDeviceToHost, c->stream));
         XY_TRY(c, cudaStreamSynchronize(c->stream));
@@ -879,7 +914,8 @@ int xy_set_state(xy_ctx* c, const float* host_angles, const int32_t* perm, const
             }
         float* stage = c->at<float>(c->lay.staging);
         XY_TRY(c, cudaMemcpyAsync(stage, packed.data(), N * 4, cudaMemcpyHostToDevice, c->stream));
-        k_from_angles<<<conv_blocks(N), 256, 0, c->stream>>>(stage, N, c->spins() + h.spin_off + 2 * r * N);
+        k_from_angles<<<conv_blocks(N), 256, 0, c->stream>>>(stage, N, c->spins() + h.spin_off + 2 * r * N,
+                                                             angle_storage(h.kind) ? 1 : 0);
         XY_CHECK_LAUNCH(c);
         XY_TRY(c, cudaStreamSynchronize(c->stream));
         at += static_cast<size_t>(N);
@@ -976,7 +1012,8 @@ int xy_set_packed_angles(xy_ctx* c, const float* host_angles) {
                                 static_cast<size_t>(N / 2) * 4, static_cast<size_t>(2 * h.R), cudaMemcpyHostToDevice,
                                 c->stream));
     const long long n = N * h.R;
-    k_angles_in_place<<<static_cast<int>(std::min<long long>((n + 255) / 256, 4096)), 256, 0, c->stream>>>(dst, N, h.R);
+    k_angles_in_place<<<static_cast<int>(std::min<long long>((n + 255) / 256, 4096)), 256, 0, c->stream>>>(
+        dst, N, h.R, angle_storage(h.kind) ? 1 : 0);
     XY_CHECK_LAUNCH(c);
     at += static_cast<size_t>(n);
   }
@@ -1013,7 +1050,8 @@ int xy_get_packed_angles(xy_ctx* c, float* host_angles) {
   for (const LatHost& h : c->lat) {
     const long long N = h.N();
     for (int r = 0; r < h.R; ++r) {
-      k_to_angles<<<conv_blocks(N), 256, 0, c->stream>>>(c->spins() + h.spin_off + 2 * r * N, N, stage);
+      k_to_angles<<<conv_blocks(N), 256, 0, c->stream>>>(c->spins() + h.spin_off + 2 * r * N, N, stage,
+                                                         angle_storage(h.kind) ? 1 : 0);
       XY_CHECK_LAUNCH(c);
       XY_TRY(c, cudaMemcpyAsync(host_angles + at, stage, static_cast<size_t>(N) * 4, cudaMemcpyDeviceToHost,
                                 c->stream));
@@ -1063,7 +1101,8 @@ int xy_debug_fast_math(int kind, int64_t n, const void* d_in, float* d_out, void
 int xy_set_tile(xy_ctx* c, int lattice, int kind, int ty, int tz) {
   XY_ENTER(c);
   if (lattice < 0 || lattice >= c->n_lat) return XY_ERR_ARG;
-  if (kind != kTileMarch && kind != kTileBlock && kind != kTileStream && kind != kTileDirect) return XY_ERR_ARG;
+  if (kind != kTileMarch && kind != kTileBlock && kind != kTileStream && kind != kTileDirect && kind != kTileAngle)
+    return XY_ERR_ARG;
   LatHost h = c->lat[lattice];
   h.kind = kind;
   h.ty = ty;
@@ -1072,6 +1111,10 @@ int xy_set_tile(xy_ctx* c, int lattice, int kind, int ty, int tz) {
   if (kind == kTileBlock && tz > 64) return XY_ERR_ARG;  // block z extent
   if (h.nyt() * h.nzt() > h.part_cap) return XY_ERR_ARG;
   if (h.smem() > 200 * 1024) return XY_ERR_ARG;
+  if (angle_storage(h.kind) != angle_storage(c->lat[lattice].kind)) {
+    const int rc = convert_storage(c, lattice, angle_storage(h.kind));
+    if (rc != XY_OK) return rc;
+  }
   c->lat[lattice] = h;
   drop_graphs(c);
   return sync_lats(c);
@@ -1106,7 +1149,10 @@ const void* persistent_kernel(int kind, int part) {
   (part == kPartMetropolis   ? reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis>) \
    : part == kPartOverrelax ? reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax>) \
                             : reinterpret_cast<const void*>(k_persistent<K, kPartFinish>))
-  return kind == kTileBlock ? XY_PK(kTileBlock) : kind == kTileDirect ? XY_PK(kTileDirect) : XY_PK(kTileMarch);
+  return kind == kTileBlock    ? XY_PK(kTileBlock)
+         : kind == kTileDirect ? XY_PK(kTileDirect)
+         : kind == kTileAngle  ? XY_PK(kTileAngle)
+                               : XY_PK(kTileMarch);
 #undef XY_PK
 }
 
@@ -1350,6 +1396,24 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
   XY_TRY(c, cudaEventCreate(&e1));
   int rc = XY_OK;
   const bool persistent = exec == XY_EXEC_PERSISTENT;
+  // Angle storage (kTileAngle) is a candidate only when the context's
+  // vector state does not fit in L2: there the half-sweeps are bound by HBM
+  // bytes, which it halves; an L2-resident state keeps its vectors.
+  int l2 = 0;
+  XY_TRY(c, cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device));
+  const bool allow_angle = spin_bytes > static_cast<size_t>(l2);
+  const int kind_end = allow_angle ? kTileAngle + 1 : kTileAngle;
+  // The storage each lattice's state is in now (trial sweeps of a kind run
+  // on its storage; the saved state is in the storage of the starting kind).
+  std::vector<char> stored_ang(c->n_lat), start_ang(c->n_lat);
+  for (int i = 0; i < c->n_lat; ++i) stored_ang[i] = start_ang[i] = angle_storage(c->lat[i].kind) ? 1 : 0;
+  auto ensure_storage = [&](int i, int kind) {
+    const char want = angle_storage(kind) ? 1 : 0;
+    if (rc == XY_OK && stored_ang[i] != want) {
+      rc = convert_storage(c, i, want != 0);
+      stored_ang[i] = want;
+    }
+  };
   // Fastest tile of lattice i among kinds [k0, k1) and blocks of at most
   // max_threads threads, timed on half-sweep launches.
   auto search = [&](int i, int k0, int k1, int max_threads) {
@@ -1370,6 +1434,8 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
           if (kind != kTileBlock && tz < 2) continue;  // a march covers two planes or more
           if (cand.threads() > std::min(max_threads, kind_max_threads(c, kind)) || cand.threads() < 32) continue;
           if (cand.nyt() * cand.nzt() > h.part_cap || cand.smem() > 200 * 1024) continue;
+          ensure_storage(i, kind);
+          if (rc != XY_OK) break;
           h = cand;
           if ((rc = sync_lats(c)) != XY_OK) break;
           auto run = [&](int reps) {
@@ -1407,26 +1473,29 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
     h = best_h;
   };
   if (!persistent) {
-    for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, 0, 4, c->max_block);
+    for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, 0, kind_end, c->max_block);
   } else {
     // One tile kind and one block size serve every lattice of a persistent
-    // launch (the block is as wide as the widest tile): for each kind and
-    // each cap on the tile's threads (64, 128, 256), take each lattice's
-    // best tile under the cap, then time the persistent launch itself with
-    // each set and keep the fastest.
-    constexpr int kSets = 9;
-    std::vector<LatHost> sets[kSets];
+    // launch (the block is as wide as the widest tile): for each kind (not
+    // the stream kind) and each cap on the tile's threads (64, 128, 256),
+    // take each lattice's best tile under the cap, then time the persistent
+    // launch itself with each set and keep the fastest.
+    const int kinds[4] = {kTileMarch, kTileBlock, kTileDirect, kTileAngle};
+    const int n_sets = 3 * (allow_angle ? 4 : 3);
+    std::vector<std::vector<LatHost>> sets(n_sets);
     const std::vector<LatHost> start = c->lat;
-    for (int q = 0; q < kSets && rc == XY_OK; ++q) {
-      const int kind = q < 3 ? kTileMarch : (q < 6 ? kTileBlock : kTileDirect), cap = 64 << (q % 3);
+    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
+      const int kind = kinds[q / 3], cap = 64 << (q % 3);
       c->lat = start;
       for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, kind, kind + 1, cap);
       sets[q] = c->lat;
     }
     float best = 1e30f;
-    int best_q = kSets - 1;
-    for (int q = 0; q < kSets && rc == XY_OK; ++q) {
+    int best_q = n_sets - 1;
+    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
       c->lat = sets[q];
+      for (int i = 0; i < c->n_lat; ++i) ensure_storage(i, c->lat[i].kind);
+      if (rc != XY_OK) break;
       drop_graphs(c);
       if ((rc = sync_lats(c)) != XY_OK) break;
       if (persistent_sweeps(c, nM, nOR, 1, 0, 0) != XY_OK) {  // a set the persistent kernel cannot run
@@ -1456,6 +1525,12 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
   XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.spins, saved.data(), spin_bytes, cudaMemcpyHostToDevice, c->stream));
   XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.ctr, ctr.data(), ctr.size(), cudaMemcpyHostToDevice, c->stream));
   XY_TRY(c, cudaMemcpyAsync(c->ws + c->lay.acc_met, acc.data(), acc.size(), cudaMemcpyHostToDevice, c->stream));
+  // the restored state is in each lattice's starting storage
+  for (int i = 0; i < c->n_lat; ++i)
+    if ((angle_storage(c->lat[i].kind) ? 1 : 0) != start_ang[i]) {
+      rc = convert_storage(c, i, start_ang[i] == 0);
+      if (rc != XY_OK) return rc;
+    }
   XY_TRY(c, cudaStreamSynchronize(c->stream));
   std::memcpy(c->h_ctr, h_ctr, sizeof h_ctr);
   drop_graphs(c);

@@ -121,8 +121,8 @@ __host__ __device__ inline unsigned long long persistent_barriers(int part, int 
 
 // Every lattice of a persistent launch uses tile kind KIND, with blocks of
 // at most 256 threads, and each part's kernel is compiled for the blocks per
-// SM its kind keeps: the block kind three (at most 80 registers), the march
-// and the direct kinds two (at most 128).  The direct kind's other-colour
+// SM its kind keeps: the block kind three (at most 80 registers), the march,
+// the direct and the angle kinds two (at most 128).  The direct kind's other-colour
 // loads go through L1: a half-sweep starts after the launch boundary or a
 // grid barrier whose acquire (by one thread, then the block barrier) orders
 // the block's later loads after every block's writes of the previous
@@ -178,6 +178,8 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
       } else if (KIND == kTileDirect) {
         // threads beyond the tile's rows return at once
         tile_direct<MODE, MEAS>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc);
+      } else if (KIND == kTileAngle) {
+        tile_angle<MODE, MEAS>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc);
       } else {
         tile_pass<MODE, MEAS>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc);
       }

@@ -70,7 +70,15 @@ enum Mode : int { kMetropolis = 0, kOverrelax = 1, kMeasureOnly = 2 };
 // every warp marches on its own.  In the persistent kernel the grid
 // barrier between half-sweeps (an acquire, then the block barrier) orders
 // these loads after the previous half-sweep's writes.
-enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2, kTileDirect = 3 };
+// kTileAngle: the direct tile on a lattice stored as FP32 angles instead of
+// vectors (4 instead of 8 bytes per spin, for lattices that do not fit in
+// L2, where the half-sweep is bound by HBM bytes): every angle read is
+// turned into its vector with the fast sincos, and the update stores the
+// new angle (the proposal's, or atan2 of the reflected vector).
+enum TileKind : int { kTileMarch = 0, kTileBlock = 1, kTileStream = 2, kTileDirect = 3, kTileAngle = 4 };
+
+// Whether a tile kind keeps the lattice as angles (else as vectors).
+__host__ __device__ inline bool angle_storage(int kind) { return kind == kTileAngle; }
 
 // Threads of a kTileDirect block at most, and the registers a thread of its
 // kernel may use.  Each of an SM's four schedulers holds 16K registers, so
@@ -157,12 +165,13 @@ __host__ __device__ inline int tile_threads(int kind, int L, int ty, int tz) {
          : kind == kTileStream ? 32 * (stream_compute_warps(L, ty) + 1)
                                : (L / 8) * ty;
 }
-// kTileDirect keeps no tile in shared memory (only the reduction area).
+// kTileDirect and kTileAngle keep no tile in shared memory (only the
+// reduction area).
 __host__ __device__ inline int tile_floats(int kind, int L, int ty, int tz) {
-  return kind == kTileBlock    ? block_tile_floats(L, ty, tz)
-         : kind == kTileStream ? stream_tile_floats(L, ty)
-         : kind == kTileDirect ? 0
-                               : tile_plane_floats(L, ty);
+  return kind == kTileBlock                            ? block_tile_floats(L, ty, tz)
+         : kind == kTileStream                         ? stream_tile_floats(L, ty)
+         : (kind == kTileDirect || kind == kTileAngle) ? 0
+                                                       : tile_plane_floats(L, ty);
 }
 __host__ __device__ inline int tile_bytes(int kind, int L, int ty, int tz) {
   return tile_floats(kind, L, ty, tz) * 4 + kReduceBytes;
@@ -198,6 +207,24 @@ __device__ __forceinline__ float accept_threshold(float x) { return __expf(x) * 
 struct Spins4 {
   float4 c, s;
 };
+
+// An angle in [0, 2 pi) from atan2's (-pi, pi]; a value that rounds to 2 pi
+// is 0.
+__device__ __forceinline__ float wrap_angle(float t) {
+  t = t < 0.f ? t + kTwoPi : t;
+  return t >= kTwoPi ? 0.f : t;
+}
+
+// The vectors of four stored angles (kTileAngle), with the fast sincos of
+// spin() (the stored angles lie in [0, 2 pi)).
+__device__ __forceinline__ Spins4 spins_of_angles(const float4& a) {
+  Spins4 v;
+  spin(a.x, v.c.x, v.s.x);
+  spin(a.y, v.c.y, v.s.y);
+  spin(a.z, v.c.z, v.s.z);
+  spin(a.w, v.c.w, v.s.w);
+  return v;
+}
 
 // Bounds of the spin accesses of one tile pass: the slot's 2N floats.  In a
 // build with XY_BOUNDS_CHECK defined (the debug library, in place of
@@ -344,12 +371,17 @@ __device__ __forceinline__ void reflect2(float2 hx, float2 hy, float2 c, float2 
 // other colour's float4s of rows y-1, y+1 and planes z-1, z+1 at the same k;
 // o: the own spins.  w0, w1: the Philox words of sites (0, 1) and (2, 3)
 // (Metropolis).  Returns the new spins; accumulates the accepted proposals
-// and, when measuring, this plane's lattice-sum terms (stepv).
-template <int MODE, bool MEAS>
+// and, when measuring, this plane's lattice-sum terms (stepv).  ANG (angle
+// storage): *oa holds the own angles, and *na receives the new angles: the
+// proposal's where accepted, atan2 of the reflected vector where reflected,
+// the old angle elsewhere (also where the field is zero); the new spins n
+// are then the vectors of those angles when measuring.
+template <int MODE, bool MEAS, bool ANG = false>
 __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int s, const Spins4& ym,
                                         const Spins4& yp, const Spins4& zm, const Spins4& zp, const Spins4& o,
                                         const uint4& w0, const uint4& w1, float beta, Spins4& n, uint32_t& n_acc,
-                                        float* stepv) {
+                                        float* stepv, const float4* oa = nullptr, float4* na = nullptr) {
+  float2 nang[2];
   float Xc[5], Xs[5];
 #pragma unroll
   for (int e = 0; e < 5; ++e) {
@@ -391,15 +423,32 @@ __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int
       n_acc += (a0 ? 1u : 0u) + (a1 ? 1u : 0u);
       nc[q] = make_float2(a0 ? cp.x : co.x, a1 ? cp.y : co.y);
       ns[q] = make_float2(a0 ? sp.x : so.x, a1 ? sp.y : so.y);
+      if (ANG) {
+        const float2 ta = q ? make_float2(oa->z, oa->w) : make_float2(oa->x, oa->y);
+        nang[q] = make_float2(a0 ? tp.x : ta.x, a1 ? tp.y : ta.y);
+      }
     } else if (MODE == kOverrelax) {
       reflect2(hx[q], hy[q], co, so, nc[q], ns[q]);
+      if (ANG) {
+        const float2 ta = q ? make_float2(oa->z, oa->w) : make_float2(oa->x, oa->y);
+        const float2 n2 = __ffma2_rn(hy[q], hy[q], __fmul2_rn(hx[q], hx[q]));
+        nang[q] = make_float2(n2.x > 0.f ? wrap_angle(atan2f(ns[q].x, nc[q].x)) : ta.x,
+                              n2.y > 0.f ? wrap_angle(atan2f(ns[q].y, nc[q].y)) : ta.y);
+      }
     } else {
       nc[q] = co;
       ns[q] = so;
+      if (ANG) nang[q] = q ? make_float2(oa->z, oa->w) : make_float2(oa->x, oa->y);
     }
   }
   n.c = make_float4(nc[0].x, nc[0].y, nc[1].x, nc[1].y);
   n.s = make_float4(ns[0].x, ns[0].y, ns[1].x, ns[1].y);
+  if (ANG) {
+    *na = make_float4(nang[0].x, nang[0].y, nang[1].x, nang[1].y);
+    // the sums measure the stored state: the vectors of the stored angles,
+    // as a later measure-only pass forms them
+    if (MEAS) n = spins_of_angles(*na);
+  }
   if (MEAS) {
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
@@ -701,6 +750,144 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
     step(P1, P2, P3, P0, A, B, i + 2);
     if (i + 3 >= TZa) break;
     step(P2, P3, P0, P1, B, A, i + 3);
+  }
+  if (MEAS) sums.export_to(acc_out);
+}
+
+// Four stored angles (kTileAngle): through L2 (own colour) or L1 (other
+// colour, as the direct tile's vectors).
+__device__ __forceinline__ float4 ld_ang(const SpinGuard& g, const float* p) {
+  return g.ok(p, 4) ? ld4(p) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ float4 ld_ang_l1(const SpinGuard& g, const float* p) {
+  return g.ok(p, 4) ? __ldca(reinterpret_cast<const float4*>(p)) : make_float4(0.f, 0.f, 0.f, 0.f);
+}
+__device__ __forceinline__ void st_ang(const SpinGuard& g, float* p, const float4& v) {
+  if (g.ok(p, 4)) st4(p, v);
+}
+
+// One tile of one half-sweep, kTileAngle: tile_direct's thread layout, plane
+// march and loads on a lattice stored as angles, each colour's N/2 FP32
+// angles at the places of its cosines (the sine places are unused), so a
+// half-sweep moves 12 bytes per update instead of 24.  Every angle is turned
+// into its vector one plane after its load (when its value is needed; the
+// column's planes once, for their three uses) by the fast sincos, and the
+// update (update4, the same arithmetic as every tile kind on those vectors)
+// stores the new angle: the proposal's where a Metropolis move is accepted,
+// atan2 of the reflected vector of Eq. (2) where the field is non-zero, the
+// old angle otherwise.  The spins therefore differ from the vector kinds'
+// by the fast sincos of the neighbours (a few 1e-7 per vector) instead of
+// their stored rounding.  Arguments as tile_direct.
+template <int MODE, bool MEAS, int LC = 0>
+__device__ __forceinline__ void tile_angle(const Lattice& lat, int r, int yt, int zt, int colour, int tx, int ty,
+                                           const PassParams& pp, float* acc_out, uint32_t& n_acc) {
+  static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
+  static_assert(LC % 8 == 0, "L % 8 == 0");
+  const int L = LC ? LC : lat.L;
+  const int H = L >> 1;
+  const uint32_t PS = static_cast<uint32_t>(H) * static_cast<uint32_t>(L);  // plane stride
+  const uint32_t half = PS * static_cast<uint32_t>(L);                       // N / 2
+  const int y0 = yt * lat.ty, z0 = zt * lat.tz;
+  const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
+  if (ty >= TYa) return;
+  const int y = y0 + ty;
+  float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
+  const SpinGuard sg = spin_guard(slot, 4 * static_cast<size_t>(half), pp.status);
+  float* const own = slot + colour * (2 * half);  // angles where the cosines of the vector layout are
+  const float* const oth = slot + (colour ^ 1) * (2 * half);
+  const int ym = (y == 0 ? L : y) - 1;
+  const int yp = (y + 1 == L) ? 0 : y + 1;
+  const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
+  const uint32_t offym = static_cast<uint32_t>(H * ym + 4 * tx);
+  const uint32_t offyp = static_cast<uint32_t>(H * yp + 4 * tx);
+  const uint32_t offh0 = static_cast<uint32_t>(H * y + ((tx == 0) ? H - 1 : 4 * tx - 1));
+  const uint32_t offh1 = static_cast<uint32_t>(H * y + ((4 * tx + 4 == H) ? 0 : 4 * tx + 4));
+
+  uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
+  if (MODE == kMetropolis) {
+    tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) | kTagMet;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    mlo = static_cast<uint32_t>(mp);
+    mhi = static_cast<uint32_t>(mp >> 32);
+  }
+  SumAcc<MEAS> sums;
+
+  // Registers: the vectors of the column's other-colour planes z-1, z, z+1
+  // rotate through four slots (plane z+1's vector is formed at the step that
+  // first uses it); two sets of this plane's and the next plane's operands
+  // alternate, held as angles (half the registers of vectors) with the next
+  // column plane's angles and the Metropolis words.
+  struct Operands {
+    float4 own, ym, yp, zn;  // angles: own sites; other colour rows y-1, y+1; column plane z+1
+    float h;                 // the other colour's x-halo angle
+    uint4 w0, w1;            // Metropolis words of sites (0, 1) and (2, 3)
+  };
+  Spins4 P0, P1, P2, P3{};
+  Operands A, B;
+  auto load_own = [&](Operands& o, uint32_t pz) {
+    o.own = ld_ang(sg, own + offy + pz);
+    if (MODE == kMetropolis) {
+      const uint32_t q0 = (offy + pz) >> 1;
+      o.w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+      o.w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+    } else {
+      o.w0 = o.w1 = make_uint4(0u, 0u, 0u, 0u);
+    }
+  };
+  auto load_other = [&](Operands& o, int z, uint32_t pz) {
+    o.ym = ld_ang_l1(sg, oth + offym + pz);
+    o.yp = ld_ang_l1(sg, oth + offyp + pz);
+    o.h = ld1_l1(sg, oth + (((y + z + colour) & 1) ? offh1 : offh0) + pz);
+  };
+  float beta = 0.f;
+  {
+    const uint32_t zz = static_cast<uint32_t>(z0) * PS;
+    // the own colour before griddepcontrol.wait in library-chained launches,
+    // as in tile_direct (other launches waited on entry)
+    load_own(A, zz);
+    if (pp.own_ready) chain_wait_and_release();
+    if (MODE == kMetropolis) beta = __ldcg(pp.beta_slot + lat.slot0 + r);
+    P3 = spins_of_angles(ld_ang_l1(sg, oth + offy + static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS));
+    P0 = spins_of_angles(ld_ang_l1(sg, oth + offy + zz));
+    A.zn = ld_ang_l1(sg, oth + offy + static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS);
+    load_other(A, z0, zz);
+  }
+
+  // One plane: zm, zc = the vectors of planes z-1, z; zn receives plane
+  // z+1's (from cur.zn); cur holds this plane's operands, nxt receives the
+  // next plane's (with plane z+2's column angles).
+  auto step = [&](Spins4& zm, Spins4& zc, Spins4& zn, Operands& cur, Operands& nxt, int i) {
+    const int z = z0 + i;
+    if (i + 1 < TZa) {
+      nxt.zn = ld_ang_l1(sg, oth + offy + static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS);
+      load_own(nxt, static_cast<uint32_t>(z + 1) * PS);
+      load_other(nxt, z + 1, static_cast<uint32_t>(z + 1) * PS);
+    }
+    zn = spins_of_angles(cur.zn);
+    const Spins4 vo = spins_of_angles(cur.own), vym = spins_of_angles(cur.ym), vyp = spins_of_angles(cur.yp);
+    float hc, hs;
+    spin(cur.h, hc, hs);
+    const int s = (y + z + colour) & 1;
+    const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
+    float stepv[kNumSums];
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
+    Spins4 nw;
+    float4 na;
+    update4<MODE, MEAS, true>(zc, hc, hs, s, vym, vyp, zm, zn, vo, cur.w0, cur.w1, beta, nw, n_acc, stepv,
+                              &cur.own, &na);
+    if (MEAS) sums.add_plane(stepv);
+    if (MODE != kMeasureOnly) st_ang(sg, own + offz, na);
+  };
+
+  for (int i = 0; i < TZa; i += 4) {
+    step(P3, P0, P1, A, B, i);
+    if (i + 1 >= TZa) break;
+    step(P0, P1, P2, B, A, i + 1);
+    if (i + 2 >= TZa) break;
+    step(P1, P2, P3, A, B, i + 2);
+    if (i + 3 >= TZa) break;
+    step(P2, P3, P0, B, A, i + 3);
   }
   if (MEAS) sums.export_to(acc_out);
 }

@@ -25,7 +25,7 @@ CHECK_LIB_PATH = os.path.join(_HERE, "libxy_check.so")
 XY_OK, XY_ERR_ARG, XY_ERR_CUDA, XY_ERR_TIMEOUT, XY_ERR_STATE, XY_ERR_NOMEM, XY_ERR_BOUNDS = 0, -1, -2, -3, -4, -5, -6
 EXEC_PLAIN, EXEC_GRAPH, EXEC_PERSISTENT = 0, 1, 2
 TAG_INIT, TAG_MET, TAG_PT = 1, 2, 3
-TILE_MARCH, TILE_BLOCK, TILE_STREAM, TILE_DIRECT = 0, 1, 2, 3
+TILE_MARCH, TILE_BLOCK, TILE_STREAM, TILE_DIRECT, TILE_ANGLE = 0, 1, 2, 3, 4
 
 
 class XYError(RuntimeError):

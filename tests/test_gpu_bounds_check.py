@@ -25,7 +25,8 @@ out = {}
 cases = [([16], [2], [(4, 8, 0)]), ([24], [1], [(5, 7, 1)]), ([40], [1], [(3, 16, 2)]),
          ([24], [2], [(5, 7, 3)]), ([64], [2], [(8, 8, 3)]), ([8], [1], [(1, 8, 3)]),
          ([40], [1], [(40, 2, 3)]), ([80], [1], [(6, 9, 3)]), ([16, 24], [3, 2], [(4, 8, 3), (3, 5, 3)]),
-         ([16, 24], [3, 2], [(4, 8, 0), (3, 5, 0)])]
+         ([16, 24], [3, 2], [(4, 8, 0), (3, 5, 0)]), ([24], [2], [(5, 7, 4)]), ([40], [1], [(40, 2, 4)]),
+         ([16, 24], [3, 2], [(4, 8, 4), (3, 5, 4)])]
 for i, (Ls, Rs, tiles) in enumerate(cases):
     for mode in (xy.EXEC_PLAIN, xy.EXEC_GRAPH, xy.EXEC_PERSISTENT):
         if mode == xy.EXEC_PERSISTENT and any(t[2] == 2 for t in tiles):
