@@ -1143,12 +1143,13 @@ int xy_device_status(xy_ctx* c, int* status_out) {
 
 namespace {
 
-// The persistent kernel of one tile kind and sweep part.
-const void* persistent_kernel(int kind, int part) {
-#define XY_PK(K) \
-  (part == kPartMetropolis   ? reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis>) \
-   : part == kPartOverrelax ? reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax>) \
-                            : reinterpret_cast<const void*>(k_persistent<K, kPartFinish>))
+// The persistent kernel of one tile kind, sweep part and finishing flag.
+const void* persistent_kernel(int kind, int part, bool fin) {
+#define XY_PK(K)                                                                                        \
+  (part == kPartMetropolis ? (fin ? reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis, true>)  \
+                                  : reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis, false>)) \
+   : fin                   ? reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax, true>)        \
+                           : reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax, false>))
   return kind == kTileBlock    ? XY_PK(kTileBlock)
          : kind == kTileDirect ? XY_PK(kTileDirect)
          : kind == kTileAngle  ? XY_PK(kTileAngle)
@@ -1176,8 +1177,8 @@ int build_plan(xy_ctx* c) {
   // Every part's kernel runs on the same grid and item plan: the grid is
   // sized by the part that keeps the fewest blocks per SM.
   int nb = 1 << 30;
-  for (int part = kPartMetropolis; part <= kPartFinish; ++part) {
-    const void* fn = persistent_kernel(kind, part);
+  for (int v = 0; v < 4; ++v) {
+    const void* fn = persistent_kernel(kind, v >> 1, (v & 1) != 0);
     cudaFuncAttributes fa{};
     XY_TRY(c, cudaFuncGetAttributes(&fa, fn));
     if (B > fa.maxThreadsPerBlock) return XY_ERR_ARG;  // a tile wider than one persistent block
@@ -1225,7 +1226,7 @@ PersistentArgs persistent_args(xy_ctx* c) {
   a.items = c->at<int4>(c->lay.plan_items);
   a.n_items = c->plan.n_items;
   a.n_lat = c->n_lat;
-  a.n_pass = 0;
+  a.n_half = 0;
   a.mpass_off = 0;
   a.bar0 = 0;
   a.work0 = 0;
@@ -1236,7 +1237,7 @@ PersistentArgs persistent_args(xy_ctx* c) {
   return a;
 }
 
-cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, int part) {
+cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, int part, bool fin) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(c->plan.G);
   cfg.blockDim = dim3(c->plan.B);
@@ -1248,13 +1249,14 @@ cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& 
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   void* args[] = {const_cast<PersistentArgs*>(&a)};
-  return cudaLaunchKernelExC(&cfg, persistent_kernel(c->plan.kind, part), args);
+  return cudaLaunchKernelExC(&cfg, persistent_kernel(c->plan.kind, part, fin), args);
 }
 
 // Issues the persistent launches of `ns` sweeps starting at host sweep
-// index s0 on `st` -- the barrier reset, then per sweep the Metropolis part,
-// the over-relaxation part and (measured or exchanging sweeps) the finish
-// part -- followed by the counter advance.  No synchronisation.
+// index s0 on `st` -- the barrier reset, then per sweep the Metropolis part
+// and the over-relaxation part, the last of them finishing measured or
+// exchanging sweeps -- followed by the counter advance.  No
+// synchronisation.
 cudaError_t issue_persistent(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, int se, uint64_t s0,
                              const BlockCounts& bc) {
   PersistentArgs a = persistent_args(c);
@@ -1262,21 +1264,25 @@ cudaError_t issue_persistent(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns
   uint64_t n_rec = 0, n_swp = 0;
   for (int s = 0; s < ns && e == cudaSuccess; ++s) {
     const bool meas = due(s0 + s, me), swp = due(s0 + s, se);
-    for (int part = kPartMetropolis; part <= kPartFinish && e == cudaSuccess; ++part) {
-      const int n_pass = part == kPartMetropolis ? nM : (part == kPartOverrelax ? nOR : 0);
-      if (part == kPartFinish ? !(meas || swp) : n_pass == 0) continue;
-      a.n_pass = n_pass;
-      a.mpass_off = static_cast<uint64_t>(s) * nM;
+    for (int part = kPartMetropolis; part <= kPartOverrelax && e == cudaSuccess; ++part) {
+      const int n_pass = part == kPartMetropolis ? nM : nOR;
+      if (n_pass == 0) continue;
+      // the sweep's last part leaves its last half-sweep to the finishing launch
+      const bool finishes = (meas || swp) && (part == kPartOverrelax || nOR == 0);
       a.fp.sweep_off = s;
       a.fp.series_off = n_rec;
       a.fp.swap_off = n_swp;
       a.fp.record = meas ? 1 : 0;
       a.fp.swap = swp ? 1 : 0;
-      e = launch_persistent(c, st, a, part);
-      a.bar0 += persistent_barriers(part, n_pass, a.fp.swap);
-      // half-sweeps of this launch: 2 per pass, the finish part's measure pass
-      const unsigned long long halves = part == kPartFinish ? 1ull : 2ull * n_pass;
-      a.work0 += halves * (static_cast<unsigned long long>(c->plan.n_items) + c->plan.G);
+      for (int fin = 0; fin < (finishes ? 2 : 1) && e == cudaSuccess; ++fin) {
+        a.n_half = fin ? 1 : 2 * n_pass - (finishes ? 1 : 0);
+        if (a.n_half == 0) continue;
+        a.mpass_off = static_cast<uint64_t>(s) * nM + (fin ? n_pass - 1 : 0);
+        e = launch_persistent(c, st, a, part, fin != 0);
+        a.bar0 += persistent_barriers(a.n_half, fin != 0, swp);
+        a.work0 += static_cast<unsigned long long>(a.n_half) *
+                   (static_cast<unsigned long long>(c->plan.n_items) + c->plan.G);
+      }
     }
     n_rec += meas ? 1 : 0;
     n_swp += swp ? 1 : 0;
@@ -1348,7 +1354,8 @@ int xy_debug_barrier_timeout(xy_ctx* c, int budget_us, int* status_out) {
   a.budget_ns = static_cast<long long>(budget_us) * 1000;
   XY_TRY(c, cudaMemsetAsync(a.bar, 0, kBarBytes, c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));
-  XY_TRY(c, launch_persistent(c, c->stream, a, kPartOverrelax));
+  a.n_half = 1;
+  XY_TRY(c, launch_persistent(c, c->stream, a, kPartOverrelax, false));
   int st = 0;
   XY_TRY(c, cudaMemcpyAsync(&st, a.status, 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));

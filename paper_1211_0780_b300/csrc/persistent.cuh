@@ -1,9 +1,10 @@
 // Persistent batched sweep: cooperative launches that each advance every
 // replica of every lattice (uneven L included) through one part of a sweep
-// -- its Metropolis passes, its over-relaxation passes, or the fused
-// measurement with the on-device exchange of Sec. II, Eq. (3) -- so that each
-// part's kernel keeps its own register budget (one kernel holding every
-// variant needed 246 registers a thread for the direct tile, two warps per
+// -- its Metropolis passes, or its over-relaxation passes with, on measured
+// or exchanging sweeps, the fused measurement in the last white half-sweep
+// and the on-device exchange of Sec. II, Eq. (3) -- so that each part's
+// kernel keeps its own register budget (one kernel holding every variant
+// needed 246 registers a thread for the direct tile, two warps per
 // scheduler).  Each half-sweep is one list of tile work items (lattice,
 // slot, tile), sorted by the host by decreasing cost; the blocks take items
 // from the list in that order through one atomic counter, so the longest
@@ -39,18 +40,22 @@ constexpr int kBarStride = 16;  // 64-bit words between counters (128 bytes)
 // The work counter sits after the barrier's group and top counters.
 constexpr int kBarWords = (kBarGroups + 2) * kBarStride;
 
-// The part of a sweep one persistent launch runs.
-enum PersistentPart : int { kPartMetropolis = 0, kPartOverrelax = 1, kPartFinish = 2 };
+// The update passes one persistent launch runs.  The launch that ends a
+// measured or exchanging sweep (FIN) runs that sweep's last half-sweep (the
+// last pass's white sites) with the fused measurement, then the slots'
+// sums, records and exchange; the launch before it stops one half-sweep
+// short.
+enum PersistentPart : int { kPartMetropolis = 0, kPartOverrelax = 1 };
 
 struct PersistentArgs {
   PassParams pp;            // mpass_off and measure are set per pass
-  FinishParams fp;          // offsets, record and swap set by the host per sweep
+  FinishParams fp;          // offsets, record and swap set by the host per sweep (FIN)
   const Lattice* lats;
   const int4* items;        // (lattice, local slot, tile, unused), by decreasing cost
   int n_items;              // items of one half-sweep
   int n_lat;
-  int n_pass;               // kPartMetropolis / kPartOverrelax: passes of this launch
-  uint64_t mpass_off;       // kPartMetropolis: pass counter offset of its first pass
+  int n_half;               // half-sweeps of this launch (black, white, black, ...; FIN: 1, white)
+  uint64_t mpass_off;       // kPartMetropolis: pass counter offset of its first half-sweep's pass
   unsigned long long bar0;  // barrier instances completed before this launch
   unsigned long long work0; // work-counter value at this launch's first half-sweep
   unsigned long long* bar;  // kBarGroups group counters, the top counter, then
@@ -112,24 +117,25 @@ __device__ __forceinline__ bool grid_barrier(const PersistentArgs& a, unsigned l
   return ok != 0;
 }
 
-// Barrier instances one launch of `part` runs: one between consecutive
-// half-sweeps; the finish part, one before the slots' sums and one before
-// the exchange.
-__host__ __device__ inline unsigned long long persistent_barriers(int part, int n_pass, int swap) {
-  return part == kPartFinish ? (swap ? 2ull : 1ull) : (n_pass > 0 ? 2ull * n_pass - 1ull : 0ull);
+// Barrier instances one launch runs: one between consecutive half-sweeps,
+// and when finishing a sweep one before the slots' sums and one before the
+// exchange.
+__host__ __device__ inline unsigned long long persistent_barriers(int n_half, bool fin, bool swap) {
+  return static_cast<unsigned long long>(n_half) - 1ull + (fin ? (swap ? 2ull : 1ull) : 0ull);
 }
 
 // Every lattice of a persistent launch uses tile kind KIND, with blocks of
 // at most 256 threads, and each part's kernel is compiled for the blocks per
 // SM its kind keeps: the block kind three (at most 80 registers), the march,
-// the direct and the angle kinds two (at most 128).  The direct kind's other-colour
+// the direct and the angle kinds two (at most 128).  FIN: the launch ends a
+// measured or exchanging sweep.  The direct kind's other-colour
 // loads go through L1: a half-sweep starts after the launch boundary or a
 // grid barrier whose acquire (by one thread, then the block barrier) orders
 // the block's later loads after every block's writes of the previous
 // half-sweep, as the launch boundary does for the per-launch kernels.
 constexpr int kPersistentBlockThreads = 256;
 
-template <int KIND, int PART>
+template <int KIND, int PART, bool FIN>
 __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 3 : 2)
     k_persistent(PersistentArgs a) {
   extern __shared__ __align__(16) float sm[];
@@ -145,15 +151,12 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
   // advances the counter by exactly n_items + gridDim.x.
   unsigned long long base = a.work0;
   __shared__ int s_item;
-  // One pass of colour `colour` over this block's tile items.  The update
-  // passes never measure: the lattice sums of a measured sweep come from a
-  // measure-only pass after its last half-sweep, which forms the same
-  // per-thread sums in the same order as the per-launch path's fused pass
-  // (the white sites' stored spins are the updated ones), so the records
-  // are identical.
-  auto tile_items = [&](auto mode, int colour, const PassParams& pp) {
+  // One half-sweep of colour `colour` over the tile items the block takes.
+  // The measuring variant (the last white half-sweep of a finishing launch)
+  // is the per-launch path's fused pass, so the records are identical.
+  auto tile_items = [&](auto mode, auto meas, int colour, const PassParams& pp) {
     constexpr int MODE = decltype(mode)::value;
-    constexpr bool MEAS = MODE == kMeasureOnly;
+    constexpr bool MEAS = decltype(meas)::value != 0;
     for (;;) {
       if (tid == 0) {
         const unsigned long long t = atomicAdd(work, 1ull) - base;
@@ -192,26 +195,21 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
     }
     base += static_cast<unsigned long long>(a.n_items) + gridDim.x;
   };
-  if (PART != kPartFinish) {
-    for (int p = 0; p < a.n_pass; ++p) {
-      for (int colour = 0; colour < 2; ++colour) {
-        if (p > 0 || colour > 0)
-          if (!grid_barrier(a, nbar++)) return;
-        PassParams pp = a.pp;
-        pp.measure = 0;
-        if (PART == kPartMetropolis) {
-          pp.mpass_off = a.mpass_off + static_cast<uint64_t>(p);
-          tile_items(IC<kMetropolis>{}, colour, pp);
-        } else {
-          pp.mpass_off = 0ull;
-          tile_items(IC<kOverrelax>{}, colour, pp);
-        }
-      }
+  constexpr int MODE = PART == kPartMetropolis ? kMetropolis : kOverrelax;
+  if (!FIN) {
+    for (int h = 0; h < a.n_half; ++h) {
+      if (h > 0)
+        if (!grid_barrier(a, nbar++)) return;
+      PassParams pp = a.pp;
+      pp.mpass_off = PART == kPartMetropolis ? a.mpass_off + static_cast<uint64_t>(h >> 1) : 0ull;
+      pp.measure = 0;
+      tile_items(IC<MODE>{}, IC<0>{}, h & 1, pp);
     }
   } else {
     PassParams pp = a.pp;
+    pp.mpass_off = PART == kPartMetropolis ? a.mpass_off : 0ull;
     pp.measure = 1;
-    tile_items(IC<kMeasureOnly>{}, 1, pp);
+    tile_items(IC<MODE>{}, IC<1>{}, 1, pp);
     if (!grid_barrier(a, nbar++)) return;
     // every slot's sums and record on its own warp, spread over the grid,
     // then (after a barrier) each ladder's exchange on one block
