@@ -6,7 +6,8 @@ Creates one lattice (seeded hot start), runs a few warm-up sweeps, then
 issues `--launches` half-sweeps of the chosen kernel (or = over-relaxation,
 met = Metropolis, meas = measurement-only; sweep = 1 + 5 sweeps; pt = sweeps of
 1 + 3 passes with sums and an exchange, the ladder spaced on [0.450, 0.458])
-and synchronises; reweight =
+and synchronises (--exec picks plain launches, the CUDA graph or the persistent launches
+for the sweep and pt modes); reweight =
 `--launches` forward reweightings of one synthetic series of `--T` samples to
 `--K` couplings.  No autotuning,
 so the launch list is short and deterministic.
@@ -30,6 +31,8 @@ def main():
     ap.add_argument("--K", type=int, default=4096, help="couplings of the reweight mode")
     ap.add_argument("--launches", type=int, default=5)
     ap.add_argument("--warm-sweeps", type=int, default=2)
+    ap.add_argument("--exec", type=int, default=0,
+                    help="execution mode of the sweep and pt modes: 0 plain launches, 1 CUDA graph, 2 persistent")
     args = ap.parse_args()
     import torch
     from paper_1211_0780_b300 import xy
@@ -50,6 +53,7 @@ def main():
     if args.ty and args.tz:
         sim.set_tile(0, args.ty, args.tz, args.kind)
     sim.sweep(1, 1, args.warm_sweeps)
+    sim.set_exec(args.exec)
     for i in range(args.launches):
         if args.mode == "or":
             sim.overrelax_half(i & 1)
