@@ -31,6 +31,9 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "xy_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle.so")
+# A compiled copy of the oracle to load instead (the mutation tests point it
+# at copies with a planted mistake); it is used as it is, never rebuilt.
+_LIB_OVERRIDE = os.environ.get("XY_ORACLE_LIBRARY")
 
 TAG_INIT = 1
 TAG_MET = 2
@@ -43,6 +46,8 @@ _i32p = np.ctypeslib.ndpointer(dtype=np.int32, flags="C_CONTIGUOUS")
 
 def build(force: bool = False) -> str:
     """Compile ``xy_oracle.c`` into ``liboracle.so`` (gcc, -O2, OpenMP)."""
+    if _LIB_OVERRIDE:
+        return _LIB_OVERRIDE
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         cmd = ["gcc", "-O2", "-fopenmp", "-shared", "-fPIC", "-std=c99", "-o", _LIB, _SRC, "-lm"]
         subprocess.run(cmd, check=True)
