@@ -74,9 +74,12 @@ enum {
 enum {
   XY_EXEC_PLAIN = 0,      /* one kernel launch per half-sweep per lattice          */
   XY_EXEC_GRAPH = 1,      /* the same launches captured once into a CUDA graph     */
-  XY_EXEC_PERSISTENT = 2  /* one cooperative launch runs every pass of every
-                             lattice and replica, the measurement and the exchange;
-                             captured into a CUDA graph                            */
+  XY_EXEC_PERSISTENT = 2  /* cooperative launches, each running one part of a
+                             sweep (its Metropolis passes, its over-relaxation
+                             passes, the last half-sweep with the measurement and
+                             the exchange) for every lattice and replica, with
+                             bounded grid barriers between half-sweeps; one CUDA
+                             graph per xy_sweep call                                */
 };
 
 typedef struct xy_ctx xy_ctx; /* opaque; owned by the library */
