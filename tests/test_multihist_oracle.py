@@ -1,6 +1,7 @@
 """Pins of the multi-histogram oracle (CPU): reduction to single-histogram
 reweighting for one coupling, exact free energies and energies of a
-Gaussian density of states, and the energy-shift covariance."""
+Gaussian density of states (equal and unequal record counts), and the
+energy-shift covariance."""
 
 import numpy as np
 import pytest
@@ -55,3 +56,21 @@ def test_energy_shift():
     a = omh.averages(E, E[:, None], betas, [3000] * 3, f, bp)[0]
     b = omh.averages(E + 123.0, E[:, None], betas, [3000] * 3, g, bp)[0]
     np.testing.assert_allclose(b, a + 123.0, rtol=1e-12)
+
+
+def test_unequal_record_counts():
+    """Runs with 2,000 and 24,000 records alternating: the counts N_m weight
+    each run's histogram, so the exact free energies and energies of the
+    Gaussian density of states still come out (statistical)."""
+    betas = np.linspace(0.40, 0.50, 6)
+    E0, s = -2000.0, 30.0
+    ns = [2000, 24000] * 3
+    rng = np.random.default_rng(11)
+    E = np.concatenate([E0 - b * s * s + s * rng.standard_normal(n) for b, n in zip(betas, ns)])
+    f, _ = omh.solve(E, betas, ns, tol=1e-11)
+    lnZ = -betas * E0 + betas ** 2 * s * s / 2
+    np.testing.assert_allclose(f, -(lnZ - lnZ[0]), atol=0.05)
+    bp = np.linspace(0.41, 0.49, 9)
+    mE, _, cov = omh.averages(E, E[:, None], betas, ns, f, bp)
+    np.testing.assert_allclose(mE, E0 - bp * s * s, atol=0.05 * s)
+    np.testing.assert_allclose(cov[:, 0], s * s, rtol=0.05)
