@@ -9,8 +9,9 @@ measurement = 10 * 6 * 160^3 = 245,760,000 spin updates.  The lattice
 timed step, outside its CUDA-event bracket.
 
 Also reported (extra keys): the batched parallel-tempering workload (64^3 x
-32 replicas, 1 + 3 passes, exchange every sweep) in one persistent
-cooperative launch vs the plain per-replica launch loop, the ragged batch,
+32 replicas, 1 + 3 passes, exchange every sweep) batched into each
+half-sweep kernel (CUDA graph) and in the persistent launches vs the plain
+per-replica launch loop, the ragged batch,
 and reweighting throughput.
 
 --impl reference runs the FP64 CPU oracle (the reference arm of this build)
@@ -295,8 +296,8 @@ def time_kernel(fn, stream, n, warm=5):
 def bench_pt(steps: int, warmup: int):
     """64^3 x 32 replicas, beta in [0.450, 0.458], 1 + 3 passes, exchange and
     lattice sums every sweep, three ways: every replica batched into each
-    half-sweep kernel (CUDA graph), the persistent cooperative launch (one
-    launch per call, graph-captured), and the plain per-replica launch loop
+    half-sweep kernel (CUDA graph), the persistent launches (one per part
+    of a sweep, chained, graph-captured), and the plain per-replica launch loop
     (one context per replica, kernels issued replica by replica)."""
     import torch
     from paper_1211_0780_b300 import xy
@@ -340,8 +341,11 @@ RAGGED_L = (16, 24, 32, 48, 64, 96, 128)
 def bench_ragged(steps: int, warmup: int):
     """L in {16, 24, 32, 48, 64, 96, 128} x 16 replicas each (beta in
     [0.452, 0.456]), 1 Metropolis + 3 over-relaxation passes, exchange every
-    sweep and lattice sums every 10 sweeps, all lattices in one persistent
-    cooperative launch per call (218 MB of angles: HBM-resident)."""
+    sweep and lattice sums every 10 sweeps, all lattices in the persistent
+    launches and, with per-lattice tiles, as a CUDA graph (436 MB
+    of (cos, sin) state: HBM-resident).  Also the bandwidth each figure
+    implies against the measured HBM peak, on the metric's 12 B per update
+    and on the 24 B per update the vector layout moves."""
     import torch
     from paper_1211_0780_b300 import xy
     R, sweeps = 16, 10
@@ -367,6 +371,15 @@ def bench_ragged(steps: int, warmup: int):
             out[name] = upd / (ms * 1e6)
         except Exception as exc:
             out[name] = {"error": repr(exc)}
+    hbm, src = measured_peaks()
+    best = max((v for k, v in out.items() if k in ("persistent", "graph") and isinstance(v, float)), default=None)
+    if best is not None:
+        out["roofline"] = {"bound": "hbm", "unit": "GB/s", "peak": hbm, "peak_source": f"MEASURED_PEAKS.json ({src})",
+                           "achieved_12B": best * BYTES_PER_UPDATE, "frac_12B": best * BYTES_PER_UPDATE / hbm,
+                           "achieved_moved": best * 24, "frac_moved": best * 24 / hbm,
+                           "note": "best of the two figures; 24 B per update is what the (cos, sin) layout reads "
+                                   "and writes (the 128^3 half-sweeps read exactly 16 B per update from DRAM, "
+                                   "profiles/overrelax_L128x16_direct4x8_dram.md)"}
     return out
 
 

@@ -63,7 +63,7 @@ enum {
   XY_OK = 0,
   XY_ERR_ARG = -1,     /* invalid argument; nothing was done             */
   XY_ERR_CUDA = -2,    /* a CUDA call failed; the context is now unusable */
-  XY_ERR_TIMEOUT = -3, /* a bounded device-side wait ran out (grid barrier) */
+  XY_ERR_TIMEOUT = -3, /* a bounded device-side wait ran out               */
   XY_ERR_STATE = -4,   /* the context is in a sticky error state          */
   XY_ERR_NOMEM = -5,   /* workspace or series buffer too small            */
   XY_ERR_BOUNDS = -6   /* bounds-checked build (XY_BOUNDS_CHECK, libxy_check)
@@ -74,12 +74,15 @@ enum {
 enum {
   XY_EXEC_PLAIN = 0,      /* one kernel launch per half-sweep per lattice          */
   XY_EXEC_GRAPH = 1,      /* the same launches captured once into a CUDA graph     */
-  XY_EXEC_PERSISTENT = 2  /* cooperative launches, each running one part of a
+  XY_EXEC_PERSISTENT = 2  /* persistent launches, each running one part of a
                              sweep (its Metropolis passes, its over-relaxation
                              passes, the last half-sweep with the measurement and
-                             the exchange) for every lattice and replica, with
-                             bounded grid barriers between half-sweeps; one CUDA
-                             graph per xy_sweep call                                */
+                             the exchange) for every lattice and replica as one
+                             list of tile items; no grid barrier: an item waits
+                             (bounded) only for its own slot's previous work,
+                             counted per slot; the launches are chained by
+                             programmatic dependent launch; one CUDA graph per
+                             xy_sweep call                                          */
 };
 
 typedef struct xy_ctx xy_ctx; /* opaque; owned by the library */
@@ -297,8 +300,8 @@ int xy_debug_fast_math(int kind, int64_t n, const void *d_in, float *d_out,
  * march's thread layout and plane march without shared memory or block
  * barriers: each thread loads its y-neighbour rows and x-halo element
  * itself through the L1 cache, one plane ahead (in XY_EXEC_PERSISTENT the
- * grid barrier between half-sweeps orders those loads after the previous
- * half-sweep's writes).  kind 4 (angle): the direct tile on a lattice kept
+ * acquire of the slot's count before each tile orders those loads after
+ * the previous half-sweep's writes).  kind 4 (angle): the direct tile on a lattice kept
  * as FP32 angles in [0, 2 pi) instead of vectors (4 instead of 8 bytes per
  * spin; each colour's angles sit where its cosines are in the vector
  * layout): every angle read is turned into its vector by the fast sincos
@@ -332,11 +335,12 @@ int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
 /* Device-side status word of the last persistent launch (0 = fine). */
 int xy_device_status(xy_ctx *ctx, int *status_out);
 
-/* Test hook for the bounded grid barrier: runs one persistent launch whose
- * barrier expects one more block than the grid has, so every wait runs out
- * after `budget_us` microseconds and the kernel returns XY_ERR_TIMEOUT
- * through the status word without hanging.  The context stays usable (the
- * timeout is reported, not made sticky).  No GPU fault is involved. */
+/* Test hook for the bounded waits of XY_EXEC_PERSISTENT: runs one
+ * persistent launch whose blocks each wait for a slot count that nothing
+ * raises, so every wait runs out after `budget_us` microseconds and the
+ * kernel returns XY_ERR_TIMEOUT through the status word without hanging.
+ * The context stays usable (the timeout is reported, not made sticky).  No
+ * GPU fault is involved. */
 int xy_debug_barrier_timeout(xy_ctx *ctx, int budget_us, int *status_out);
 
 /* Test hook for the bounded plane waits of stream tiles (kind 2): lattice 0

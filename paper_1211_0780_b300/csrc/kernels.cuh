@@ -294,14 +294,12 @@ __device__ void exchange_ladder(const Lattice& lat, int l, const FinishParams& f
   if (fp.n_swapped && count) atomicAdd(fp.n_swapped, count);
 }
 
-// Per-launch finishing step: one warp (block of 32 threads) per slot of
-// every lattice, so the FP64 sums of all slots run on as many SMs.  A
-// lattice's slots are counted on fp.done[l] as they finish (after a fence);
-// the warp that finishes the last one runs the lattice's exchange and resets
-// the count.  No warp waits for another.
-__global__ void k_finish(const Lattice* lats, int n_lat, FinishParams fp) {
-  chain_wait_and_release();
-  const int g = blockIdx.x, lane = threadIdx.x & 31;
+// Finishing step of slot g, by one warp: its sums and record; on an
+// exchanging sweep a lattice's slots are counted on fp.done[l] as they
+// finish (after a fence), and the warp that finishes the last one runs the
+// lattice's exchange and resets the count.  No warp waits for another.
+__device__ __forceinline__ void finish_slot_and_exchange(const Lattice* lats, int n_lat, const FinishParams& fp,
+                                                         int g, int lane) {
   int lo = 0, hi = n_lat - 1;  // the lattice of slot g: the last with slot0 <= g
   while (lo < hi) {
     const int mid = (lo + hi + 1) >> 1;
@@ -319,6 +317,13 @@ __global__ void k_finish(const Lattice* lats, int n_lat, FinishParams fp) {
   __threadfence();
   exchange_ladder(lat, lo, fp, lane, 32);
   if (lane == 0) fp.done[lo] = 0;
+}
+
+// Per-launch finishing step: one warp (block of 32 threads) per slot of
+// every lattice, so the FP64 sums of all slots run on as many SMs.
+__global__ void k_finish(const Lattice* lats, int n_lat, FinishParams fp) {
+  chain_wait_and_release();
+  finish_slot_and_exchange(lats, n_lat, fp, blockIdx.x, threadIdx.x & 31);
 }
 
 __global__ void k_advance(uint64_t* ctr, uint64_t d_mpass, uint64_t d_sweep, uint64_t d_swap,

@@ -2,7 +2,8 @@
 //
 // Host-side responsibilities: validate arguments, carve the caller's device
 // workspace, issue the half-sweep kernels in the sweep schedule (plain
-// launches, a captured CUDA graph, or one persistent cooperative launch),
+// launches, a captured CUDA graph, or persistent launches, one per part of
+// a sweep),
 // keep host mirrors of the device counters, and marshal state between the
 // natural host layout and the packed device layout.
 #include <cuda_runtime.h>
@@ -48,11 +49,12 @@ int part_cap_for(int L) { return std::max(1, (L * L) / 4); }
 
 struct Layout {
   size_t spins, ladder_beta, perm, beta_slot, beta_slot64, bidx_slot, E_slot, sums_slot, partials,
-      acc_met, acc_swap, ctr, status, barrier, nswapped, fin_done, lats, staging, plan_items, series, total;
+      acc_met, acc_swap, ctr, status, sync, nswapped, fin_done, lats, staging, plan_items, series, total;
 };
 
 constexpr int kMaxPlanBlocks = 8192;
-constexpr size_t kBarBytes = static_cast<size_t>(kBarWords) * 8;
+// The persistent launches' item counter and per-slot completion counts.
+size_t sync_bytes(long long slots) { return static_cast<size_t>(kSyncSlot0 + slots) * 8; }
 
 bool valid_lattices(int n, const int* L, const int* R) {
   if (n <= 0 || n > 4096 || !L || !R) return false;
@@ -92,7 +94,7 @@ Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
   o.acc_swap = take(slots * 8);
   o.ctr = take(kNumCounters * 8);
   o.status = take(64);
-  o.barrier = take(kBarBytes);
+  o.sync = take(sync_bytes(slots));
   o.nswapped = take(64);
   o.fin_done = take(static_cast<size_t>(n) * 4);
   o.lats = take(static_cast<size_t>(n) * sizeof(Lattice));
@@ -104,6 +106,13 @@ Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
 }
 
 int lcm_int(int a, int b) { return a / std::gcd(a, b) * b; }
+
+// The period after which the pattern of measured and exchanging sweeps
+// repeats: lcm(me, se) of the periods that are set (1 if neither is).
+uint64_t sweep_period(int me, int se) {
+  const uint64_t a = me > 0 ? static_cast<uint64_t>(me) : 1u, b = se > 0 ? static_cast<uint64_t>(se) : 1u;
+  return a / std::gcd(a, b) * b;
+}
 
 }  // namespace
 
@@ -129,7 +138,7 @@ struct xy_ctx {
   uint64_t h_ctr[kNumCounters] = {0};
   int exec = XY_EXEC_PLAIN;
   int sticky = XY_OK;
-  std::map<std::tuple<int, int, int, int, int, int, int>, cudaGraphExec_t> graphs;
+  std::map<std::tuple<int, int, int, int, int, long long, int>, cudaGraphExec_t> graphs;
   struct Plan {
     int G = 0, B = 0, smem = 0, kind = 0, n_items = 0;
     bool graph_ok = true;
@@ -214,7 +223,7 @@ struct NvtxRange {
 
 // Synchronises the context's stream and reads the device status word: a
 // bounded wait that ran out inside a kernel (a stream tile waiting for a
-// copied plane, the persistent grid barrier) fails the context with
+// copied plane, a persistent launch's wait for a slot's tiles) fails the context with
 // XY_ERR_TIMEOUT.
 int sync_checked(xy_ctx* c) {
   int st = 0;
@@ -470,7 +479,7 @@ uint64_t count_due(uint64_t s0, uint64_t n, int every) {
 }
 
 int run_graph_block(xy_ctx* c, int nM, int nOR, int me, int se, int P, uint64_t s0) {
-  const auto key = std::make_tuple(nM, nOR, me, se, P, static_cast<int>(s0 % P), 0);
+  const auto key = std::make_tuple(nM, nOR, me, se, P, static_cast<long long>(s0 % P), 0);
   auto it = c->graphs.find(key);
   if (it == c->graphs.end()) {
     XY_TRY(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1226,42 +1235,49 @@ PersistentArgs persistent_args(xy_ctx* c) {
   a.items = c->at<int4>(c->lay.plan_items);
   a.n_items = c->plan.n_items;
   a.n_lat = c->n_lat;
-  a.n_half = 0;
-  a.mpass_off = 0;
-  a.bar0 = 0;
-  a.work0 = 0;
-  a.bar = c->at<unsigned long long>(c->lay.barrier);
+  unsigned long long* sync = c->at<unsigned long long>(c->lay.sync);
+  a.work = sync;
+  a.cnt = sync + kSyncSlot0;
   a.status = c->at<int>(c->lay.status);
   a.budget_ns = 2000000000ll;
   a.poison = 0;
   return a;
 }
 
-cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, int part, bool fin) {
+// One persistent launch; `chained`: programmatic dependent launch after the
+// previous persistent launch of the same call (its blocks start as the
+// previous launch's blocks leave; the slot counts order the work).
+cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, int part, bool fin,
+                              bool chained) {
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(c->plan.G);
   cfg.blockDim = dim3(c->plan.B);
   cfg.dynamicSmemBytes = c->plan.smem;
   cfg.stream = st;
   cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = chained ? 1 : 0;
   void* args[] = {const_cast<PersistentArgs*>(&a)};
   return cudaLaunchKernelExC(&cfg, persistent_kernel(c->plan.kind, part, fin), args);
 }
 
 // Issues the persistent launches of `ns` sweeps starting at host sweep
-// index s0 on `st` -- the barrier reset, then per sweep the Metropolis part
-// and the over-relaxation part, the last of them finishing measured or
+// index s0 on `st` -- the counters' reset, then per sweep the Metropolis
+// part and the over-relaxation part, the last of them finishing measured or
 // exchanging sweeps -- followed by the counter advance.  No
 // synchronisation.
 cudaError_t issue_persistent(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, int se, uint64_t s0,
                              const BlockCounts& bc) {
   PersistentArgs a = persistent_args(c);
-  cudaError_t e = cudaMemsetAsync(a.bar, 0, kBarBytes, st);
+  unsigned long long* const work[2] = {a.work, a.work + kSyncWork1};
+  unsigned long long work_base[2] = {0ull, 0ull};
+  cudaError_t e = cudaMemsetAsync(a.work, 0, sync_bytes(c->n_slots), st);
   uint64_t n_rec = 0, n_swp = 0;
+  int n_launch = 0;
+  a.hs0 = 0;
+  a.fin0 = 0;
   for (int s = 0; s < ns && e == cudaSuccess; ++s) {
     const bool meas = due(s0 + s, me), swp = due(s0 + s, se);
     for (int part = kPartMetropolis; part <= kPartOverrelax && e == cudaSuccess; ++part) {
@@ -1278,10 +1294,17 @@ cudaError_t issue_persistent(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns
         a.n_half = fin ? 1 : 2 * n_pass - (finishes ? 1 : 0);
         if (a.n_half == 0) continue;
         a.mpass_off = static_cast<uint64_t>(s) * nM + (fin ? n_pass - 1 : 0);
-        e = launch_persistent(c, st, a, part, fin != 0);
-        a.bar0 += persistent_barriers(a.n_half, fin != 0, swp);
-        a.work0 += static_cast<unsigned long long>(a.n_half) *
-                   (static_cast<unsigned long long>(c->plan.n_items) + c->plan.G);
+        const int q = n_launch & 1;
+        a.work = work[q];
+        a.work0 = work_base[q];
+        e = launch_persistent(c, st, a, part, fin != 0, n_launch > 0);
+        // every block makes one grab that finds the list empty
+        work_base[q] += static_cast<unsigned long long>(
+                            persistent_items(a.n_half, c->plan.n_items, fin != 0, c->n_slots, c->plan.B)) +
+                        static_cast<unsigned long long>(c->plan.G);
+        a.hs0 += static_cast<unsigned long long>(a.n_half);
+        if (fin) a.fin0 += 1ull;
+        ++n_launch;
       }
     }
     n_rec += meas ? 1 : 0;
@@ -1308,8 +1331,7 @@ int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
     // The kernels read the device counters; which sweeps measure or
     // exchange, and the counter advance, depend on the phase of s0 against
     // the two periods.
-    const uint64_t P = static_cast<uint64_t>(lcm_int(me > 0 ? me : 1, se > 0 ? se : 1));
-    const auto key = std::make_tuple(nM, nOR, ns, me, se, static_cast<int>(s0 % P), 1);
+    const auto key = std::make_tuple(nM, nOR, ns, me, se, static_cast<long long>(s0 % sweep_period(me, se)), 1);
     auto it = c->graphs.find(key);
     if (it == c->graphs.end()) {
       cudaGraph_t g = nullptr;
@@ -1324,7 +1346,7 @@ int persistent_sweeps(xy_ctx* c, int nM, int nOR, int ns, int me, int se) {
         if (e != cudaSuccess) return fail_cuda(c, e, "cudaGraphInstantiate");
         it = c->graphs.emplace(key, ex).first;
       } else {
-        // Capture of a cooperative launch is not available: launch directly.
+        // The launches could not be captured: launch directly.
         if (g) cudaGraphDestroy(g);
         cudaGetLastError();
         c->plan.graph_ok = false;
@@ -1352,10 +1374,10 @@ int xy_debug_barrier_timeout(xy_ctx* c, int budget_us, int* status_out) {
   PersistentArgs a = persistent_args(c);
   a.poison = 1;
   a.budget_ns = static_cast<long long>(budget_us) * 1000;
-  XY_TRY(c, cudaMemsetAsync(a.bar, 0, kBarBytes, c->stream));
+  XY_TRY(c, cudaMemsetAsync(a.work, 0, sync_bytes(c->n_slots), c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));
   a.n_half = 1;
-  XY_TRY(c, launch_persistent(c, c->stream, a, kPartOverrelax, false));
+  XY_TRY(c, launch_persistent(c, c->stream, a, kPartOverrelax, false, false));
   int st = 0;
   XY_TRY(c, cudaMemcpyAsync(&st, a.status, 4, cudaMemcpyDeviceToHost, c->stream));
   XY_TRY(c, cudaMemsetAsync(a.status, 0, 4, c->stream));

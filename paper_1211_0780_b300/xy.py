@@ -419,7 +419,9 @@ class Simulation:
         return int(s.value)
 
     def debug_barrier_timeout(self, budget_us: int):
-        """Runs the bounded-barrier test hook; returns (status code, device status)."""
+        """Runs the test hook of the persistent launch's bounded waits (every
+        block waits for a count nothing raises); returns (status code,
+        device status)."""
         s = ctypes.c_int(0)
         rc = lib().xy_debug_barrier_timeout(self._ctx, int(budget_us), ctypes.byref(s))
         return int(rc), int(s.value)

@@ -449,8 +449,8 @@ def test_counters_and_series_records():
 
 
 def test_exec_modes_bit_identical():
-    """Plain launches, the captured graph and the persistent cooperative
-    launch give the same angles, permutations and records, bit for bit."""
+    """Plain launches, the captured graph and the persistent launches give
+    the same angles, permutations and records, bit for bit."""
     from paper_1211_0780_b300 import xy
     Ls, Rs = [16, 24], [4, 3]
     betas = [0.40, 0.43, 0.46, 0.49, 0.44, 0.45, 0.46]
@@ -523,7 +523,7 @@ def test_direct_tile_matches_march_tile_bit_for_bit():
     records and accept counts, bit for bit, over many chained launches of
     plain, graph and persistent execution (a stale L1 line would show
     here: in the persistent launch the other colour is rewritten within the
-    launch, between grid barriers)."""
+    launch, by other blocks, ordered only by the per-slot counts)."""
     from paper_1211_0780_b300 import xy
     Ls, Rs = [16, 24], [4, 3]
     betas = [0.40, 0.43, 0.46, 0.49, 0.44, 0.45, 0.46]
@@ -564,8 +564,9 @@ def test_direct_tile_fixed_sizes_match_march(L):
 
 
 def test_barrier_timeout_reports_status_without_hanging():
-    """The persistent kernel's grid barrier gives up after its budget and
-    reports XY_ERR_TIMEOUT through the status word; the context stays usable."""
+    """A persistent launch whose waits nothing satisfies gives up after its
+    budget and reports XY_ERR_TIMEOUT through the status word; the context
+    stays usable."""
     from paper_1211_0780_b300 import xy
     s = sim(16, 2, [0.40, 0.45])
     s.set_exec(xy.EXEC_PERSISTENT)
