@@ -471,6 +471,32 @@ def test_exec_modes_bit_identical():
         assert np.array_equal(outs[0][4][1], other[4][1])
 
 
+@pytest.mark.parametrize("nM,nOR,me,se", [(0, 2, 2, 1), (2, 0, 1, 3), (3, 1, 4, 2)])
+def test_persistent_pass_mixes_bit_identical(nM, nOR, me, se):
+    """The persistent launches against plain launches for sweeps with no
+    Metropolis pass, no over-relaxation pass (the finishing launch then ends
+    the Metropolis part) and several of each, over calls that start at
+    different phases of the measuring and exchange periods, on a ladder of
+    40 replicas (more slots than a warp's lanes in the exchange's counts)."""
+    from paper_1211_0780_b300 import xy
+    Ls, Rs = [8, 16, 24], [40, 3, 2]
+    betas = list(np.linspace(0.40, 0.50, 40)) + [0.43, 0.45, 0.47, 0.44, 0.46]
+    outs = []
+    for mode in (xy.EXEC_PLAIN, xy.EXEC_PERSISTENT):
+        s = sim(Ls, Rs, betas, series_capacity=64)
+        s.set_exec(mode)
+        for n in (3, 5, 4):
+            s.sweep(nM, nOR, n, measure_every=me, pt_swap_every=se)
+        a, p, c = s.get_state()
+        outs.append((s.get_packed(), p, c, s.read_series(), s.accepts()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+    assert len(outs[0][3]) > 0 and outs[0][3].tobytes() == outs[1][3].tobytes()
+    assert np.array_equal(outs[0][4][0], outs[1][4][0])
+    assert np.array_equal(outs[0][4][1], outs[1][4][1])
+
+
 def test_tile_shapes_give_identical_angles():
     res = []
     for tile in ((16, 16, MARCH), (4, 8, MARCH), (5, 3, MARCH), (2, 4, MARCH), (8, 8, BLOCK),
