@@ -301,13 +301,15 @@ int xy_debug_fast_math(int kind, int64_t n, const void *d_in, float *d_out,
  * barriers: each thread loads its y-neighbour rows and x-halo element
  * itself through the L1 cache, one plane ahead (in XY_EXEC_PERSISTENT the
  * acquire of the slot's count before each tile orders those loads after
- * the previous half-sweep's writes).  kind 4 (angle): the direct tile on a lattice kept
- * as FP32 angles in [0, 2 pi) instead of vectors (4 instead of 8 bytes per
- * spin; each colour's angles sit where its cosines are in the vector
- * layout): every angle read is turned into its vector by the fast sincos
- * and the update stores the new angle (the proposal's, or atan2 of the
- * reflected vector).  Changing a lattice between kind 4 and another kind
- * converts its state in place (atan2f / sincosf, within 1e-6 rad).
+ * the previous half-sweep's writes).  kind 4 (angle): the march's thread
+ * layout on a lattice kept as FP32 angles in [0, 2 pi) instead of vectors
+ * (4 instead of 8 bytes per spin; each colour's angles sit where its
+ * cosines are in the vector layout): every other-colour angle of the tile
+ * is turned into its vector once by the fast sincos and shared through the
+ * shared-memory plane buffers, and the update stores the new angle (the
+ * proposal's, or 2 phi - theta with phi the field's angle, Eq. 2).
+ * Changing a lattice between kind 4 and another kind converts its state in
+ * place (atan2f / sincosf, within 1e-6 rad).
  * xy_set_tile checks 1 <= ty, tz <= L, the block size against
  * the kernels' limit (512 threads at their register use on sm_103a; 240
  * for kinds 3 and 4), tz <= 64 for kind 1, and that the tile count fits the

@@ -169,8 +169,9 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDi
 }
 
 // One half-sweep of one lattice with the kTileAngle tile (angle storage):
-// grid and block as k_half_direct.
-template <int MODE, bool MEAS, int LC>
+// grid (tiles per slot, R), block (L/8, ty); shared memory: the tile's
+// plane buffers, then the reduction area of the measuring variant.
+template <int MODE, bool MEAS>
 __global__ void __maxnreg__(kDirectMaxRegs) k_half_angle(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   if (!pp.own_ready) chain_wait_and_release();  // else tile_angle waits after its own-colour loads
@@ -181,13 +182,14 @@ __global__ void __maxnreg__(kDirectMaxRegs) k_half_angle(Lattice lat, int colour
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
-  tile_angle<MODE, MEAS, LC>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
+  tile_angle<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nth = blockDim.x * blockDim.y;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);
   if (MEAS) {
+    double* red = reinterpret_cast<double*>(sm + tile_floats(kTileAngle, lat.L, lat.ty, lat.tz));
     const long long part = lat.part0 + static_cast<long long>(r) * lat.nyt * lat.nzt + t;
-    block_sums_to(pp.partials + part * kNumSums, acc, tid, nth, reinterpret_cast<double*>(sm));
+    block_sums_to(pp.partials + part * kNumSums, acc, tid, nth, red);
   }
 }
 

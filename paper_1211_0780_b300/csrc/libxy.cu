@@ -313,9 +313,9 @@ template <int MODE>
 cudaError_t launch_angle(dim3 grid, dim3 block, int smem, cudaStream_t st, const Lattice& d, int colour,
                          const PassParams& pp) {
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
-  if (MODE == kMeasureOnly) return launch_chained(k_half_angle<kMeasureOnly, true, 0>, grid, block, smem, st, d, colour, pp);
-  if (pp.measure && colour == 1) return launch_chained(k_half_angle<M, true, 0>, grid, block, smem, st, d, colour, pp);
-  return launch_chained(k_half_angle<M, false, 0>, grid, block, smem, st, d, colour, pp);
+  if (MODE == kMeasureOnly) return launch_chained(k_half_angle<kMeasureOnly, true>, grid, block, smem, st, d, colour, pp);
+  if (pp.measure && colour == 1) return launch_chained(k_half_angle<M, true>, grid, block, smem, st, d, colour, pp);
+  return launch_chained(k_half_angle<M, false>, grid, block, smem, st, d, colour, pp);
 }
 
 template <int MODE, int KIND>
@@ -628,20 +628,23 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
     if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncGetAttributes"));
     c->max_block = std::min(c->max_block, fa.maxThreadsPerBlock);
   }
-  // The kTileDirect kernels: their own block limit (kDirectMaxThreads), no
-  // tile in shared memory.
+  // The kTileDirect and kTileAngle kernels: their own block limit
+  // (kDirectMaxThreads); the angle tile keeps its plane buffers in shared
+  // memory (up to ~50 KB at L = 1024).
   const void* direct_kernels[10] = {
       reinterpret_cast<const void*>(k_half_direct<kMetropolis, false, 0>),
       reinterpret_cast<const void*>(k_half_direct<kMetropolis, true, 0>),
       reinterpret_cast<const void*>(k_half_direct<kOverrelax, false, 0>),
       reinterpret_cast<const void*>(k_half_direct<kOverrelax, true, 0>),
       reinterpret_cast<const void*>(k_half_direct<kMeasureOnly, true, 0>),
-      reinterpret_cast<const void*>(k_half_angle<kMetropolis, false, 0>),
-      reinterpret_cast<const void*>(k_half_angle<kMetropolis, true, 0>),
-      reinterpret_cast<const void*>(k_half_angle<kOverrelax, false, 0>),
-      reinterpret_cast<const void*>(k_half_angle<kOverrelax, true, 0>),
-      reinterpret_cast<const void*>(k_half_angle<kMeasureOnly, true, 0>)};
+      reinterpret_cast<const void*>(k_half_angle<kMetropolis, false>),
+      reinterpret_cast<const void*>(k_half_angle<kMetropolis, true>),
+      reinterpret_cast<const void*>(k_half_angle<kOverrelax, false>),
+      reinterpret_cast<const void*>(k_half_angle<kOverrelax, true>),
+      reinterpret_cast<const void*>(k_half_angle<kMeasureOnly, true>)};
   for (const void* fn : direct_kernels) {
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+    if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncSetAttribute"));
     cudaFuncAttributes fa{};
     e = cudaFuncGetAttributes(&fa, fn);
     if (e != cudaSuccess) return bail(fail_cuda(nullptr, e, "cudaFuncGetAttributes"));

@@ -278,7 +278,7 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
       // threads beyond the tile's rows return at once
       tile_direct<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc);
     } else if (KIND == kTileAngle) {
-      tile_angle<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc);
+      tile_angle<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc);
     } else {
       tile_pass<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc);
     }

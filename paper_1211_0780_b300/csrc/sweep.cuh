@@ -170,7 +170,7 @@ __host__ __device__ inline int tile_threads(int kind, int L, int ty, int tz) {
 __host__ __device__ inline int tile_floats(int kind, int L, int ty, int tz) {
   return kind == kTileBlock                            ? block_tile_floats(L, ty, tz)
          : kind == kTileStream                         ? stream_tile_floats(L, ty)
-         : (kind == kTileDirect || kind == kTileAngle) ? 0
+         : kind == kTileDirect                         ? 0
                                                        : tile_plane_floats(L, ty);
 }
 __host__ __device__ inline int tile_bytes(int kind, int L, int ty, int tz) {
@@ -213,6 +213,17 @@ struct Spins4 {
 __device__ __forceinline__ float wrap_angle(float t) {
   t = t < 0.f ? t + kTwoPi : t;
   return t >= kTwoPi ? 0.f : t;
+}
+
+// The reflection of Eq. (2) of an angle t in [0, 2 pi) about the field
+// (hx, hy) != 0: 2 phi - t with phi = atan2(hy, hx) in [-pi, pi], taken into
+// [0, 2 pi) (2 phi - t lies in (-4 pi, 2 pi]; 2 phi is exact, so the fused
+// multiply-add rounds once).
+__device__ __forceinline__ float reflect_angle(float hx, float hy, float t) {
+  float u = fmaf(2.f, atan2f(hy, hx), -t);
+  u = u < 0.f ? u + kTwoPi : u;
+  u = u < 0.f ? u + kTwoPi : u;
+  return u >= kTwoPi ? 0.f : u;
 }
 
 // The vectors of four stored angles (kTileAngle), with the fast sincos of
@@ -373,9 +384,10 @@ __device__ __forceinline__ void reflect2(float2 hx, float2 hy, float2 c, float2 
 // (Metropolis).  Returns the new spins; accumulates the accepted proposals
 // and, when measuring, this plane's lattice-sum terms (stepv).  ANG (angle
 // storage): *oa holds the own angles, and *na receives the new angles: the
-// proposal's where accepted, atan2 of the reflected vector where reflected,
+// proposal's where accepted, 2 phi - theta (reflect_angle) where reflected,
 // the old angle elsewhere (also where the field is zero); the new spins n
-// are then the vectors of those angles when measuring.
+// are then the vectors of those angles when measuring (o is not read by
+// the over-relaxation update).
 template <int MODE, bool MEAS, bool ANG = false>
 __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int s, const Spins4& ym,
                                         const Spins4& yp, const Spins4& zm, const Spins4& zp, const Spins4& o,
@@ -428,12 +440,17 @@ __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int
         nang[q] = make_float2(a0 ? tp.x : ta.x, a1 ? tp.y : ta.y);
       }
     } else if (MODE == kOverrelax) {
-      reflect2(hx[q], hy[q], co, so, nc[q], ns[q]);
       if (ANG) {
+        // Eq. (2) on the stored angle itself: theta' = 2 phi - theta with
+        // phi the field's angle (no vector of the own site is needed)
         const float2 ta = q ? make_float2(oa->z, oa->w) : make_float2(oa->x, oa->y);
         const float2 n2 = __ffma2_rn(hy[q], hy[q], __fmul2_rn(hx[q], hx[q]));
-        nang[q] = make_float2(n2.x > 0.f ? wrap_angle(atan2f(ns[q].x, nc[q].x)) : ta.x,
-                              n2.y > 0.f ? wrap_angle(atan2f(ns[q].y, nc[q].y)) : ta.y);
+        nang[q] = make_float2(n2.x > 0.f ? reflect_angle(hx[q].x, hy[q].x, ta.x) : ta.x,
+                              n2.y > 0.f ? reflect_angle(hx[q].y, hy[q].y, ta.y) : ta.y);
+        nc[q] = co;  // unused: the measuring variant forms the vectors of the new angles
+        ns[q] = so;
+      } else {
+        reflect2(hx[q], hy[q], co, so, nc[q], ns[q]);
       }
     } else {
       nc[q] = co;
@@ -766,128 +783,150 @@ __device__ __forceinline__ void st_ang(const SpinGuard& g, float* p, const float
   if (g.ok(p, 4)) st4(p, v);
 }
 
-// One tile of one half-sweep, kTileAngle: tile_direct's thread layout, plane
-// march and loads on a lattice stored as angles, each colour's N/2 FP32
-// angles at the places of its cosines (the sine places are unused), so a
-// half-sweep moves 12 bytes per update instead of 24.  Every angle is turned
-// into its vector one plane after its load (when its value is needed; the
-// column's planes once, for their three uses) by the fast sincos, and the
-// update (update4, the same arithmetic as every tile kind on those vectors)
-// stores the new angle: the proposal's where a Metropolis move is accepted,
-// atan2 of the reflected vector of Eq. (2) where the field is non-zero, the
-// old angle otherwise.  The spins therefore differ from the vector kinds'
-// by the fast sincos of the neighbours (a few 1e-7 per vector) instead of
-// their stored rounding.  Arguments as tile_direct.
-template <int MODE, bool MEAS, int LC = 0>
+// One tile of one half-sweep, kTileAngle: a lattice stored as angles, each
+// colour's N/2 FP32 angles at the places of its cosines (the sine places are
+// unused), so a half-sweep moves 12 bytes per update instead of 24.  The
+// march's thread layout and plane march (tile_pass): every thread loads its
+// row of the other colour's next plane as angles and turns them into
+// vectors (the fast sincos) once; the row goes to a shared-memory plane
+// buffer, where the threads of rows y-1 and y+1 read it, and stays in the
+// thread's registers for its three uses as planes z+1, z and z-1 (the
+// tile's edge rows and planes are turned by the threads next to them).  So
+// each other-colour angle of the tile becomes a vector once, not once per
+// reader.  The update (update4: the field and the Metropolis test are the
+// same arithmetic as every tile kind's on those vectors) stores the new
+// angle: the proposal's where a Metropolis move is accepted, the reflection
+// of Eq. (2) taken on the angle itself (2 phi - theta, phi the field's angle
+// by atan2) where the field is non-zero, the old angle otherwise.  The spins
+// therefore differ from the vector kinds' by the fast sincos of the
+// neighbours (a few 1e-7 per vector) and by the reflection's arithmetic, and
+// do not depend on the tile.
+// Arguments as tile_pass; every thread of the block must call it (it
+// contains barriers).  Library-chained launches (pp.own_ready) load the own
+// colour's first plane before griddepcontrol.wait, as tile_direct does.
+template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_angle(const Lattice& lat, int r, int yt, int zt, int colour, int tx, int ty,
-                                           const PassParams& pp, float* acc_out, uint32_t& n_acc) {
+                                           bool in_block, const PassParams& pp, float* sm, float* acc_out,
+                                           uint32_t& n_acc) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
-  static_assert(LC % 8 == 0, "L % 8 == 0");
-  const int L = LC ? LC : lat.L;
+  const int L = lat.L;
   const int H = L >> 1;
   const uint32_t PS = static_cast<uint32_t>(H) * static_cast<uint32_t>(L);  // plane stride
   const uint32_t half = PS * static_cast<uint32_t>(L);                       // N / 2
   const int y0 = yt * lat.ty, z0 = zt * lat.tz;
   const int TYa = min(lat.ty, L - y0), TZa = min(lat.tz, L - z0);
-  if (ty >= TYa) return;
+  const bool act = in_block && ty < TYa;
   const int y = y0 + ty;
   float* const slot = lat.spins + static_cast<size_t>(r) * (4 * static_cast<size_t>(half));
   const SpinGuard sg = spin_guard(slot, 4 * static_cast<size_t>(half), pp.status);
   float* const own = slot + colour * (2 * half);  // angles where the cosines of the vector layout are
   const float* const oth = slot + (colour ^ 1) * (2 * half);
-  const int ym = (y == 0 ? L : y) - 1;
-  const int yp = (y + 1 == L) ? 0 : y + 1;
+  const int rows = lat.ty + 2;
+  const int ym = (y0 == 0 ? L : y0) - 1;          // halo row y0 - 1 (periodic)
+  const int yp = (y0 + TYa == L) ? 0 : y0 + TYa;  // halo row y0 + TYa
+  const bool top = act && ty == 0;
+  const bool bot = act && ty == TYa - 1;
   const uint32_t offy = static_cast<uint32_t>(H * y + 4 * tx);
   const uint32_t offym = static_cast<uint32_t>(H * ym + 4 * tx);
   const uint32_t offyp = static_cast<uint32_t>(H * yp + 4 * tx);
-  const uint32_t offh0 = static_cast<uint32_t>(H * y + ((tx == 0) ? H - 1 : 4 * tx - 1));
-  const uint32_t offh1 = static_cast<uint32_t>(H * y + ((4 * tx + 4 == H) ? 0 : 4 * tx + 4));
+  auto row_ptr = [&](int b, int rr) -> float* { return sm + (b * rows + rr) * 2 * H; };
+  const int kh0 = (tx == 0) ? H - 1 : 4 * tx - 1;
+  const int kh1 = (4 * tx + 4 == H) ? 0 : 4 * tx + 4;
 
+  float beta = 0.f;
   uint32_t tagw = 0u, mlo = 0u, mhi = 0u;
   if (MODE == kMetropolis) {
     tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) | kTagMet;
+  }
+  SumAcc<MEAS> sums;
+
+  Spins4 pa{}, pb{}, pc{};  // rotating register planes: vectors of the other colour's column rows
+  float4 nx_oth{}, nx_own{}, nx_h0{}, nx_h1{};  // the next plane's angles
+  const uint32_t zz = static_cast<uint32_t>(z0) * PS;
+  if (act) nx_own = ld_ang(sg, own + offy + zz);
+  if (pp.own_ready) chain_wait_and_release();
+  if (MODE == kMetropolis) {
+    beta = __ldcg(pp.beta_slot + lat.slot0 + r);
     const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
     mlo = static_cast<uint32_t>(mp);
     mhi = static_cast<uint32_t>(mp >> 32);
   }
-  SumAcc<MEAS> sums;
-
-  // Registers: the vectors of the column's other-colour planes z-1, z, z+1
-  // rotate through four slots (plane z+1's vector is formed at the step that
-  // first uses it); two sets of this plane's and the next plane's operands
-  // alternate, held as angles (half the registers of vectors) with the next
-  // column plane's angles and the Metropolis words.
-  struct Operands {
-    float4 own, ym, yp, zn;  // angles: own sites; other colour rows y-1, y+1; column plane z+1
-    float h;                 // the other colour's x-halo angle
-    uint4 w0, w1;            // Metropolis words of sites (0, 1) and (2, 3)
-  };
-  Spins4 P0, P1, P2, P3{};
-  Operands A, B;
-  auto load_own = [&](Operands& o, uint32_t pz) {
-    o.own = ld_ang(sg, own + offy + pz);
-    if (MODE == kMetropolis) {
-      const uint32_t q0 = (offy + pz) >> 1;
-      o.w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
-      o.w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
-    } else {
-      o.w0 = o.w1 = make_uint4(0u, 0u, 0u, 0u);
+  if (act) {
+    const uint32_t zb = static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS;
+    const uint32_t z1 = static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS;
+    pa = spins_of_angles(ld_ang_l1(sg, oth + offy + zb));
+    pb = spins_of_angles(ld_ang_l1(sg, oth + offy + zz));
+    put_row(row_ptr(0, ty + 1), H, tx, pb);
+    if (top) put_row(row_ptr(0, 0), H, tx, spins_of_angles(ld_ang_l1(sg, oth + offym + zz)));
+    if (bot) put_row(row_ptr(0, TYa + 1), H, tx, spins_of_angles(ld_ang_l1(sg, oth + offyp + zz)));
+    nx_oth = ld_ang_l1(sg, oth + offy + z1);
+    if (TZa > 1) {
+      if (top) nx_h0 = ld_ang_l1(sg, oth + offym + z1);
+      if (bot) nx_h1 = ld_ang_l1(sg, oth + offyp + z1);
     }
-  };
-  auto load_other = [&](Operands& o, int z, uint32_t pz) {
-    o.ym = ld_ang_l1(sg, oth + offym + pz);
-    o.yp = ld_ang_l1(sg, oth + offyp + pz);
-    o.h = ld1_l1(sg, oth + (((y + z + colour) & 1) ? offh1 : offh0) + pz);
-  };
-  float beta = 0.f;
-  {
-    const uint32_t zz = static_cast<uint32_t>(z0) * PS;
-    // the own colour before griddepcontrol.wait in library-chained launches,
-    // as in tile_direct (other launches waited on entry)
-    load_own(A, zz);
-    if (pp.own_ready) chain_wait_and_release();
-    if (MODE == kMetropolis) beta = __ldcg(pp.beta_slot + lat.slot0 + r);
-    P3 = spins_of_angles(ld_ang_l1(sg, oth + offy + static_cast<uint32_t>((z0 == 0 ? L : z0) - 1) * PS));
-    P0 = spins_of_angles(ld_ang_l1(sg, oth + offy + zz));
-    A.zn = ld_ang_l1(sg, oth + offy + static_cast<uint32_t>((z0 + 1 == L) ? 0 : z0 + 1) * PS);
-    load_other(A, z0, zz);
   }
+  __syncthreads();
 
-  // One plane: zm, zc = the vectors of planes z-1, z; zn receives plane
-  // z+1's (from cur.zn); cur holds this plane's operands, nxt receives the
-  // next plane's (with plane z+2's column angles).
-  auto step = [&](Spins4& zm, Spins4& zc, Spins4& zn, Operands& cur, Operands& nxt, int i) {
+  // One plane: zm, zc = the vectors of planes z-1, z (registers); zn
+  // receives plane z+1's.
+  auto step = [&](auto bc, Spins4& zm, Spins4& zc, Spins4& zn, int i) {
+    constexpr int b0 = decltype(bc)::value;
+    constexpr int b1 = b0 == 2 ? 0 : b0 + 1;
     const int z = z0 + i;
-    if (i + 1 < TZa) {
-      nxt.zn = ld_ang_l1(sg, oth + offy + static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS);
-      load_own(nxt, static_cast<uint32_t>(z + 1) * PS);
-      load_other(nxt, z + 1, static_cast<uint32_t>(z + 1) * PS);
-    }
-    zn = spins_of_angles(cur.zn);
-    const Spins4 vo = spins_of_angles(cur.own), vym = spins_of_angles(cur.ym), vyp = spins_of_angles(cur.yp);
-    float hc, hs;
-    spin(cur.h, hc, hs);
-    const int s = (y + z + colour) & 1;
-    const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
-    float stepv[kNumSums];
+    if (act) {
+      const float4 t_own = nx_own;
+      zn = spins_of_angles(nx_oth);
+      if (i + 1 < TZa) {
+        put_row(row_ptr(b1, ty + 1), H, tx, zn);
+        if (top) put_row(row_ptr(b1, 0), H, tx, spins_of_angles(nx_h0));
+        if (bot) put_row(row_ptr(b1, TYa + 1), H, tx, spins_of_angles(nx_h1));
+        // prefetch the next plane's operands
+        const uint32_t pz1 = static_cast<uint32_t>(z + 1) * PS;
+        const uint32_t pz2 = static_cast<uint32_t>(z + 2 >= L ? z + 2 - L : z + 2) * PS;
+        nx_oth = ld_ang_l1(sg, oth + offy + pz2);
+        nx_own = ld_ang(sg, own + offy + pz1);
+        if (i + 2 < TZa) {
+          if (top) nx_h0 = ld_ang_l1(sg, oth + offym + pz2);
+          if (bot) nx_h1 = ld_ang_l1(sg, oth + offyp + pz2);
+        }
+      }
+      const float* rm = row_ptr(b0, ty);
+      const float* rp = row_ptr(b0, ty + 2);
+      const float* r0 = row_ptr(b0, ty + 1);
+      Spins4 ysm, ysp;
+      ysm.c = reinterpret_cast<const float4*>(rm)[tx];
+      ysm.s = reinterpret_cast<const float4*>(rm + H)[tx];
+      ysp.c = reinterpret_cast<const float4*>(rp)[tx];
+      ysp.s = reinterpret_cast<const float4*>(rp + H)[tx];
+      const int s = (y + z + colour) & 1;
+      const int kh = s ? kh1 : kh0;
+      const float hc = r0[kh], hs = r0[H + kh];
+      const uint32_t offz = offy + static_cast<uint32_t>(z) * PS;
+      uint4 w0 = make_uint4(0u, 0u, 0u, 0u), w1 = w0;
+      if (MODE == kMetropolis) {
+        const uint32_t q0 = offz >> 1;
+        w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
+        w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
+      }
+      float stepv[kNumSums];
 #pragma unroll
-    for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
-    Spins4 nw;
-    float4 na;
-    update4<MODE, MEAS, true>(zc, hc, hs, s, vym, vyp, zm, zn, vo, cur.w0, cur.w1, beta, nw, n_acc, stepv,
-                              &cur.own, &na);
-    if (MEAS) sums.add_plane(stepv);
-    if (MODE != kMeasureOnly) st_ang(sg, own + offz, na);
+      for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
+      Spins4 nw;
+      float4 na;
+      update4<MODE, MEAS, true>(zc, hc, hs, s, ysm, ysp, zm, zn, spins_of_angles(t_own), w0, w1, beta, nw, n_acc,
+                                stepv, &t_own, &na);
+      if (MEAS) sums.add_plane(stepv);
+      if (MODE != kMeasureOnly) st_ang(sg, own + offz, na);
+    }
+    __syncthreads();
   };
 
-  for (int i = 0; i < TZa; i += 4) {
-    step(P3, P0, P1, A, B, i);
+  for (int i = 0; i < TZa; i += 3) {
+    step(IC<0>{}, pa, pb, pc, i);
     if (i + 1 >= TZa) break;
-    step(P0, P1, P2, B, A, i + 1);
+    step(IC<1>{}, pb, pc, pa, i + 1);
     if (i + 2 >= TZa) break;
-    step(P1, P2, P3, A, B, i + 2);
-    if (i + 3 >= TZa) break;
-    step(P2, P3, P0, B, A, i + 3);
+    step(IC<2>{}, pc, pa, pb, i + 2);
   }
   if (MEAS) sums.export_to(acc_out);
 }

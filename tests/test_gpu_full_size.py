@@ -20,7 +20,7 @@ pytestmark = pytest.mark.gpu
 SEED = 0x5EED2012
 TOL_RAD, MARGIN = 1e-5, 1e-6
 OR_A, OR_B = 8.4e-6, 1e-6  # the conditioning bound of test_gpu_parity
-OR_A_ANG, OR_B_ANG = 7.6e-6, 2.1e-6  # the angle tile kind's (test_gpu_angle)
+OR_A_ANG, OR_B_ANG = 7.6e-6, 2.8e-6  # the angle tile kind's (test_gpu_angle)
 BOND_TOL = 2e-6
 
 
