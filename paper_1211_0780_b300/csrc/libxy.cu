@@ -1296,7 +1296,9 @@ cudaError_t issue_persistent(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns
       for (int fin = 0; fin < (finishes ? 2 : 1) && e == cudaSuccess; ++fin) {
         a.n_half = fin ? 1 : 2 * n_pass - (finishes ? 1 : 0);
         if (a.n_half == 0) continue;
-        a.mpass_off = static_cast<uint64_t>(s) * nM + (fin ? n_pass - 1 : 0);
+        // the pass counter offset of the launch's first pass (the kernel
+        // adds the later passes' index)
+        a.pp.mpass_off = part == kPartMetropolis ? static_cast<uint64_t>(s) * nM + (fin ? n_pass - 1 : 0) : 0ull;
         const int q = n_launch & 1;
         a.work = work[q];
         a.work0 = work_base[q];

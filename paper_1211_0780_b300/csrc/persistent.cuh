@@ -68,14 +68,13 @@ constexpr int kSyncSlot0 = 32;
 enum PersistentPart : int { kPartMetropolis = 0, kPartOverrelax = 1 };
 
 struct PersistentArgs {
-  PassParams pp;                 // mpass_off and measure are set per item
+  PassParams pp;                 // mpass_off: the pass counter offset of a Metropolis launch's first pass
   FinishParams fp;               // offsets, record and swap set by the host per sweep (FIN)
   const Lattice* lats;
   const int4* items;             // (lattice, local slot, tile, unused), by decreasing cost
   int n_items;                   // tile items of one half-sweep
   int n_lat;
   int n_half;                    // half-sweeps of this launch (black, white, black, ...; FIN: 1, white)
-  uint64_t mpass_off;            // kPartMetropolis: pass counter offset of its first half-sweep's pass
   unsigned long long hs0;        // half-sweeps every slot finished before this launch in the call
   unsigned long long fin0;       // finishing steps every slot finished before this launch in the call
   unsigned long long work0;      // this launch's item counter's value at its start
@@ -264,23 +263,22 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
     // FIN: one half-sweep, the last pass's white sites, measured (the
     // per-launch path's fused pass, so the records are identical)
     const int colour = FIN ? 1 : (h & 1);
-    PassParams pp = a.pp;
-    pp.mpass_off = PART == kPartMetropolis ? a.mpass_off + static_cast<uint64_t>(h >> 1) : 0ull;
-    pp.measure = FIN ? 1 : 0;
+    const PassParams& pp = a.pp;
+    const uint32_t pass_add = PART == kPartMetropolis ? static_cast<uint32_t>(h >> 1) : 0u;
     float acc[kNumSums];
 #pragma unroll
     for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
     uint32_t n_acc = 0u;
     if (KIND == kTileBlock) {
       const int ty = rest % lat.ty, tz = rest / lat.ty;
-      tile_block<MODE, FIN>(lat, w.y, yt, zt, colour, tx, ty, tz, tz < lat.tz, pp, sm, acc, n_acc);
+      tile_block<MODE, FIN>(lat, w.y, yt, zt, colour, tx, ty, tz, tz < lat.tz, pp, sm, acc, n_acc, pass_add);
     } else if (KIND == kTileDirect) {
       // threads beyond the tile's rows return at once
-      tile_direct<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc);
+      tile_direct<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc, pass_add);
     } else if (KIND == kTileAngle) {
-      tile_angle<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc);
+      tile_angle<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc, pass_add);
     } else {
-      tile_pass<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc);
+      tile_pass<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc, pass_add);
     }
     if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + w.y, n_acc, tid, B);
     if (FIN) {

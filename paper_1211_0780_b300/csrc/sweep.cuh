@@ -492,11 +492,12 @@ __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int
 // onto the tile at all (the persistent kernel's flat blocks have spares).
 // Every thread of the block must call this (it contains barriers).
 // acc_out[] receives this thread's FP32 lattice-sum partials (MEAS);
-// n_acc its accepted Metropolis proposals.
+// n_acc its accepted Metropolis proposals; pass_add is added to the
+// Metropolis pass counter (a persistent launch's later passes).
 template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int zt, int colour,
                                           int tx, int ty, bool in_block, const PassParams& pp,
-                                          float* sm, float* acc_out, uint32_t& n_acc) {
+                                          float* sm, float* acc_out, uint32_t& n_acc, uint32_t pass_add = 0) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
   const int L = lat.L;
   const int H = L >> 1;
@@ -529,7 +530,7 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
     beta = __ldcg(pp.beta_slot + lat.slot0 + r);
     tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) |
            kTagMet;
-    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off + pass_add;
     mlo = static_cast<uint32_t>(mp);
     mhi = static_cast<uint32_t>(mp >> 32);
   }
@@ -644,7 +645,7 @@ __device__ __forceinline__ float ld1_l1(const SpinGuard& g, const float* p) {
 // cos-to-sin offset are constants folded into the addressing.
 template <int MODE, bool MEAS, int LC = 0>
 __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, int zt, int colour, int tx,
-                                            int ty, const PassParams& pp, float* acc_out, uint32_t& n_acc) {
+                                            int ty, const PassParams& pp, float* acc_out, uint32_t& n_acc, uint32_t pass_add = 0) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
   static_assert(LC % 8 == 0, "L % 8 == 0");
   const int L = LC ? LC : lat.L;
@@ -672,7 +673,7 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   if (MODE == kMetropolis) {
     tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) |
            kTagMet;
-    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off + pass_add;
     mlo = static_cast<uint32_t>(mp);
     mhi = static_cast<uint32_t>(mp >> 32);
   }
@@ -807,7 +808,7 @@ __device__ __forceinline__ void st_ang(const SpinGuard& g, float* p, const float
 template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_angle(const Lattice& lat, int r, int yt, int zt, int colour, int tx, int ty,
                                            bool in_block, const PassParams& pp, float* sm, float* acc_out,
-                                           uint32_t& n_acc) {
+                                           uint32_t& n_acc, uint32_t pass_add = 0) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
   const int L = lat.L;
   const int H = L >> 1;
@@ -847,7 +848,7 @@ __device__ __forceinline__ void tile_angle(const Lattice& lat, int r, int yt, in
   if (pp.own_ready) chain_wait_and_release();
   if (MODE == kMetropolis) {
     beta = __ldcg(pp.beta_slot + lat.slot0 + r);
-    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off + pass_add;
     mlo = static_cast<uint32_t>(mp);
     mhi = static_cast<uint32_t>(mp >> 32);
   }
@@ -1009,7 +1010,7 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // kernel, whose other blocks write the planes within one launch.
 template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, int zt, int colour, int tid,
-                                            const PassParams& pp, float* sm, float* acc_out, uint32_t& n_acc) {
+                                            const PassParams& pp, float* sm, float* acc_out, uint32_t& n_acc, uint32_t pass_add = 0) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
   constexpr int D = kStreamStages;
   const int L = lat.L;
@@ -1118,7 +1119,7 @@ __device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, i
     if (MODE == kMetropolis) {
       beta = __ldcg(pp.beta_slot + lat.slot0 + r);
       tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) | kTagMet;
-      const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+      const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off + pass_add;
       mlo = static_cast<uint32_t>(mp);
       mhi = static_cast<uint32_t>(mp >> 32);
     }
@@ -1209,7 +1210,7 @@ __device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, i
 template <int MODE, bool MEAS>
 __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, int zt, int colour,
                                            int tx, int ty, int tz, bool in_block, const PassParams& pp,
-                                           float* sm, float* acc_out, uint32_t& n_acc) {
+                                           float* sm, float* acc_out, uint32_t& n_acc, uint32_t pass_add = 0) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
   const int L = lat.L;
   const int H = L >> 1;
@@ -1236,7 +1237,7 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
     beta = __ldcg(pp.beta_slot + lat.slot0 + r);
     tagw = (static_cast<uint32_t>(lat.slot0 + r) << 4) | (static_cast<uint32_t>(colour) << 3) |
            kTagMet;
-    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off;
+    const uint64_t mp = (pp.ctr ? pp.ctr[kCtrMpass] : 0ull) + pp.mpass_off + pass_add;
     mlo = static_cast<uint32_t>(mp);
     mhi = static_cast<uint32_t>(mp >> 32);
   }
