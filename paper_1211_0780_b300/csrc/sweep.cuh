@@ -467,23 +467,39 @@ __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int
     if (MEAS) n = spins_of_angles(*na);
   }
   if (MEAS) {
+    // Bonds (w, w+mu) and (w-mu, w) of the white site w: every bond has
+    // exactly one white end, so each is counted once.  C_mu: cos of the
+    // bond's angle difference, w . (w+mu + w-mu); S_mu: sin,
+    // w x (w+mu - w-mu); M: the white site and the black site of this
+    // column.  Sites in pairs, the two pairs added lane-wise, then the
+    // lanes.
+    float2 t[kNumSums];
 #pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      // Bonds (w, w+mu) and (w-mu, w) of the white site w: every bond has
-      // exactly one white end, so each is counted once.
-      const float c = comp(n.c, e), sn = comp(n.s, e);
-      const float pxc = Xc[e + 1], qxc = Xc[e], pxs = Xs[e + 1], qxs = Xs[e];
-      const float pyc = comp(yp.c, e), qyc = comp(ym.c, e), pys = comp(yp.s, e), qys = comp(ym.s, e);
-      const float pzc = comp(zp.c, e), qzc = comp(zm.c, e), pzs = comp(zp.s, e), qzs = comp(zm.s, e);
-      stepv[0] += c + comp(z.c, e);  // white site + the black site of this column
-      stepv[1] += sn + comp(z.s, e);
-      stepv[2] += c * (pxc + qxc) + sn * (pxs + qxs);
-      stepv[3] += c * (pyc + qyc) + sn * (pys + qys);
-      stepv[4] += c * (pzc + qzc) + sn * (pzs + qzs);
-      stepv[5] += sn * (pxc - qxc) - c * (pxs - qxs);
-      stepv[6] += sn * (pyc - qyc) - c * (pys - qys);
-      stepv[7] += sn * (pzc - qzc) - c * (pzs - qzs);
+    for (int q = 0; q < 2; ++q) {
+      const float2 c2 = q ? hi2(n.c) : lo2(n.c), s2 = q ? hi2(n.s) : lo2(n.s);
+      float2 v[kNumSums];
+      v[0] = __fadd2_rn(c2, q ? hi2(z.c) : lo2(z.c));
+      v[1] = __fadd2_rn(s2, q ? hi2(z.s) : lo2(z.s));
+      // +mu and -mu neighbours of the pair's two sites along x, y, z
+      const float2 pc[3] = {make_float2(Xc[2 * q + 1], Xc[2 * q + 2]), q ? hi2(yp.c) : lo2(yp.c),
+                            q ? hi2(zp.c) : lo2(zp.c)};
+      const float2 mc[3] = {make_float2(Xc[2 * q], Xc[2 * q + 1]), q ? hi2(ym.c) : lo2(ym.c),
+                            q ? hi2(zm.c) : lo2(zm.c)};
+      const float2 ps[3] = {make_float2(Xs[2 * q + 1], Xs[2 * q + 2]), q ? hi2(yp.s) : lo2(yp.s),
+                            q ? hi2(zp.s) : lo2(zp.s)};
+      const float2 ms[3] = {make_float2(Xs[2 * q], Xs[2 * q + 1]), q ? hi2(ym.s) : lo2(ym.s),
+                            q ? hi2(zm.s) : lo2(zm.s)};
+#pragma unroll
+      for (int mu = 0; mu < 3; ++mu) {
+        v[2 + mu] = __ffma2_rn(c2, __fadd2_rn(pc[mu], mc[mu]), __fmul2_rn(s2, __fadd2_rn(ps[mu], ms[mu])));
+        v[5 + mu] = __ffma2_rn(s2, __fadd2_rn(pc[mu], neg2(mc[mu])),
+                               __fmul2_rn(neg2(c2), __fadd2_rn(ps[mu], neg2(ms[mu]))));
+      }
+#pragma unroll
+      for (int j = 0; j < kNumSums; ++j) t[j] = q ? __fadd2_rn(t[j], v[j]) : v[j];
     }
+#pragma unroll
+    for (int j = 0; j < kNumSums; ++j) stepv[j] += t[j].x + t[j].y;
   }
 }
 
