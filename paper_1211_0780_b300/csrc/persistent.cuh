@@ -193,11 +193,13 @@ __device__ __noinline__ void finish_items(const PersistentArgs& a, long long it,
     if (tid == 0) {
       const unsigned long long t = atomicAdd(a.work, 1ull) - a.work0;
       *s_item = t < static_cast<unsigned long long>(n_all) ? static_cast<long long>(t) : -1ll;
-      if (*s_item < 0) launch_dependents();
     }
     __syncthreads();
     it = *s_item;
-    if (it < 0) return;
+    if (it < 0) {
+      launch_dependents();  // every item of this launch is taken
+      return;
+    }
     __syncthreads();  // every thread has read s_item before it is written again
   }
 }
@@ -232,7 +234,6 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
       const unsigned long long t = atomicAdd(a.work, 1ull) - a.work0;
       const long long it = t < static_cast<unsigned long long>(n_all) ? static_cast<long long>(t) : -1ll;
       int ok = 1;
-      if (it < 0) launch_dependents();  // every item of this launch is taken
       if (it >= 0 && it < n_tile) {
         const long long h = it / a.n_items;
         s_h = static_cast<int>(h);
@@ -247,6 +248,7 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
     }
     __syncthreads();
     const long long it = s_item;
+    if (it < 0) launch_dependents();  // every item of this launch is taken
     if (it < 0 || !s_ok) return;
     if (FIN && it >= static_cast<long long>(a.n_half) * a.n_items) {
       __syncthreads();  // every thread has read s_item before it is written again
