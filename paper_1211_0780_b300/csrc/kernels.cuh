@@ -144,13 +144,37 @@ __global__ void __launch_bounds__(512) k_half(Lattice lat, int colour, PassParam
   }
 }
 
+// Draws the calls [pp.gen_begin, pp.gen_end) of the Metropolis words of
+// lattice lat for the pass with counter ctr[kCtrMpass] + pp.gen_mpass, one
+// call per thread of the grid at a time: call i is call q = i mod N/4 of
+// colour c of local slot r, (2 r + c) = i / (N/4), with the counter
+// (q, pass, 0, tag) that the Metropolis update would use.
+__device__ __forceinline__ void draw_words(const Lattice& lat, const PassParams& pp) {
+  const uint32_t quarter = static_cast<uint32_t>(lat.L) * static_cast<uint32_t>(lat.L) * static_cast<uint32_t>(lat.L) / 4u;
+  const uint64_t mp = pp.ctr[kCtrMpass] + pp.gen_mpass;
+  const uint32_t mlo = static_cast<uint32_t>(mp), mhi = static_cast<uint32_t>(mp >> 32);
+  const uint32_t nth = gridDim.x * gridDim.y * blockDim.x * blockDim.y;
+  const uint32_t t0 = ((blockIdx.y * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y) * blockDim.x + threadIdx.x;
+  for (uint32_t i = pp.gen_begin + t0; i < pp.gen_end; i += nth) {
+    const uint32_t sc = i / quarter;
+    const uint32_t q = i - sc * quarter;
+    const uint32_t tagw = ((static_cast<uint32_t>(lat.slot0) + (sc >> 1)) << 4) | ((sc & 1u) << 3) | kTagMet;
+    __stcg(pp.words + i, philox4x32_10(make_uint4(q, mlo, mhi, tagw), pp.rk));
+  }
+}
+
 // One half-sweep of one lattice with the kTileDirect tile: grid (tiles per
 // slot, R), block (L/8, ty); shared memory only for the reduction of the
 // measuring variant.  LC: the lattice size fixed at compile time, or 0.
-template <int MODE, bool MEAS, int LC>
+// WG: 1, a Metropolis half-sweep that reads its pass's words (pp.words)
+// instead of drawing them; 2, an over-relaxation half-sweep that also draws
+// calls of the next Metropolis pass's words (before griddepcontrol.wait in
+// library-chained launches: no launch in flight reads them).
+template <int MODE, bool MEAS, int LC, int WG = 0>
 __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDirectMaxRegs) k_half_direct(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   if (!pp.own_ready) chain_wait_and_release();  // else tile_direct waits after its own-colour loads
+  if (WG == 2) draw_words(lat, pp);
   const int r = blockIdx.y;
   const int t = blockIdx.x;
   const int yt = t % lat.nyt, zt = t / lat.nyt;
@@ -158,7 +182,7 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDi
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
-  tile_direct<MODE, MEAS, LC>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
+  tile_direct<MODE, MEAS, LC, WG == 1>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nth = blockDim.x * blockDim.y;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);

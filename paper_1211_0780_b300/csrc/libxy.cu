@@ -35,6 +35,7 @@ struct LatHost {
   int kind;  // kTileMarch, kTileBlock, kTileStream or kTileDirect
   int ty, tz;
   size_t spin_off;  // floats from the spin base (2N per slot)
+  long long words_off;  // uint4s from the words base (R N/2), or -1: no words region
   int part0;         // first partial slot
   int part_cap;      // partial slots reserved per slot
   long long N() const { return static_cast<long long>(L) * L * L; }
@@ -49,7 +50,7 @@ int part_cap_for(int L) { return std::max(1, (L * L) / 4); }
 
 struct Layout {
   size_t spins, ladder_beta, perm, beta_slot, beta_slot64, bidx_slot, E_slot, sums_slot, partials,
-      acc_met, acc_swap, ctr, status, sync, nswapped, fin_done, lats, staging, plan_items, series, total;
+      acc_met, acc_swap, ctr, status, sync, nswapped, fin_done, words, words_bytes, lats, staging, plan_items, series, total;
 };
 
 constexpr int kMaxPlanBlocks = 8192;
@@ -64,6 +65,12 @@ bool valid_lattices(int n, const int* L, const int* R) {
   }
   return true;
 }
+
+// Whether a context keeps a words region: its (cos, sin) state, 8 bytes per
+// site, at most 40 MB, so that state and words (another 8 bytes per site)
+// fit in L2 together.
+constexpr long long kWordsMaxStateBytes = 40ll << 20;
+bool words_region(long long spin_floats) { return spin_floats * 4 <= kWordsMaxStateBytes; }
 
 Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
   Layout o{};
@@ -97,6 +104,11 @@ Layout layout_for(int n, const int* L, const int* R, int64_t series_cap) {
   o.sync = take(sync_bytes(slots));
   o.nswapped = take(64);
   o.fin_done = take(static_cast<size_t>(n) * 4);
+  // Metropolis words drawn ahead: one pass of every slot (16 B per two
+  // sites), only for a vector state small enough that state and words stay
+  // in L2 together
+  o.words_bytes = words_region(spin_floats) ? static_cast<size_t>(spin_floats) * 4 : 0;
+  o.words = take(o.words_bytes);
   o.lats = take(static_cast<size_t>(n) * sizeof(Lattice));
   o.staging = take(static_cast<size_t>(maxN) * 4);
   o.plan_items = take(static_cast<size_t>(parts) * sizeof(int4));
@@ -165,7 +177,7 @@ struct xy_ctx {
     return d;
   }
   PassParams pass_params(bool use_ctr, uint64_t mpass_off, int measure) const {
-    PassParams p;
+    PassParams p{};
     p.rk = philox_round_keys(seed);
     p.ctr = use_ctr ? ctr() : nullptr;
     p.mpass_off = mpass_off;
@@ -305,6 +317,10 @@ cudaError_t launch_direct(dim3 grid, dim3 block, int smem, cudaStream_t st, cons
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
   if (MODE == kMeasureOnly) return launch_chained(k_half_direct<kMeasureOnly, true, LC>, grid, block, smem, st, d, colour, pp);
   if (pp.measure && colour == 1) return launch_chained(k_half_direct<M, true, LC>, grid, block, smem, st, d, colour, pp);
+  if (MODE == kMetropolis && pp.words && pp.words_read)
+    return launch_chained(k_half_direct<M, false, LC, 1>, grid, block, smem, st, d, colour, pp);
+  if (MODE == kOverrelax && pp.words && pp.gen_end > pp.gen_begin)
+    return launch_chained(k_half_direct<M, false, LC, 2>, grid, block, smem, st, d, colour, pp);
   return launch_chained(k_half_direct<M, false, LC>, grid, block, smem, st, d, colour, pp);
 }
 
@@ -345,23 +361,49 @@ cudaError_t launch_half_kind(const LatHost& h, const Lattice& d, cudaStream_t st
   }
 }
 
+// The Metropolis words drawn ahead, for one half-sweep of issue_sweeps: a
+// Metropolis half-sweep of a sweep's first pass reads the words the previous
+// sweep's over-relaxation half-sweeps drew (read); over-relaxation
+// half-sweep `part` of `parts` draws that share of the next sweep's words,
+// for the pass counter offset `mpass`.  Only lattices on the direct tile in
+// a context with a words region take part.
+struct WordPlan {
+  int read = 0;
+  int part = 0, parts = 0;
+  uint64_t mpass = 0;
+};
+
 template <int MODE>
-int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams& pp) {
+int launch_half(xy_ctx* c, cudaStream_t st, int i, int colour, const PassParams& pp, const WordPlan& wp = WordPlan()) {
   const LatHost& h = c->lat[i];
   const Lattice d = c->dev_lat(i);
-  const cudaError_t e = h.kind == kTileBlock    ? launch_half_kind<MODE, kTileBlock>(h, d, st, colour, pp)
-                       : h.kind == kTileStream ? launch_half_kind<MODE, kTileStream>(h, d, st, colour, pp)
-                       : h.kind == kTileDirect ? launch_half_kind<MODE, kTileDirect>(h, d, st, colour, pp)
-                       : h.kind == kTileAngle  ? launch_half_kind<MODE, kTileAngle>(h, d, st, colour, pp)
-                                               : launch_half_kind<MODE, kTileMarch>(h, d, st, colour, pp);
+  PassParams q = pp;
+  q.words = nullptr;
+  q.words_read = 0;
+  q.gen_begin = q.gen_end = 0;
+  if (h.kind == kTileDirect && h.words_off >= 0 && (wp.read || wp.parts > 0)) {
+    q.words = c->at<uint4>(c->lay.words) + h.words_off;
+    q.words_read = wp.read;
+    if (wp.parts > 0) {
+      const uint64_t calls = static_cast<uint64_t>(h.R) * static_cast<uint64_t>(h.N() / 2);
+      q.gen_begin = static_cast<uint32_t>(calls * wp.part / wp.parts);
+      q.gen_end = static_cast<uint32_t>(calls * (wp.part + 1) / wp.parts);
+      q.gen_mpass = wp.mpass;
+    }
+  }
+  const cudaError_t e = h.kind == kTileBlock    ? launch_half_kind<MODE, kTileBlock>(h, d, st, colour, q)
+                       : h.kind == kTileStream ? launch_half_kind<MODE, kTileStream>(h, d, st, colour, q)
+                       : h.kind == kTileDirect ? launch_half_kind<MODE, kTileDirect>(h, d, st, colour, q)
+                       : h.kind == kTileAngle  ? launch_half_kind<MODE, kTileAngle>(h, d, st, colour, q)
+                                               : launch_half_kind<MODE, kTileMarch>(h, d, st, colour, q);
   XY_TRY(c, e);
   return XY_OK;
 }
 
 template <int MODE>
-int launch_half_all(xy_ctx* c, cudaStream_t st, int colour, const PassParams& pp) {
+int launch_half_all(xy_ctx* c, cudaStream_t st, int colour, const PassParams& pp, const WordPlan& wp = WordPlan()) {
   for (int i = 0; i < c->n_lat; ++i) {
-    const int rc = launch_half<MODE>(c, st, i, colour, pp);
+    const int rc = launch_half<MODE>(c, st, i, colour, pp, wp);
     if (rc != XY_OK) return rc;
   }
   return XY_OK;
@@ -425,13 +467,28 @@ int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, in
           // Every half-sweep of a sweep but the first is chained behind the
           // other colour's half-sweep on the same stream (see tile_direct).
           pp.own_ready = (p > 0 || colour > 0) ? 1 : 0;
+          // Metropolis words drawn ahead: the over-relaxation half-sweeps
+          // after the sweep's first and before its last draw the next
+          // sweep's first-pass words (no launch in flight reads them then:
+          // the Metropolis half-sweeps that read the current ones completed
+          // before the first of those launches passed its wait, and the next
+          // sweep's first Metropolis half-sweep starts after the last one's),
+          // which that pass reads instead of drawing.
+          WordPlan wp;
+          const int k = 2 * (p - nM) + colour;  // over-relaxation half-sweep of the sweep
+          if (p == 0 && nM > 0 && nOR >= 2 && j > 0) wp.read = 1;
+          if (p >= nM && nM > 0 && j + 1 < ns && k >= 1 && k <= 2 * nOR - 2 && !measure) {
+            wp.part = k - 1;
+            wp.parts = 2 * nOR - 2;
+            wp.mpass = bc.mpass + nM;
+          }
           int rc;
           if (branches)
-            rc = p < nM ? launch_half<kMetropolis>(c, c->lat_streams[i], i, colour, pp)
-                        : launch_half<kOverrelax>(c, c->lat_streams[i], i, colour, pp);
+            rc = p < nM ? launch_half<kMetropolis>(c, c->lat_streams[i], i, colour, pp, wp)
+                        : launch_half<kOverrelax>(c, c->lat_streams[i], i, colour, pp, wp);
           else
-            rc = p < nM ? launch_half_all<kMetropolis>(c, st, colour, pp)
-                        : launch_half_all<kOverrelax>(c, st, colour, pp);
+            rc = p < nM ? launch_half_all<kMetropolis>(c, st, colour, pp, wp)
+                        : launch_half_all<kOverrelax>(c, st, colour, pp, wp);
           if (rc != XY_OK) return rc;
         }
         if (p < nM) mp += 1;
@@ -563,6 +620,8 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
     h.slot0 = slot;
     default_tile(h);
     h.spin_off = aoff;
+    // the words region mirrors the spin region: R N/2 uint4s per lattice
+    h.words_off = lay.words_bytes ? static_cast<long long>(aoff / 4) : -1;
     h.part_cap = part_cap_for(h.L);
     h.part0 = part;
     aoff += 2 * static_cast<size_t>(h.N()) * h.R;  // (cos, sin) per site

@@ -140,6 +140,13 @@ struct PassParams {
                                 // griddepcontrol.wait (see tile_direct)
   int* status;                  // set to XY_ERR_TIMEOUT when a bounded wait runs out
   long long wait_ns;            // bound of one wait for a copied plane
+  // Metropolis words drawn ahead (kTileDirect, per-launch path): the words
+  // of one Metropolis pass of the launch's lattice, one Philox4x32-10 output
+  // per call, at (slot * 2 + colour) * N/4 + call; null: none.
+  uint4* words;
+  int words_read;               // Metropolis: read the pass's words instead of drawing them
+  uint32_t gen_begin, gen_end;  // over-relaxation: draw the calls [begin, end) of the words
+  uint64_t gen_mpass;           // the pass counter of the words drawn = ctr[kCtrMpass] + gen_mpass
 };
 
 // Shared-memory bytes of one tile pass: three plane buffers of ty+2 rows of
@@ -659,7 +666,7 @@ __device__ __forceinline__ float ld1_l1(const SpinGuard& g, const float* p) {
 // return at once.  acc_out / n_acc as tile_pass.  LC > 0: the lattice size
 // fixed at compile time (it must equal lat.L), so that plane strides and the
 // cos-to-sin offset are constants folded into the addressing.
-template <int MODE, bool MEAS, int LC = 0>
+template <int MODE, bool MEAS, int LC = 0, bool WORDS = false>
 __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, int zt, int colour, int tx,
                                             int ty, const PassParams& pp, float* acc_out, uint32_t& n_acc, uint32_t pass_add = 0) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
@@ -710,9 +717,17 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
   Spins4 P0, P1, P2, P3{};
   Operands A, B;
   // The own colour's spins and the Metropolis words of one plane.
+  const uint4* const wrow =
+      WORDS ? pp.words + static_cast<size_t>(2 * r + colour) * static_cast<size_t>(half >> 1) : nullptr;
   auto load_own = [&](Operands& o, uint32_t pz) {
     o.own = ld_spins(sg, own + offy + pz, half);
-    if (MODE == kMetropolis) {
+    if (MODE == kMetropolis && WORDS) {
+      // the pass's words, drawn ahead by the preceding over-relaxation
+      // launches (the same Philox outputs)
+      const uint32_t q0 = (offy + pz) >> 1;
+      o.w0 = __ldcg(wrow + q0);
+      o.w1 = __ldcg(wrow + q0 + 1u);
+    } else if (MODE == kMetropolis) {
       const uint32_t q0 = (offy + pz) >> 1;
       o.w0 = philox4x32_10(make_uint4(q0, mlo, mhi, tagw), pp.rk);
       o.w1 = philox4x32_10(make_uint4(q0 + 1u, mlo, mhi, tagw), pp.rk);
@@ -740,8 +755,10 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
     // before griddepcontrol.wait: its predecessor writes only the other
     // colour, and the own colour's last writer, the launch before that, has
     // completed once the predecessor passed its own wait, which it did
-    // before releasing this launch.  Everything the predecessor may write
-    // (the other colour, the coupling after an exchange) is read after it.
+    // before releasing this launch (so have the launches that drew words
+    // read here: never the predecessor).  Everything the predecessor may
+    // write (the other colour, the coupling after an exchange) is read
+    // after it.
     if (pp.own_ready) {
       load_own(A, zz);
       chain_wait_and_release();
