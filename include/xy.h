@@ -106,7 +106,11 @@ typedef struct xy_record {
 
 /* Bytes of device workspace xy_init needs for these lattices and a series
  * buffer of `series_capacity` measurement events (each event holds one
- * record per slot).  Returns 0 for invalid arguments. */
+ * record per slot).  When the lattices' vector state (8 bytes per site) is
+ * at most 40 MB the workspace also holds one Metropolis pass's Philox words
+ * (another 8 bytes per site), which the over-relaxation half-sweeps of
+ * XY_EXEC_PLAIN and XY_EXEC_GRAPH draw ahead for the direct tile (kind 3).
+ * Returns 0 for invalid arguments. */
 size_t xy_workspace_bytes(int n_lattices, const int *L, const int *n_replicas,
                           int64_t series_capacity);
 
@@ -148,7 +152,12 @@ int xy_set_exec(xy_ctx *ctx, int mode);
  * (cos theta' - cos theta) + h_y (sin theta' - sin theta)] and h the sum of
  * the six neighbour spin vectors.  Over-relaxation half-sweep (Eq. 2): the
  * spin is reflected about its local field, S' = 2 (S.h / h.h) h - S (as an
- * angle theta' = 2 atan2(h_y, h_x) - theta mod 2 pi); h = 0 leaves it.  Errors: XY_ERR_ARG (negative counts,
+ * angle theta' = 2 atan2(h_y, h_x) - theta mod 2 pi); h = 0 leaves it.  The
+ * Philox words of a Metropolis pass depend only on the seed, the pass
+ * counter, the slot, the colour and the site, so with a words region (see
+ * xy_workspace_bytes) the over-relaxation half-sweeps between a sweep's
+ * first and last draw the next sweep's first-pass words and that pass reads
+ * them: the same words, the same spins.  Errors: XY_ERR_ARG (negative counts,
  * n_metropolis + n_overrelax == 0 with n_sweeps > 0), XY_ERR_NOMEM (the
  * series buffer would overflow: read it first), XY_ERR_TIMEOUT, XY_ERR_CUDA. */
 int xy_sweep(xy_ctx *ctx, int n_metropolis, int n_overrelax, int n_sweeps,
