@@ -573,6 +573,33 @@ def test_direct_tile_matches_march_tile_bit_for_bit():
         assert np.array_equal(outs[0][4][1], other[4][1])
 
 
+@pytest.mark.parametrize("nM,nOR", [(1, 5), (2, 3), (1, 2), (1, 1)])
+def test_words_drawn_ahead_bit_identical(nM, nOR):
+    """The Metropolis words drawn ahead by the over-relaxation half-sweeps
+    (direct tile, plain and graph execution) give the spins, records and
+    accept counts of the persistent launches, which draw every word in the
+    Metropolis update itself, bit for bit: one lattice at a compiled size
+    and two lattices on separate streams, over calls of several sweeps
+    (with nOR = 1 nothing is drawn ahead)."""
+    from paper_1211_0780_b300 import xy
+    for Ls, Rs, tiles in (([64], [2], [(8, 8)]), ([32, 48], [2, 1], [(4, 8), (8, 6)])):
+        betas = list(np.linspace(0.44, 0.46, sum(Rs)))
+        outs = []
+        for mode in (xy.EXEC_PLAIN, xy.EXEC_GRAPH, xy.EXEC_PERSISTENT):
+            s = sim(Ls, Rs, betas, series_capacity=32)
+            for i, (ty, tz) in enumerate(tiles):
+                s.set_tile(i, ty, tz, DIRECT)
+            s.set_exec(mode)
+            s.sweep(nM, nOR, 5, measure_every=2, pt_swap_every=1)
+            s.sweep(nM, nOR, 3, measure_every=2, pt_swap_every=1)
+            outs.append((s.get_packed(), s.get_state()[1], s.read_series(), s.accepts()))
+        for other in outs[1:]:
+            assert np.array_equal(outs[0][0], other[0])
+            assert np.array_equal(outs[0][1], other[1])
+            assert outs[0][2].tobytes() == other[2].tobytes()
+            assert np.array_equal(outs[0][3][0], other[3][0])
+
+
 @pytest.mark.parametrize("L", [64, 80, 96, 128])
 def test_direct_tile_fixed_sizes_match_march(L):
     """The direct-tile kernels compiled for the paper's lattice sizes (L
