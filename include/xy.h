@@ -340,7 +340,9 @@ int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
  * wide as the widest tile: for the march, the block, the direct (and, as
  * above, the angle) kind and for tiles of at most 64, 128 and 256 threads,
  * each lattice's best tile is found as above, and the sets are timed in the
- * persistent launch itself; the fastest is kept. */
+ * persistent launch itself (on sweeps that end with an exchange when a
+ * ladder has two or more replicas; the ladders' permutations, couplings and
+ * exchange counts are saved and restored too); the fastest is kept. */
 int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
 
 /* Device-side status word of the last persistent launch (0 = fine). */
