@@ -96,6 +96,36 @@ def test_autotune_cache_reuses_tiles(tmp_path):
     assert len(xy.load_tile_cache(path)) == 2
 
 
+@pytest.mark.parametrize("mode", [0, 2])
+def test_autotune_leaves_the_state(mode):
+    """Autotuning runs trial sweeps (in persistent mode with an exchange at
+    every sweep's end) but restores the spins, the ladder's permutation and
+    couplings, and the counters and accept counts: the context then sweeps
+    exactly as a fresh one set to the tiles autotune chose."""
+    from paper_1211_0780_b300 import xy
+    betas = [0.42, 0.44, 0.46, 0.48]
+    a = xy.Simulation([16, 24], [4, 2], betas + [0.44, 0.45], 11, series_capacity=16)
+    a.set_exec(mode)
+    a.sweep(1, 2, 3, pt_swap_every=1)
+    before = (a.get_packed(), a.get_state()[1], a.get_state()[2], a.accepts())
+    tiles = a.autotune(1, 2)
+    after = (a.get_packed(), a.get_state()[1], a.get_state()[2], a.accepts())
+    assert np.array_equal(before[0], after[0])
+    assert np.array_equal(before[1], after[1])
+    assert np.array_equal(before[2], after[2])
+    assert np.array_equal(before[3][0], after[3][0]) and np.array_equal(before[3][1], after[3][1])
+    b = xy.Simulation([16, 24], [4, 2], betas + [0.44, 0.45], 11, series_capacity=16)
+    b.set_exec(mode)
+    b.sweep(1, 2, 3, pt_swap_every=1)
+    for i, (ty, tz, kind) in enumerate(tiles):
+        b.set_tile(i, ty, tz, kind)
+    for s in (a, b):
+        s.sweep(1, 2, 4, measure_every=2, pt_swap_every=1)
+    assert np.array_equal(a.get_packed(), b.get_packed())
+    assert np.array_equal(a.get_state()[1], b.get_state()[1])
+    assert a.read_series().tobytes() == b.read_series().tobytes()
+
+
 def test_readme_usage_runs():
     """The usage example of the README at a small size: ladder run, series
     split by coupling, differentiable reweighting, checkpoint and resume."""
