@@ -290,9 +290,12 @@ int xy_debug_draws(xy_ctx *ctx, int slot, int colour, int tag, uint64_t count,
  * product) as the update forms it with the fast sincos.  kind 1: d_in holds
  * n FP32 exponents x = -beta dE; d_out[i] receives the threshold exp(x) 2^24
  * (fast exponential) that the update compares the acceptance word's
- * (w >> 8) with.  Device pointers owned by the caller, on the current
- * device; ordered on `stream`, which the call synchronises.  XY_ERR_ARG for
- * another kind, n < 0 or a null pointer with n > 0. */
+ * (w >> 8) with.  kind 2: d_in holds n FP32 pairs (x, y), not both zero;
+ * d_out[i] receives the angle-storage tile's atan2(y, x) (the field's
+ * angle of the over-relaxation of Eq. 2 on stored angles).  Device pointers
+ * owned by the caller, on the current device; ordered on `stream`, which
+ * the call synchronises.  XY_ERR_ARG for another kind, n < 0 or a null
+ * pointer with n > 0. */
 int xy_debug_fast_math(int kind, int64_t n, const void *d_in, float *d_out,
                        void *stream);
 

@@ -20,7 +20,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 SOURCES = ["libxy.cu", "reweight.cu", "fss.cu", "multihist.cu", "peaks.cu", "ladder.cpp"]
-HEADERS = ["philox.cuh", "sweep.cuh", "kernels.cuh", "persistent.cuh"]
+HEADERS = ["philox.cuh", "sweep.cuh", "kernels.cuh", "persistent.cuh", "atan_poly.cuh"]
 LIB = os.path.join(HERE, "libxy.so")
 CHECK_LIB = os.path.join(HERE, "libxy_check.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -377,8 +377,11 @@ __global__ void k_fast_math(int kind, long long n, const void* __restrict__ in, 
       spin(proposal_angle(static_cast<const uint32_t*>(in)[i]), c, s);
       out[2 * i] = c;
       out[2 * i + 1] = s;
-    } else {
+    } else if (kind == 1) {
       out[i] = accept_threshold(static_cast<const float*>(in)[i]);
+    } else {
+      const float* xy2 = static_cast<const float*>(in);
+      out[i] = atan2_poly(xy2[2 * i + 1], xy2[2 * i]);
     }
   }
 }

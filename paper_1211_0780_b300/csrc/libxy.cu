@@ -1160,7 +1160,7 @@ int xy_debug_draws(xy_ctx* c, int slot, int colour, int tag, uint64_t count, uin
 }
 
 int xy_debug_fast_math(int kind, int64_t n, const void* d_in, float* d_out, void* stream) {
-  if ((kind != 0 && kind != 1) || n < 0 || (n > 0 && (!d_in || !d_out))) return XY_ERR_ARG;
+  if (kind < 0 || kind > 2 || n < 0 || (n > 0 && (!d_in || !d_out))) return XY_ERR_ARG;
   if (n == 0) return XY_OK;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int blocks = static_cast<int>(std::min<int64_t>((n + 255) / 256, 16384));

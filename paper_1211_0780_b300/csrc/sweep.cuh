@@ -40,6 +40,7 @@
 #include <cstdint>
 
 #include "../../include/xy.h"
+#include "atan_poly.cuh"
 #include "philox.cuh"
 
 namespace xy {
@@ -222,12 +223,34 @@ __device__ __forceinline__ float wrap_angle(float t) {
   return t >= kTwoPi ? 0.f : t;
 }
 
+// atan2(y, x) in [-pi, pi] for (x, y) != (0, 0), without a division:
+// the octant reduction r = min(|x|, |y|) / max(|x|, |y|) in [0, 1] (the
+// approximate reciprocal and one Newton correction of the quotient), the
+// minimax polynomial atan(r) ~ r P(r^2) of atan_poly.cuh, then
+// pi/2 - a where |y| > |x|, pi - a where x < 0 (each constant as a
+// rounded value plus its FP32 remainder), and the sign of y.  Measured
+// against FP64 atan2: at most 3.0e-7 rad (tests/test_gpu_accuracy.py).
+__device__ __forceinline__ float atan2_poly(float y, float x) {
+  constexpr float kPio2Hi = 1.57079637e+00f, kPio2Lo = -4.37113883e-08f;
+  constexpr float kPiHi = 3.14159274e+00f, kPiLo = -8.74227766e-08f;
+  const float ax = fabsf(x), ay = fabsf(y);
+  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
+  float inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(mx));
+  const float q = mn * inv;
+  const float r = fmaf(fmaf(-q, mx, mn), inv, q);
+  float a = r * atan_poly(r * r);
+  a = ay > ax ? (kPio2Hi - a) + kPio2Lo : a;
+  a = x < 0.f ? (kPiHi - a) + kPiLo : a;
+  return copysignf(a, y);
+}
+
 // The reflection of Eq. (2) of an angle t in [0, 2 pi) about the field
 // (hx, hy) != 0: 2 phi - t with phi = atan2(hy, hx) in [-pi, pi], taken into
 // [0, 2 pi) (2 phi - t lies in (-4 pi, 2 pi]; 2 phi is exact, so the fused
 // multiply-add rounds once).
 __device__ __forceinline__ float reflect_angle(float hx, float hy, float t) {
-  float u = fmaf(2.f, atan2f(hy, hx), -t);
+  float u = fmaf(2.f, atan2_poly(hy, hx), -t);
   u = u < 0.f ? u + kTwoPi : u;
   u = u < 0.f ? u + kTwoPi : u;
   return u >= kTwoPi ? 0.f : u;

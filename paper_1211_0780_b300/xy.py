@@ -477,15 +477,16 @@ def peak_probe(kind: str) -> float:
 
 
 def fast_math(kind: str, values) -> np.ndarray:
-    """The Metropolis update's fast-math expressions on the device (see
+    """The update's fast-math expressions on the device (see
     xy_debug_fast_math).  kind "proposal": uint32 proposal words -> (n, 2)
     FP32 proposal vectors (cos, sin); kind "accept": FP32 exponents x ->
-    the FP32 thresholds exp(x) 2^24."""
+    the FP32 thresholds exp(x) 2^24; kind "atan2": (n, 2) FP32 pairs
+    (x, y) -> the angle-storage tile's atan2(y, x)."""
     torch = _require_cuda()
-    k = {"proposal": 0, "accept": 1}[kind]
+    k = {"proposal": 0, "accept": 1, "atan2": 2}[kind]
     src = torch.as_tensor(np.ascontiguousarray(values, dtype=np.uint32 if k == 0 else np.float32).view(
         np.int32 if k == 0 else np.float32), device="cuda")
-    n = src.numel()
+    n = src.numel() // 2 if k == 2 else src.numel()
     out = torch.empty(2 * n if k == 0 else n, dtype=torch.float32, device="cuda")
     _check(lib().xy_debug_fast_math(k, n, src.data_ptr(), out.data_ptr(),
                                     torch.cuda.current_stream().cuda_stream), "xy_debug_fast_math")

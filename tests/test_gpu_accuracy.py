@@ -5,6 +5,7 @@ numbers with asserted bounds.
    same device functions the sweep kernels inline (xy_debug_fast_math):
    the proposal vector of every one of the 2^24 proposal words, and the
    acceptance threshold exp(x) 2^24 over the exponents x = -beta dE reached.
+   Also the angle-storage tile's atan2 over the plane.
 2. The error of each measured observable against the FP64 oracle on the
    same stored states: the lattice sums E, M, C_mu, S_mu of every record
    (Eqs. 4-6), U_L and rho_s of the series (Eqs. 5-6), and the reweighted
@@ -69,6 +70,34 @@ def test_acceptance_threshold_exponential():
           f"{rel.max():.3e} over [-30, 6]")
     assert np.all(rel <= (2.0 + 1.2 * np.abs(x.astype(np.float64))) * 2.0 ** -23)
     assert rel[inrange].max() <= 1.1e-6
+
+
+def test_angle_tile_atan2():
+    """The angle-storage tile's atan2 (octant reduction, the minimax
+    polynomial of atan_poly.cuh, no division) against FP64 atan2: random
+    pairs over eight decades of magnitude and both signs, the circle at
+    2 million angles (every octant boundary), the axes and the diagonals.
+    Bound: the polynomial's 6e-9, the quotient's and the evaluation's FP32
+    roundings (a few ulp of an angle below pi/4) and the final pi/2 - a and
+    pi - a (half an ulp of pi, with the constants' remainders added back):
+    4e-7 rad, below the 3 ulp (7.2e-7) of atan2f that the over-relaxation
+    bound of the angle kind allows for."""
+    from paper_1211_0780_b300 import xy
+    rng = np.random.default_rng(11)
+    n = 1 << 22
+    x = rng.standard_normal(n) * 10.0 ** rng.uniform(-6, 2, n)
+    y = rng.standard_normal(n) * 10.0 ** rng.uniform(-6, 2, n)
+    t = np.linspace(-np.pi, np.pi, 2_000_001)
+    axes = np.array([[1, 0], [0, 1], [-1, 0], [0, -1], [1, 1], [-1, 1], [-1, -1], [1, -1], [-1, 0.0]])
+    pts = np.concatenate([np.stack([x, y], 1), 3.7 * np.stack([np.cos(t), np.sin(t)], 1), 2.5 * axes])
+    pts = pts.astype(np.float32)
+    got = xy.fast_math("atan2", pts).astype(np.float64)
+    ref = np.arctan2(pts[:, 1].astype(np.float64), pts[:, 0].astype(np.float64))
+    d = np.abs(got - ref)
+    d = np.minimum(d, 2 * np.pi - d)
+    print(f"\nangle-tile atan2, {len(pts)} pairs: max error {d.max():.3e} rad, rms {np.sqrt(np.mean(d ** 2)):.3e}")
+    assert d.max() <= 4e-7
+    assert np.all(np.abs(got) <= np.pi + 1e-6)
 
 
 def test_observable_errors_against_the_oracle():

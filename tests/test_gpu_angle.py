@@ -26,10 +26,11 @@ TOL_RAD, MARGIN = 1e-5, 1e-6
 # (<= 3.5e-7 per component, measured <= 3.4e-7; as a vector error <= 4.3e-7
 # with the measured length error), six of them and the FP32 field sum
 # (<= 1.2e-6 per component) move the field by <= 3.8e-6 and phi by
-# <= |dh| / |h|, which the reflection doubles; atan2f (<= 3 ulp of phi,
-# 7.2e-7, doubled), the one rounding of 2 phi - theta (<= 4.8e-7, |2 phi -
-# theta| < 4 pi) and up to two additions of the FP32 2 pi to take it into
-# [0, 2 pi) (<= 1.75e-7 + 2.4e-7 each) add a constant.
+# <= |dh| / |h|, which the reflection doubles; the tile's atan2 (<= 4e-7,
+# test_gpu_accuracy; the bound keeps atan2f's 3 ulp, 7.2e-7, doubled), the
+# one rounding of 2 phi - theta (<= 4.8e-7, |2 phi - theta| < 4 pi) and up
+# to two additions of the FP32 2 pi to take it into [0, 2 pi)
+# (<= 1.75e-7 + 2.4e-7 each) add a constant.
 OR_A, OR_B = 7.6e-6, 2.8e-6
 BOND_TOL, SITE_TOL = 2e-6, 1e-6
 
