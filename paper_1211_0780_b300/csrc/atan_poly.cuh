@@ -20,4 +20,20 @@ __host__ __device__ __forceinline__ float atan_poly(float s) {
   return p;
 }
 
+#ifdef __CUDACC__
+// P of two values at once (__ffma2_rn: each lane rounds as fmaf does).
+__device__ __forceinline__ float2 atan_poly2(float2 s) {
+  float2 p = make_float2(0x1.4201f40000000p-9f, 0x1.4201f40000000p-9f);
+  p = __ffma2_rn(p, s, make_float2(-0x1.d7e7520000000p-7f, -0x1.d7e7520000000p-7f));
+  p = __ffma2_rn(p, s, make_float2(0x1.45e3460000000p-5f, 0x1.45e3460000000p-5f));
+  p = __ffma2_rn(p, s, make_float2(-0x1.2856fc0000000p-4f, -0x1.2856fc0000000p-4f));
+  p = __ffma2_rn(p, s, make_float2(0x1.ae09700000000p-4f, 0x1.ae09700000000p-4f));
+  p = __ffma2_rn(p, s, make_float2(-0x1.2205a00000000p-3f, -0x1.2205a00000000p-3f));
+  p = __ffma2_rn(p, s, make_float2(0x1.994fb60000000p-3f, 0x1.994fb60000000p-3f));
+  p = __ffma2_rn(p, s, make_float2(-0x1.5553680000000p-2f, -0x1.5553680000000p-2f));
+  p = __ffma2_rn(p, s, make_float2(0x1.fffffc0000000p-1f, 0x1.fffffc0000000p-1f));
+  return p;
+}
+#endif
+
 }  // namespace xy

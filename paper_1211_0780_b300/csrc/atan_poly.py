@@ -62,7 +62,19 @@ def main() -> None:
     for k in range(DEGREE - 1, -1, -1):
         v = float(c32[k])
         lines.append(f"  p = fmaf(p, s, {v.hex()}f);  // s^{k}: {v:.9g}")
-    lines += ["  return p;", "}", "", "}  // namespace xy", ""]
+    lines += ["  return p;", "}", ""]
+    # the same polynomial for two values at once in the paired FP32
+    # instructions of sm_100 and later (each lane rounds as fmaf does)
+    lines += [
+        "#ifdef __CUDACC__",
+        "// P of two values at once (__ffma2_rn: each lane rounds as fmaf does).",
+        "__device__ __forceinline__ float2 atan_poly2(float2 s) {",
+        f"  float2 p = make_float2({float(c32[DEGREE]).hex()}f, {float(c32[DEGREE]).hex()}f);",
+    ]
+    for k in range(DEGREE - 1, -1, -1):
+        v = float(c32[k]).hex()
+        lines.append(f"  p = __ffma2_rn(p, s, make_float2({v}f, {v}f));")
+    lines += ["  return p;", "}", "#endif", "", "}  // namespace xy", ""]
     with open(HEADER, "w") as fh:
         fh.write("\n".join(lines))
     print(HEADER, f"max |r P(r^2) - atan(r)| = {err:.3e}")

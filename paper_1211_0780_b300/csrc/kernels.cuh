@@ -380,8 +380,10 @@ __global__ void k_fast_math(int kind, long long n, const void* __restrict__ in, 
     } else if (kind == 1) {
       out[i] = accept_threshold(static_cast<const float*>(in)[i]);
     } else {
+      // lane 0 of the paired atan2 the tile uses (both lanes take the pair)
       const float* xy2 = static_cast<const float*>(in);
-      out[i] = atan2_poly(xy2[2 * i + 1], xy2[2 * i]);
+      const float x = xy2[2 * i], y = xy2[2 * i + 1];
+      out[i] = atan2_poly2(make_float2(y, y), make_float2(x, x)).x;
     }
   }
 }

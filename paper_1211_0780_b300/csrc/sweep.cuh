@@ -223,37 +223,46 @@ __device__ __forceinline__ float wrap_angle(float t) {
   return t >= kTwoPi ? 0.f : t;
 }
 
-// atan2(y, x) in [-pi, pi] for (x, y) != (0, 0), without a division:
-// the octant reduction r = min(|x|, |y|) / max(|x|, |y|) in [0, 1] (the
-// approximate reciprocal and one Newton correction of the quotient), the
-// minimax polynomial atan(r) ~ r P(r^2) of atan_poly.cuh, then
-// pi/2 - a where |y| > |x|, pi - a where x < 0 (each constant as a
-// rounded value plus its FP32 remainder), and the sign of y.  Measured
-// against FP64 atan2: at most 3.0e-7 rad (tests/test_gpu_accuracy.py).
-__device__ __forceinline__ float atan2_poly(float y, float x) {
+// atan2(y, x) in [-pi, pi] of two pairs (x, y) != (0, 0) at once, without
+// a division: the octant reduction r = min(|x|, |y|) / max(|x|, |y|) in
+// [0, 1] (the approximate reciprocal and one Newton correction of the
+// quotient), the minimax polynomial atan(r) ~ r P(r^2) of atan_poly.cuh,
+// then pi/2 - a where |y| > |x|, pi - a where x < 0 (each constant as a
+// rounded value plus its FP32 remainder), and the sign of y.  The quotient
+// and the polynomial run in the paired FP32 instructions (each lane rounds
+// as the scalar ones).  Measured against FP64 atan2: at most 3.0e-7 rad
+// (tests/test_gpu_accuracy.py).
+__device__ __forceinline__ float2 atan2_poly2(float2 y, float2 x) {
   constexpr float kPio2Hi = 1.57079637e+00f, kPio2Lo = -4.37113883e-08f;
   constexpr float kPiHi = 3.14159274e+00f, kPiLo = -8.74227766e-08f;
-  const float ax = fabsf(x), ay = fabsf(y);
-  const float mx = fmaxf(ax, ay), mn = fminf(ax, ay);
-  float inv;
-  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"(mx));
-  const float q = mn * inv;
-  const float r = fmaf(fmaf(-q, mx, mn), inv, q);
-  float a = r * atan_poly(r * r);
-  a = ay > ax ? (kPio2Hi - a) + kPio2Lo : a;
-  a = x < 0.f ? (kPiHi - a) + kPiLo : a;
-  return copysignf(a, y);
+  const float2 ax = make_float2(fabsf(x.x), fabsf(x.y)), ay = make_float2(fabsf(y.x), fabsf(y.y));
+  const float2 mx = make_float2(fmaxf(ax.x, ay.x), fmaxf(ax.y, ay.y));
+  const float2 mn = make_float2(fminf(ax.x, ay.x), fminf(ax.y, ay.y));
+  float2 inv;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.x) : "f"(mx.x));
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv.y) : "f"(mx.y));
+  const float2 q = __fmul2_rn(mn, inv);
+  const float2 r = __ffma2_rn(__ffma2_rn(make_float2(-q.x, -q.y), mx, mn), inv, q);
+  float2 a = __fmul2_rn(r, atan_poly2(__fmul2_rn(r, r)));
+  a.x = ay.x > ax.x ? (kPio2Hi - a.x) + kPio2Lo : a.x;
+  a.y = ay.y > ax.y ? (kPio2Hi - a.y) + kPio2Lo : a.y;
+  a.x = x.x < 0.f ? (kPiHi - a.x) + kPiLo : a.x;
+  a.y = x.y < 0.f ? (kPiHi - a.y) + kPiLo : a.y;
+  return make_float2(copysignf(a.x, y.x), copysignf(a.y, y.y));
 }
 
 // The reflection of Eq. (2) of an angle t in [0, 2 pi) about the field
 // (hx, hy) != 0: 2 phi - t with phi = atan2(hy, hx) in [-pi, pi], taken into
 // [0, 2 pi) (2 phi - t lies in (-4 pi, 2 pi]; 2 phi is exact, so the fused
-// multiply-add rounds once).
-__device__ __forceinline__ float reflect_angle(float hx, float hy, float t) {
-  float u = fmaf(2.f, atan2_poly(hy, hx), -t);
+// multiply-add rounds once).  Two sites at once.
+__device__ __forceinline__ float wrap_two_periods(float u) {
   u = u < 0.f ? u + kTwoPi : u;
   u = u < 0.f ? u + kTwoPi : u;
   return u >= kTwoPi ? 0.f : u;
+}
+__device__ __forceinline__ float2 reflect_angle2(float2 hx, float2 hy, float2 t) {
+  const float2 u = __ffma2_rn(make_float2(2.f, 2.f), atan2_poly2(hy, hx), make_float2(-t.x, -t.y));
+  return make_float2(wrap_two_periods(u.x), wrap_two_periods(u.y));
 }
 
 // The vectors of four stored angles (kTileAngle), with the fast sincos of
@@ -414,7 +423,7 @@ __device__ __forceinline__ void reflect2(float2 hx, float2 hy, float2 c, float2 
 // (Metropolis).  Returns the new spins; accumulates the accepted proposals
 // and, when measuring, this plane's lattice-sum terms (stepv).  ANG (angle
 // storage): *oa holds the own angles, and *na receives the new angles: the
-// proposal's where accepted, 2 phi - theta (reflect_angle) where reflected,
+// proposal's where accepted, 2 phi - theta (reflect_angle2) where reflected,
 // the old angle elsewhere (also where the field is zero); the new spins n
 // are then the vectors of those angles when measuring (o is not read by
 // the over-relaxation update).
@@ -475,8 +484,8 @@ __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int
         // phi the field's angle (no vector of the own site is needed)
         const float2 ta = q ? make_float2(oa->z, oa->w) : make_float2(oa->x, oa->y);
         const float2 n2 = __ffma2_rn(hy[q], hy[q], __fmul2_rn(hx[q], hx[q]));
-        nang[q] = make_float2(n2.x > 0.f ? reflect_angle(hx[q].x, hy[q].x, ta.x) : ta.x,
-                              n2.y > 0.f ? reflect_angle(hx[q].y, hy[q].y, ta.y) : ta.y);
+        const float2 rf = reflect_angle2(hx[q], hy[q], ta);
+        nang[q] = make_float2(n2.x > 0.f ? rf.x : ta.x, n2.y > 0.f ? rf.y : ta.y);
         nc[q] = co;  // unused: the measuring variant forms the vectors of the new angles
         ns[q] = so;
       } else {
