@@ -196,7 +196,7 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDi
 // grid (tiles per slot, R), block (L/8, ty); shared memory: the tile's
 // plane buffers, then the reduction area of the measuring variant.
 template <int MODE, bool MEAS>
-__global__ void __maxnreg__(kDirectMaxRegs) k_half_angle(Lattice lat, int colour, PassParams pp) {
+__global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kAngleMaxRegsOR : kDirectMaxRegs) k_half_angle(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   if (!pp.own_ready) chain_wait_and_release();  // else tile_angle waits after its own-colour loads
   const int r = blockIdx.y;

@@ -93,6 +93,12 @@ __host__ __device__ inline bool angle_storage(int kind) { return kind == kTileAn
 constexpr int kDirectMaxThreads = 240;
 constexpr int kDirectMaxRegs = 128;
 constexpr int kDirectMaxRegsOR = 120;
+// The angle tile's plain over-relaxation variant at most 96 registers
+// (81 used, no spills): five to six blocks of 128 threads per SM instead of
+// four, which the plane barrier and the load latency of the 128^3 x 16
+// half-sweep need (277 -> 329 updates/ns on the 8 x 16 tile; Metropolis
+// keeps kDirectMaxRegs, where a cap cost it 10%).
+constexpr int kAngleMaxRegsOR = 96;
 // Lattice sizes for which the kTileDirect kernels are also compiled with L
 // fixed: those of the paper's runs (Sec. III: L = 64, 80, 96, 128, 160);
 // other sizes use the kernels that read L at run time.  (At 160^3 the fixed
