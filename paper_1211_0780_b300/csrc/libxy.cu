@@ -1596,44 +1596,81 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
       for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, kind, kind + 1, cap);
       sets[q] = c->lat;
     }
-    float best = 1e30f;
-    int best_q = n_sets - 1;
     // the sets are timed on sweeps that end with an exchange when a ladder
     // has two or more replicas (parallel tempering; the finishing launch's
     // cost differs between kinds), else on plain sweeps
     int swap_every = 0;
     for (const LatHost& h : c->lat) swap_every = h.R > 1 ? 1 : swap_every;
-    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
-      c->lat = sets[q];
+    // Time of two persistent sweeps with a set: the untimed call builds the
+    // call's graph (capture and instantiation are host work that would
+    // otherwise fall inside the timed region), then the faster of two timed
+    // replays; 1e30 for a set the persistent kernel cannot run.
+    auto time_set = [&](const std::vector<LatHost>& set) -> float {
+      c->lat = set;
       for (int i = 0; i < c->n_lat; ++i) ensure_storage(i, c->lat[i].kind);
-      if (rc != XY_OK) break;
+      if (rc != XY_OK) return 1e30f;
       drop_graphs(c);
-      if ((rc = sync_lats(c)) != XY_OK) break;
-      // the untimed call builds the call's graph (capture and instantiation
-      // are host work that would otherwise fall inside the timed region);
-      // the faster of two timed replays
-      if (persistent_sweeps(c, nM, nOR, 2, 0, swap_every) != XY_OK) {  // a set the persistent kernel cannot run
+      if ((rc = sync_lats(c)) != XY_OK) return 1e30f;
+      if (persistent_sweeps(c, nM, nOR, 2, 0, swap_every) != XY_OK) {
         rc = c->sticky;
-        if (rc != XY_OK) break;
-        continue;
+        return 1e30f;
       }
       float ms = 1e30f;
       for (int round = 0; round < 2 && rc == XY_OK; ++round) {
-        XY_TRY(c, cudaEventRecord(e0, c->stream));
+        if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = fail_cuda(c, cudaGetLastError(), "autotune"); break; }
         if ((rc = persistent_sweeps(c, nM, nOR, 2, 0, swap_every)) != XY_OK) break;
-        XY_TRY(c, cudaEventRecord(e1, c->stream));
-        XY_TRY(c, cudaEventSynchronize(e1));
         float t = 0.f;
-        XY_TRY(c, cudaEventElapsedTime(&t, e0, e1));
+        if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+          rc = fail_cuda(c, cudaGetLastError(), "autotune");
+          break;
+        }
         ms = std::min(ms, t);
       }
-      if (rc != XY_OK) break;
-      if (ms < best) {
+      return ms;
+    };
+    float best = 1e30f;
+    int best_q = n_sets - 1;
+    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
+      const float ms = time_set(sets[q]);
+      if (rc == XY_OK && ms < best) {
         best = ms;
         best_q = q;
       }
     }
-    if (rc == XY_OK) c->lat = sets[best_q];
+    // The shapes came from per-launch timings: refine the kept set in the
+    // persistent launch itself, one lattice at a time (largest first), by
+    // doubling or halving its tile's rows or planes, keeping a change that
+    // is at least 1% faster.
+    std::vector<LatHost> cur = sets[best_q];
+    std::vector<int> order(c->n_lat);
+    for (int i = 0; i < c->n_lat; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return cur[a].N() * cur[a].R > cur[b].N() * cur[b].R; });
+    for (int i : order) {
+      if (rc != XY_OK || best >= 1e29f) break;
+      const LatHost h0 = cur[i];
+      const int cand_ty[4] = {h0.ty * 2, h0.ty / 2, h0.ty, h0.ty};
+      const int cand_tz[4] = {h0.tz, h0.tz, h0.tz * 2, h0.tz / 2};
+      for (int k = 0; k < 4 && rc == XY_OK; ++k) {
+        LatHost h = h0;
+        h.ty = cand_ty[k];
+        h.tz = cand_tz[k];
+        if (h.ty < 1 || h.tz < 1 || h.ty > h.L || h.tz > h.L || h.L % h.ty != 0 || h.L % h.tz != 0) continue;
+        if (h.kind != kTileBlock && h.tz < 2) continue;
+        if (h.tz > 32) continue;  // the range the per-launch search covers
+        if (h.threads() > std::min(kPersistentBlockThreads, kind_max_threads(c, h.kind)) || h.threads() < 32) continue;
+        if (h.nyt() * h.nzt() > h.part_cap || h.smem() > 200 * 1024) continue;
+        std::vector<LatHost> cand = cur;
+        cand[i] = h;
+        const float ms = time_set(cand);
+        if (rc == XY_OK && ms < 0.99f * best) {
+          best = ms;
+          cur = cand;
+        }
+      }
+    }
+    if (rc == XY_OK) c->lat = cur;
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
