@@ -497,6 +497,32 @@ def test_persistent_pass_mixes_bit_identical(nM, nOR, me, se):
     assert np.array_equal(outs[0][4][1], outs[1][4][1])
 
 
+@pytest.mark.parametrize("L,tile", [(64, (16, 8)), (80, (12, 6)), (96, (8, 5))])
+def test_persistent_direct_tile_bit_identical(L, tile):
+    """Persistent launches of the direct tile on the paper's lattice sizes
+    against plain launches (which run the kernels compiled for those sizes)
+    of the same sweeps (Metropolis and over-relaxation, sums and exchange),
+    bit for bit, with whole tiles at 64 and ragged last tiles at 80 (8 rows,
+    2 planes) and 96 (1 plane)."""
+    from paper_1211_0780_b300 import xy
+    R = 3
+    betas = [0.44, 0.45, 0.46]
+    outs = []
+    for mode in (xy.EXEC_PLAIN, xy.EXEC_PERSISTENT):
+        s = sim(L, R, betas, series_capacity=16)
+        s.set_tile(0, tile[0], tile[1], DIRECT)
+        s.set_exec(mode)
+        s.sweep(1, 2, 3, measure_every=1, pt_swap_every=1)
+        a, p, c = s.get_state()
+        outs.append((s.get_packed(), p, c, s.read_series(), s.accepts()))
+    assert np.array_equal(outs[0][0], outs[1][0])
+    assert np.array_equal(outs[0][1], outs[1][1])
+    assert np.array_equal(outs[0][2], outs[1][2])
+    assert len(outs[0][3]) == 3 * R and outs[0][3].tobytes() == outs[1][3].tobytes()
+    assert np.array_equal(outs[0][4][0], outs[1][4][0])
+    assert np.array_equal(outs[0][4][1], outs[1][4][1])
+
+
 def test_tile_shapes_give_identical_angles():
     res = []
     for tile in ((16, 16, MARCH), (4, 8, MARCH), (5, 3, MARCH), (2, 4, MARCH), (8, 8, BLOCK),
