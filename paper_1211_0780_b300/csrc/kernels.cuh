@@ -345,11 +345,12 @@ __device__ __forceinline__ void finish_slot_and_exchange(const Lattice* lats, in
   if (lane == 0) fp.done[lo] = 0;
 }
 
-// Per-launch finishing step: one warp (block of 32 threads) per slot of
-// every lattice, so the FP64 sums of all slots run on as many SMs.
-__global__ void k_finish(const Lattice* lats, int n_lat, FinishParams fp) {
+// Per-launch finishing step: one warp (block of 32 threads) per slot, for
+// the slots g0, g0 + 1, ... (all of them, or one lattice's), so the FP64 sums
+// of the slots run on as many SMs.
+__global__ void k_finish(const Lattice* lats, int n_lat, FinishParams fp, int g0) {
   chain_wait_and_release();
-  finish_slot_and_exchange(lats, n_lat, fp, blockIdx.x, threadIdx.x & 31);
+  finish_slot_and_exchange(lats, n_lat, fp, g0 + static_cast<int>(blockIdx.x), threadIdx.x & 31);
 }
 
 __global__ void k_advance(uint64_t* ctr, uint64_t d_mpass, uint64_t d_sweep, uint64_t d_swap,

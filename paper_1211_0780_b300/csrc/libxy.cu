@@ -431,9 +431,10 @@ FinishParams finish_params(xy_ctx* c) {
   return f;
 }
 
-int launch_finish(xy_ctx* c, cudaStream_t st, const FinishParams& f) {
-  XY_TRY(c, launch_chained(k_finish, dim3(c->n_slots), dim3(32), 0, st,
-                           static_cast<const Lattice*>(c->at<Lattice>(c->lay.lats)), c->n_lat, f));
+// The finishing step of slots [g0, g0 + n) (every slot: 0, n_slots).
+int launch_finish(xy_ctx* c, cudaStream_t st, const FinishParams& f, int g0, int n) {
+  XY_TRY(c, launch_chained(k_finish, dim3(n), dim3(32), 0, st,
+                           static_cast<const Lattice*>(c->at<Lattice>(c->lay.lats)), c->n_lat, f, g0));
   return XY_OK;
 }
 
@@ -445,21 +446,35 @@ struct BlockCounts {
 
 // Issues `ns` sweeps starting at host sweep index s0, relative to the device
 // counters, followed by the counter advance.  No synchronisation.
+// Lattices share nothing within a call (each has its own ladder, partial
+// sums, records and words), so with several lattices each runs all of its
+// sweeps, finishing steps and exchanges included, on its own stream: one
+// fork and one join per call, and no lattice waits for another's sweep.
 int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, int se, uint64_t s0,
                  BlockCounts* out) {
-  BlockCounts bc;
+  // the call's counter offsets at the start of each sweep (at[ns]: the total)
+  std::vector<BlockCounts> at(static_cast<size_t>(ns) + 1);
   for (int j = 0; j < ns; ++j) {
     const uint64_t s = s0 + j;
-    const bool meas = due(s, me), swp = due(s, se);
-    const bool needE = meas || swp;
-    const int n_pass = nM + nOR;
-    const bool branches = c->n_lat > 1;
-    if (branches) {
-      XY_TRY(c, cudaEventRecord(c->fork_ev, st));
-      for (int i = 0; i < c->n_lat; ++i) XY_TRY(c, cudaStreamWaitEvent(c->lat_streams[i], c->fork_ev, 0));
-    }
-    for (int i = 0; i < (branches ? c->n_lat : 1); ++i) {
-      uint64_t mp = bc.mpass;
+    at[j + 1] = at[j];
+    at[j + 1].mpass += nM;
+    at[j + 1].sweeps += 1;
+    at[j + 1].records += due(s, me) ? 1 : 0;
+    at[j + 1].swaps += due(s, se) ? 1 : 0;
+  }
+  const int n_pass = nM + nOR;
+  const bool branches = c->n_lat > 1;
+  if (branches) {
+    XY_TRY(c, cudaEventRecord(c->fork_ev, st));
+    for (int i = 0; i < c->n_lat; ++i) XY_TRY(c, cudaStreamWaitEvent(c->lat_streams[i], c->fork_ev, 0));
+  }
+  for (int i = 0; i < (branches ? c->n_lat : 1); ++i) {
+    cudaStream_t ls = branches ? c->lat_streams[i] : st;
+    for (int j = 0; j < ns; ++j) {
+      const uint64_t s = s0 + j;
+      const bool meas = due(s, me), swp = due(s, se);
+      const bool needE = meas || swp;
+      uint64_t mp = at[j].mpass;
       for (int p = 0; p < n_pass; ++p) {
         const bool last = (p == n_pass - 1);
         for (int colour = 0; colour < 2; ++colour) {
@@ -481,41 +496,39 @@ int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, in
           if (p >= nM && nM > 0 && j + 1 < ns && k >= 1 && k <= 2 * nOR - 2 && !measure) {
             wp.part = k - 1;
             wp.parts = 2 * nOR - 2;
-            wp.mpass = bc.mpass + nM;
+            wp.mpass = at[j].mpass + nM;
           }
           int rc;
           if (branches)
-            rc = p < nM ? launch_half<kMetropolis>(c, c->lat_streams[i], i, colour, pp, wp)
-                        : launch_half<kOverrelax>(c, c->lat_streams[i], i, colour, pp, wp);
+            rc = p < nM ? launch_half<kMetropolis>(c, ls, i, colour, pp, wp)
+                        : launch_half<kOverrelax>(c, ls, i, colour, pp, wp);
           else
-            rc = p < nM ? launch_half_all<kMetropolis>(c, st, colour, pp, wp)
-                        : launch_half_all<kOverrelax>(c, st, colour, pp, wp);
+            rc = p < nM ? launch_half_all<kMetropolis>(c, ls, colour, pp, wp)
+                        : launch_half_all<kOverrelax>(c, ls, colour, pp, wp);
           if (rc != XY_OK) return rc;
         }
         if (p < nM) mp += 1;
       }
-    }
-    if (branches) {
-      for (int i = 0; i < c->n_lat; ++i) {
-        XY_TRY(c, cudaEventRecord(c->join_ev[i], c->lat_streams[i]));
-        XY_TRY(c, cudaStreamWaitEvent(st, c->join_ev[i], 0));
+      if (needE) {
+        FinishParams f = finish_params(c);
+        f.sweep_off = at[j].sweeps;
+        f.series_off = at[j].records;
+        f.swap_off = at[j].swaps;
+        f.record = meas ? 1 : 0;
+        f.swap = swp ? 1 : 0;
+        const int rc = branches ? launch_finish(c, ls, f, c->lat[i].slot0, c->lat[i].R)
+                                : launch_finish(c, ls, f, 0, c->n_slots);
+        if (rc != XY_OK) return rc;
       }
     }
-    bc.mpass += nM;
-    if (needE) {
-      FinishParams f = finish_params(c);
-      f.sweep_off = bc.sweeps;
-      f.series_off = bc.records;
-      f.swap_off = bc.swaps;
-      f.record = meas ? 1 : 0;
-      f.swap = swp ? 1 : 0;
-      const int rc = launch_finish(c, st, f);
-      if (rc != XY_OK) return rc;
-    }
-    bc.sweeps += 1;
-    bc.records += meas ? 1 : 0;
-    bc.swaps += swp ? 1 : 0;
   }
+  if (branches) {
+    for (int i = 0; i < c->n_lat; ++i) {
+      XY_TRY(c, cudaEventRecord(c->join_ev[i], c->lat_streams[i]));
+      XY_TRY(c, cudaStreamWaitEvent(st, c->join_ev[i], 0));
+    }
+  }
+  const BlockCounts& bc = at[ns];
   XY_TRY(c, launch_chained(k_advance, dim3(1), dim3(1), 0, st, c->ctr(), bc.mpass, bc.sweeps, bc.swaps,
                            bc.records, bc.records));
   if (out) *out = bc;
@@ -847,7 +860,7 @@ static int measure_now(xy_ctx* c, int swap, int parity) {
   f.swap = swap;
   f.parity = parity;
   f.n_swapped = swap ? c->at<int>(c->lay.nswapped) : nullptr;
-  return launch_finish(c, c->stream, f);
+  return launch_finish(c, c->stream, f, 0, c->n_slots);
 }
 
 int xy_measure(xy_ctx* c, xy_record* out) {
