@@ -169,9 +169,11 @@ __device__ __forceinline__ void draw_words(const Lattice& lat, const PassParams&
 // WG: 1, a Metropolis half-sweep that reads its pass's words (pp.words)
 // instead of drawing them; 2, an over-relaxation half-sweep that also draws
 // calls of the next Metropolis pass's words (before griddepcontrol.wait in
-// library-chained launches: no launch in flight reads them).
-template <int MODE, bool MEAS, int LC, int WG = 0>
-__global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDirectMaxRegs) k_half_direct(Lattice lat, int colour, PassParams pp) {
+// library-chained launches: no launch in flight reads them).  EO: the
+// measuring variant sums the energy alone (an exchange that records
+// nothing), at the plain over-relaxation kernel's register limit.
+template <int MODE, bool MEAS, int LC, int WG = 0, bool EO = false>
+__global__ void __maxnreg__(MODE == kOverrelax && (!MEAS || EO) ? kDirectMaxRegsOR : kDirectMaxRegs) k_half_direct(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   if (!pp.own_ready) chain_wait_and_release();  // else tile_direct waits after its own-colour loads
   if (WG == 2) draw_words(lat, pp);
@@ -182,7 +184,7 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDi
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
-  tile_direct<MODE, MEAS, LC, WG == 1>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
+  tile_direct<MODE, MEAS, LC, WG == 1, EO ? 1 : 0>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, pp, acc, n_acc);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nth = blockDim.x * blockDim.y;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);
@@ -194,9 +196,12 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kDirectMaxRegsOR : kDi
 
 // One half-sweep of one lattice with the kTileAngle tile (angle storage):
 // grid (tiles per slot, R), block (L/8, ty); shared memory: the tile's
-// plane buffers, then the reduction area of the measuring variant.
-template <int MODE, bool MEAS>
-__global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kAngleMaxRegsOR : kDirectMaxRegs) k_half_angle(Lattice lat, int colour, PassParams pp) {
+// plane buffers, then the reduction area of the measuring variant.  EO:
+// the measuring variant sums the energy alone (an exchange that records
+// nothing); with that sum the over-relaxation kernel keeps the plain one's
+// register limit.
+template <int MODE, bool MEAS, bool EO = false>
+__global__ void __maxnreg__(MODE == kOverrelax && (!MEAS || EO) ? kAngleMaxRegsOR : kDirectMaxRegs) k_half_angle(Lattice lat, int colour, PassParams pp) {
   extern __shared__ __align__(16) float sm[];
   if (!pp.own_ready) chain_wait_and_release();  // else tile_angle waits after its own-colour loads
   const int r = blockIdx.y;
@@ -206,7 +211,7 @@ __global__ void __maxnreg__(MODE == kOverrelax && !MEAS ? kAngleMaxRegsOR : kDir
 #pragma unroll
   for (int j = 0; j < kNumSums; ++j) acc[j] = 0.f;
   uint32_t n_acc = 0u;
-  tile_angle<MODE, MEAS>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
+  tile_angle<MODE, MEAS, EO ? 1 : 0>(lat, r, yt, zt, colour, threadIdx.x, threadIdx.y, true, pp, sm, acc, n_acc);
   const int tid = threadIdx.x + blockDim.x * threadIdx.y;
   const int nth = blockDim.x * blockDim.y;
   if (MODE == kMetropolis) block_count_to(pp.acc_met + lat.slot0 + r, n_acc, tid, nth);

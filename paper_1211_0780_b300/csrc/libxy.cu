@@ -317,6 +317,8 @@ cudaError_t launch_direct(dim3 grid, dim3 block, int smem, cudaStream_t st, cons
   static_assert(sizeof(kDirectSizes) / sizeof(kDirectSizes[0]) == 5, "one case per fixed size");
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
   if (MODE == kMeasureOnly) return launch_chained(k_half_direct<kMeasureOnly, true, LC>, grid, block, smem, st, d, colour, pp);
+  if (pp.measure == 2 && colour == 1)
+    return launch_chained(k_half_direct<M, true, LC, 0, true>, grid, block, smem, st, d, colour, pp);
   if (pp.measure && colour == 1) return launch_chained(k_half_direct<M, true, LC>, grid, block, smem, st, d, colour, pp);
   if (MODE == kMetropolis && pp.words && pp.words_read)
     return launch_chained(k_half_direct<M, false, LC, 1>, grid, block, smem, st, d, colour, pp);
@@ -331,6 +333,8 @@ cudaError_t launch_angle(dim3 grid, dim3 block, int smem, cudaStream_t st, const
                          const PassParams& pp) {
   constexpr int M = MODE == kMeasureOnly ? kOverrelax : MODE;
   if (MODE == kMeasureOnly) return launch_chained(k_half_angle<kMeasureOnly, true>, grid, block, smem, st, d, colour, pp);
+  if (pp.measure == 2 && colour == 1)
+    return launch_chained(k_half_angle<M, true, true>, grid, block, smem, st, d, colour, pp);
   if (pp.measure && colour == 1) return launch_chained(k_half_angle<M, true>, grid, block, smem, st, d, colour, pp);
   return launch_chained(k_half_angle<M, false>, grid, block, smem, st, d, colour, pp);
 }
@@ -478,7 +482,9 @@ int issue_sweeps(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns, int me, in
       for (int p = 0; p < n_pass; ++p) {
         const bool last = (p == n_pass - 1);
         for (int colour = 0; colour < 2; ++colour) {
-          const int measure = (needE && last && colour == 1) ? 1 : 0;
+          // the sweep's last half-sweep measures: every sum when it records,
+          // the energy alone when it only exchanges
+          const int measure = (needE && last && colour == 1) ? (meas ? 1 : 2) : 0;
           PassParams pp = c->pass_params(true, p < nM ? mp : 0, measure);
           // Every half-sweep of a sweep but the first is chained behind the
           // other colour's half-sweep on the same stream (see tile_direct).
@@ -704,16 +710,20 @@ int xy_init(xy_ctx** out, int n_lattices, const int* L, const int* n_replicas, c
   // The kTileDirect and kTileAngle kernels: their own block limit
   // (kDirectMaxThreads); the angle tile keeps its plane buffers in shared
   // memory (up to ~50 KB at L = 1024).
-  const void* direct_kernels[10] = {
+  const void* direct_kernels[14] = {
       reinterpret_cast<const void*>(k_half_direct<kMetropolis, false, 0>),
       reinterpret_cast<const void*>(k_half_direct<kMetropolis, true, 0>),
       reinterpret_cast<const void*>(k_half_direct<kOverrelax, false, 0>),
       reinterpret_cast<const void*>(k_half_direct<kOverrelax, true, 0>),
+      reinterpret_cast<const void*>(k_half_direct<kMetropolis, true, 0, 0, true>),
+      reinterpret_cast<const void*>(k_half_direct<kOverrelax, true, 0, 0, true>),
       reinterpret_cast<const void*>(k_half_direct<kMeasureOnly, true, 0>),
       reinterpret_cast<const void*>(k_half_angle<kMetropolis, false>),
       reinterpret_cast<const void*>(k_half_angle<kMetropolis, true>),
       reinterpret_cast<const void*>(k_half_angle<kOverrelax, false>),
       reinterpret_cast<const void*>(k_half_angle<kOverrelax, true>),
+      reinterpret_cast<const void*>(k_half_angle<kMetropolis, true, true>),
+      reinterpret_cast<const void*>(k_half_angle<kOverrelax, true, true>),
       reinterpret_cast<const void*>(k_half_angle<kMeasureOnly, true>)};
   for (const void* fn : direct_kernels) {
     e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -1372,6 +1382,9 @@ cudaError_t issue_persistent(xy_ctx* c, cudaStream_t st, int nM, int nOR, int ns
         // the pass counter offset of the launch's first pass (the kernel
         // adds the later passes' index)
         a.pp.mpass_off = part == kPartMetropolis ? static_cast<uint64_t>(s) * nM + (fin ? n_pass - 1 : 0) : 0ull;
+        // the finishing launch's half-sweep measures every sum when the
+        // sweep records, the energy alone when it only exchanges
+        a.pp.measure = fin ? (meas ? 1 : 2) : 0;
         const int q = n_launch & 1;
         a.work = work[q];
         a.work0 = work_base[q];

@@ -140,7 +140,9 @@ struct PassParams {
   const float* beta_slot;       // FP32 beta of every global slot
   double* partials;             // [tiles][kNumSums], written when measuring
   unsigned long long* acc_met;  // accepted proposals per global slot
-  int measure;                  // fuse the lattice sums (white passes only)
+  int measure;                  // fuse the lattice sums (white passes only):
+                                // 1 all of them, 2 the energy alone (an
+                                // exchange that records nothing)
   int poison;                   // test hook (kTileStream): plane 2 is never copied
   int own_ready;                // kTileDirect launches chained by the library: the
                                 // own colour and the pass counter are final before
@@ -432,12 +434,13 @@ __device__ __forceinline__ void reflect2(float2 hx, float2 hy, float2 c, float2 
 // proposal's where accepted, 2 phi - theta (reflect_angle2) where reflected,
 // the old angle elsewhere (also where the field is zero); the new spins n
 // are then the vectors of those angles when measuring (o is not read by
-// the over-relaxation update).
+// the over-relaxation update).  e_only (measuring): the energy's term alone.
 template <int MODE, bool MEAS, bool ANG = false>
 __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int s, const Spins4& ym,
                                         const Spins4& yp, const Spins4& zm, const Spins4& zp, const Spins4& o,
                                         const uint4& w0, const uint4& w1, float beta, Spins4& n, uint32_t& n_acc,
-                                        float* stepv, const float4* oa = nullptr, float4* na = nullptr) {
+                                        float* stepv, const float4* oa = nullptr, float4* na = nullptr,
+                                        bool e_only = false) {
   float2 nang[2];
   float Xc[5], Xs[5];
 #pragma unroll
@@ -511,7 +514,15 @@ __device__ __forceinline__ void update4(const Spins4& z, float hc, float hs, int
     // as a later measure-only pass forms them
     if (MEAS) n = spins_of_angles(*na);
   }
-  if (MEAS) {
+  if (MEAS && e_only) {
+    // The energy alone (Eq. 1; an exchange that records nothing): the same
+    // bonds as C_x + C_y + C_z below, grouped by white site, w . h with h the
+    // sum of its six neighbours (the field of the update), in slot 2 (the
+    // other slots stay 0; the finishing step takes E = -(slots 2 + 3 + 4)).
+    const float2 t = __ffma2_rn(hi2(n.c), hx[1], __ffma2_rn(hi2(n.s), hy[1], __ffma2_rn(lo2(n.c), hx[0],
+                                __fmul2_rn(lo2(n.s), hy[0]))));
+    stepv[2] += t.x + t.y;
+  } else if (MEAS) {
     // Bonds (w, w+mu) and (w-mu, w) of the white site w: every bond has
     // exactly one white end, so each is counted once.  C_mu: cos of the
     // bond's angle difference, w . (w+mu + w-mu); S_mu: sin,
@@ -661,7 +672,8 @@ __device__ __forceinline__ void tile_pass(const Lattice& lat, int r, int yt, int
 #pragma unroll
       for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
       Spins4 nw;
-      update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
+      update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv, nullptr, nullptr,
+                          pp.measure == 2);
       if (MEAS) sums.add_plane(stepv);
       if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
     }
@@ -704,7 +716,8 @@ __device__ __forceinline__ float ld1_l1(const SpinGuard& g, const float* p) {
 // return at once.  acc_out / n_acc as tile_pass.  LC > 0: the lattice size
 // fixed at compile time (it must equal lat.L), so that plane strides and the
 // cos-to-sin offset are constants folded into the addressing.
-template <int MODE, bool MEAS, int LC = 0, bool WORDS = false>
+// EO (measuring): 1 the energy alone, 0 every sum, -1 as pp.measure says.
+template <int MODE, bool MEAS, int LC = 0, bool WORDS = false, int EO = -1>
 __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, int zt, int colour, int tx,
                                             int ty, const PassParams& pp, float* acc_out, uint32_t& n_acc, uint32_t pass_add = 0) {
   static_assert(MODE != kMeasureOnly || MEAS, "measure-only pass measures");
@@ -826,7 +839,7 @@ __device__ __forceinline__ void tile_direct(const Lattice& lat, int r, int yt, i
     for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
     Spins4 nw;
     update4<MODE, MEAS>(zc, cur.hc, cur.hs, s, cur.ym, cur.yp, zm, zn, cur.own, cur.w0, cur.w1, beta, nw, n_acc,
-                        stepv);
+                        stepv, nullptr, nullptr, EO > 0 || (EO < 0 && pp.measure == 2));
     if (MEAS) sums.add_plane(stepv);
     if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
   };
@@ -876,7 +889,8 @@ __device__ __forceinline__ void st_ang(const SpinGuard& g, float* p, const float
 // Arguments as tile_pass; every thread of the block must call it (it
 // contains barriers).  Library-chained launches (pp.own_ready) load the own
 // colour's first plane before griddepcontrol.wait, as tile_direct does.
-template <int MODE, bool MEAS>
+// EO (measuring): 1 the energy alone, 0 every sum, -1 as pp.measure says.
+template <int MODE, bool MEAS, int EO = -1>
 __device__ __forceinline__ void tile_angle(const Lattice& lat, int r, int yt, int zt, int colour, int tx, int ty,
                                            bool in_block, const PassParams& pp, float* sm, float* acc_out,
                                            uint32_t& n_acc, uint32_t pass_add = 0) {
@@ -986,7 +1000,7 @@ __device__ __forceinline__ void tile_angle(const Lattice& lat, int r, int yt, in
       Spins4 nw;
       float4 na;
       update4<MODE, MEAS, true>(zc, hc, hs, s, ysm, ysp, zm, zn, spins_of_angles(t_own), w0, w1, beta, nw, n_acc,
-                                stepv, &t_own, &na);
+                                stepv, &t_own, &na, EO > 0 || (EO < 0 && pp.measure == 2));
       if (MEAS) sums.add_plane(stepv);
       if (MODE != kMeasureOnly) st_ang(sg, own + offz, na);
     }
@@ -1248,7 +1262,8 @@ __device__ __forceinline__ void tile_stream(const Lattice& lat, int r, int yt, i
 #pragma unroll
         for (int q = 0; q < kNumSums; ++q) stepv[q] = 0.f;
         Spins4 nw;
-        update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv);
+        update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zm, zn, t_own, w0, w1, beta, nw, n_acc, stepv, nullptr,
+                            nullptr, pp.measure == 2);
         if (MEAS) sums.add_plane(stepv);
         if (MODE != kMeasureOnly) st_spins(sg, own + offz, half, nw.c, nw.s);
       }
@@ -1360,7 +1375,8 @@ __device__ __forceinline__ void tile_block(const Lattice& lat, int r, int yt, in
 #pragma unroll
     for (int j = 0; j < kNumSums; ++j) stepv[j] = 0.f;
     Spins4 nw;
-    update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zsm, zsp, t_own, w0, w1, beta, nw, n_acc, stepv);
+    update4<MODE, MEAS>(zc, hc, hs, s, ysm, ysp, zsm, zsp, t_own, w0, w1, beta, nw, n_acc, stepv, nullptr, nullptr,
+                        pp.measure == 2);
     if (MEAS) {
 #pragma unroll
       for (int j = 0; j < kNumSums; ++j) acc_out[j] = stepv[j];
