@@ -146,7 +146,10 @@ int xy_set_exec(xy_ctx *ctx, int mode);
  *     half-sweep);
  *   - if pt_swap_every > 0 and (s + 1) % pt_swap_every == 0, one exchange
  *     event runs on every ladder with the energies of the final state
- *     (Sec. II, Eq. 3), alternating even and odd pairs between events.
+ *     (Sec. II, Eq. 3), alternating even and odd pairs between events; a
+ *     sweep that exchanges without recording sums the energy alone, as
+ *     -E = sum over white sites of w . h (h the six neighbours' sum: the
+ *     same bonds as the record's C_x + C_y + C_z, in another order).
  * Metropolis half-sweep (Sec. II): each site of the colour proposes
  * theta' = 2 pi u0 and accepts iff u1 < exp(-beta dE), with dE = -[h_x
  * (cos theta' - cos theta) + h_y (sin theta' - sin theta)] and h the sum of
