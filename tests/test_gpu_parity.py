@@ -569,6 +569,42 @@ def test_pt_swap_parity():
     assert decided >= 10
 
 
+@pytest.mark.parametrize("kind,tile", [(0, (8, 4)), (1, (4, 4)), (3, (8, 4)), (4, (8, 4))])
+def test_exchange_in_sweep_on_the_energy_alone(kind, tile):
+    """A sweep that exchanges without recording sums the energy alone
+    (-E = sum over white sites of w . h) in its last half-sweep; the
+    exchange it then makes (Eq. 3) agrees, event by event, with the oracle's
+    decision on the FP64 energies of the swept state, on each tile kind
+    (march, block, direct, angle storage).  Near-ties are skipped with a
+    margin of 2e-5 on |u - W|: at 16^3 the FP32 energy of 2048 white sites
+    is within ~2e-5 of the FP64 one, times |beta_k - beta_k+1| = 0.06."""
+    betas = np.array([0.30, 0.36, 0.42, 0.48, 0.54])
+    L = 16
+    s = sim(L, 5, betas)
+    s.set_tile(0, tile[0], tile[1], kind)
+    s.sweep(1, 1, 6)
+    decided = 0
+    for event in range(14):
+        _, perm0, ctr0 = s.get_state()
+        n_ev = int(ctr0[2])
+        s.sweep(1, 1, 1, measure_every=0, pt_swap_every=1)
+        _, perm1, ctr1 = s.get_state()
+        assert int(ctr1[2]) == n_ev + 1
+        E = np.array([oracle.measure(a).E for a in stored_angles64(s)])
+        parity = n_ev & 1
+        p_ref = perm0.astype(np.int32).copy()
+        oracle.pt_swap(betas, E, p_ref, SEED, 0, n_ev, parity)
+        tie = False
+        for k in range(parity, 4, 2):
+            a, b = perm0[k], perm0[k + 1]
+            w = min(1.0, np.exp((betas[k] - betas[k + 1]) * (E[a] - E[b])))
+            tie |= abs(oracle.pt_uniform(SEED, 0, n_ev, k) - w) < 2e-5
+        if not tie:
+            assert np.array_equal(perm1, p_ref), (event, perm0, perm1, p_ref)
+            decided += 1
+    assert decided >= 10
+
+
 def test_direct_tile_matches_march_tile_bit_for_bit():
     """The direct tile (neighbours through L1, no block barrier) and the
     march tile of the same shape give the same angles, permutations,
