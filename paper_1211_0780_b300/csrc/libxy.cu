@@ -1239,12 +1239,16 @@ int xy_device_status(xy_ctx* c, int* status_out) {
 namespace {
 
 // The persistent kernel of one tile kind, sweep part and finishing flag.
-const void* persistent_kernel(int kind, int part, bool fin) {
-#define XY_PK(K)                                                                                        \
-  (part == kPartMetropolis ? (fin ? reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis, true>)  \
-                                  : reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis, false>)) \
-   : fin                   ? reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax, true>)        \
-                           : reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax, false>))
+// eo (fin): the finishing launch of a sweep that only exchanges.
+const void* persistent_kernel(int kind, int part, bool fin, bool eo) {
+#define XY_PK(K)                                                                                              \
+  (part == kPartMetropolis                                                                                    \
+       ? (fin ? (eo ? reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis, true, true>)             \
+                    : reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis, true>))                  \
+              : reinterpret_cast<const void*>(k_persistent<K, kPartMetropolis, false>))                       \
+   : fin ? (eo ? reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax, true, true>)                   \
+               : reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax, true>))                        \
+         : reinterpret_cast<const void*>(k_persistent<K, kPartOverrelax, false>))
   return kind == kTileBlock    ? XY_PK(kTileBlock)
          : kind == kTileDirect ? XY_PK(kTileDirect)
          : kind == kTileAngle  ? XY_PK(kTileAngle)
@@ -1272,8 +1276,9 @@ int build_plan(xy_ctx* c) {
   // Every part's kernel runs on the same grid and item plan: the grid is
   // sized by the part that keeps the fewest blocks per SM.
   int nb = 1 << 30;
-  for (int v = 0; v < 4; ++v) {
-    const void* fn = persistent_kernel(kind, v >> 1, (v & 1) != 0);
+  for (int v = 0; v < 6; ++v) {  // (part, fin) = (v >> 1, v & 1); v = 4, 5: the energy-only finishing parts
+    const void* fn = v < 4 ? persistent_kernel(kind, v >> 1, (v & 1) != 0, false)
+                           : persistent_kernel(kind, v - 4, true, true);
     cudaFuncAttributes fa{};
     XY_TRY(c, cudaFuncGetAttributes(&fa, fn));
     if (B > fa.maxThreadsPerBlock) return XY_ERR_ARG;  // a tile wider than one persistent block
@@ -1335,6 +1340,7 @@ PersistentArgs persistent_args(xy_ctx* c) {
 // previous launch's blocks leave; the slot counts order the work).
 cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& a, int part, bool fin,
                               bool chained) {
+  const bool eo = fin && a.pp.measure == 2;  // a finishing launch that sums the energy alone
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3(c->plan.G);
   cfg.blockDim = dim3(c->plan.B);
@@ -1346,7 +1352,7 @@ cudaError_t launch_persistent(xy_ctx* c, cudaStream_t st, const PersistentArgs& 
   cfg.attrs = attr;
   cfg.numAttrs = chained ? 1 : 0;
   void* args[] = {const_cast<PersistentArgs*>(&a)};
-  return cudaLaunchKernelExC(&cfg, persistent_kernel(c->plan.kind, part, fin), args);
+  return cudaLaunchKernelExC(&cfg, persistent_kernel(c->plan.kind, part, fin, eo), args);
 }
 
 // Issues the persistent launches of `ns` sweeps starting at host sweep

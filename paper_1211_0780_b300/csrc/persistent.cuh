@@ -208,10 +208,12 @@ __device__ __noinline__ void finish_items(const PersistentArgs& a, long long it,
 // at most 256 threads, and each part's kernel is compiled for the blocks per
 // SM its kind keeps: the block kind three (at most 80 registers), the march,
 // the direct and the angle kinds two (at most 128).  FIN: the launch ends a
-// measured or exchanging sweep.
+// measured or exchanging sweep; EO (FIN): the sweep only exchanges, and the
+// direct and angle kinds' half-sweep sums the energy alone (the other kinds
+// read that from pp.measure).
 constexpr int kPersistentBlockThreads = 256;
 
-template <int KIND, int PART, bool FIN>
+template <int KIND, int PART, bool FIN, bool EO = false>
 __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 3 : 2)
     k_persistent(PersistentArgs a) {
   extern __shared__ __align__(16) float sm[];
@@ -276,9 +278,10 @@ __global__ void __launch_bounds__(kPersistentBlockThreads, KIND == kTileBlock ? 
       tile_block<MODE, FIN>(lat, w.y, yt, zt, colour, tx, ty, tz, tz < lat.tz, pp, sm, acc, n_acc, pass_add);
     } else if (KIND == kTileDirect) {
       // threads beyond the tile's rows return at once
-      tile_direct<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc, pass_add);
+      tile_direct<MODE, FIN, 0, false, EO ? 1 : 0>(lat, w.y, yt, zt, colour, tx, rest, pp, acc, n_acc, pass_add);
     } else if (KIND == kTileAngle) {
-      tile_angle<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc, pass_add);
+      tile_angle<MODE, FIN, EO ? 1 : 0>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc,
+                                        pass_add);
     } else {
       tile_pass<MODE, FIN>(lat, w.y, yt, zt, colour, tx, rest, rest < lat.ty, pp, sm, acc, n_acc, pass_add);
     }
