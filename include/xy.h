@@ -337,18 +337,23 @@ int xy_get_tile(xy_ctx *ctx, int lattice, int *kind, int *ty, int *tz);
 
 /* Picks each lattice's tile (kind and shape) by timing the candidates on
  * the device for sweeps of `n_metropolis` + `n_overrelax` passes (the spins,
- * counters and accept counts are saved and restored); the choice stays in
- * the context.  Outside XY_EXEC_PERSISTENT every kind (0-3) is a
- * candidate, and kind 4 too when the context's vector state is larger than
- * the device's L2 cache (there a half-sweep is bound by HBM bytes, which
- * angle storage halves).  In XY_EXEC_PERSISTENT mode one tile kind serves
- * every lattice (xy_sweep returns XY_ERR_ARG otherwise) and the block is as
- * wide as the widest tile: for the march, the block, the direct (and, as
- * above, the angle) kind and for tiles of at most 64, 128 and 256 threads,
- * each lattice's best tile is found as above, and the sets are timed in the
- * persistent launch itself (on sweeps that end with an exchange when a
- * ladder has two or more replicas; the ladders' permutations, couplings and
- * exchange counts are saved and restored too); the fastest is kept. */
+ * counters, accept counts and the ladders' permutations, couplings and
+ * exchange counts are saved and restored); the choice stays in the
+ * context.  Outside XY_EXEC_PERSISTENT every kind (0-3) is a candidate,
+ * and kind 4 too when the context's vector state is larger than the
+ * device's L2 cache (there a half-sweep is bound by HBM bytes, which angle
+ * storage halves); each lattice's best tile is found on its own half-sweep
+ * launches.  In XY_EXEC_PERSISTENT mode one tile kind serves every lattice
+ * (xy_sweep returns XY_ERR_ARG otherwise) and the block is as wide as the
+ * widest tile: for the march, the block, the direct (and, as above, the
+ * angle) kind and for tiles of at most 64, 128 and 256 threads, each
+ * lattice's best tile is found as above, the sets are timed in the
+ * persistent launch itself, and the fastest is kept.  In every mode the
+ * kept set is then refined on whole sweeps of all lattices together, in
+ * the context's execution mode (ending with an exchange when a ladder has
+ * two or more replicas): lattice by lattice, largest first, a tile's rows
+ * or planes doubled or halved, a change kept when it is at least 1%
+ * faster. */
 int xy_autotune(xy_ctx *ctx, int n_metropolis, int n_overrelax);
 
 /* Device-side status word of the last persistent launch (0 = fine). */

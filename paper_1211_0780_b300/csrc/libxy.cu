@@ -1610,71 +1610,56 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
     }
     h = best_h;
   };
-  if (!persistent) {
-    for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, 0, kind_end, c->max_block);
-  } else {
-    // One tile kind and one block size serve every lattice of a persistent
-    // launch (the block is as wide as the widest tile): for each kind (not
-    // the stream kind) and each cap on the tile's threads (64, 128, 256),
-    // take each lattice's best tile under the cap, then time the persistent
-    // launch itself with each set and keep the fastest.
-    const int kinds[4] = {kTileMarch, kTileBlock, kTileDirect, kTileAngle};
-    const int n_sets = 3 * (allow_angle ? 4 : 3);
-    std::vector<std::vector<LatHost>> sets(n_sets);
-    const std::vector<LatHost> start = c->lat;
-    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
-      const int kind = kinds[q / 3], cap = 64 << (q % 3);
-      c->lat = start;
-      for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, kind, kind + 1, cap);
-      sets[q] = c->lat;
+  // Whole sweeps are timed on sweeps that end with an exchange when a ladder
+  // has two or more replicas (parallel tempering; the finishing step's cost
+  // differs between kinds and shapes), else on plain sweeps, in the
+  // context's execution mode.
+  int swap_every = 0;
+  for (const LatHost& h : c->lat) swap_every = h.R > 1 ? 1 : swap_every;
+  auto two_sweeps = [&]() -> int {
+    if (persistent) return persistent_sweeps(c, nM, nOR, 2, 0, swap_every);
+    if (exec == XY_EXEC_GRAPH) {
+      c->exec = XY_EXEC_GRAPH;
+      const int r = xy_sweep(c, nM, nOR, 2, 0, swap_every);
+      c->exec = XY_EXEC_PLAIN;
+      return r;
     }
-    // the sets are timed on sweeps that end with an exchange when a ladder
-    // has two or more replicas (parallel tempering; the finishing launch's
-    // cost differs between kinds), else on plain sweeps
-    int swap_every = 0;
-    for (const LatHost& h : c->lat) swap_every = h.R > 1 ? 1 : swap_every;
-    // Time of two persistent sweeps with a set: the untimed call builds the
-    // call's graph (capture and instantiation are host work that would
-    // otherwise fall inside the timed region), then the faster of two timed
-    // replays; 1e30 for a set the persistent kernel cannot run.
-    auto time_set = [&](const std::vector<LatHost>& set) -> float {
-      c->lat = set;
-      for (int i = 0; i < c->n_lat; ++i) ensure_storage(i, c->lat[i].kind);
-      if (rc != XY_OK) return 1e30f;
-      drop_graphs(c);
-      if ((rc = sync_lats(c)) != XY_OK) return 1e30f;
-      if (persistent_sweeps(c, nM, nOR, 2, 0, swap_every) != XY_OK) {
-        rc = c->sticky;
-        return 1e30f;
-      }
-      float ms = 1e30f;
-      for (int round = 0; round < 2 && rc == XY_OK; ++round) {
-        if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = fail_cuda(c, cudaGetLastError(), "autotune"); break; }
-        if ((rc = persistent_sweeps(c, nM, nOR, 2, 0, swap_every)) != XY_OK) break;
-        float t = 0.f;
-        if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
-            cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
-          rc = fail_cuda(c, cudaGetLastError(), "autotune");
-          break;
-        }
-        ms = std::min(ms, t);
-      }
-      return ms;
-    };
-    float best = 1e30f;
-    int best_q = n_sets - 1;
-    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
-      const float ms = time_set(sets[q]);
-      if (rc == XY_OK && ms < best) {
-        best = ms;
-        best_q = q;
-      }
+    return issue_sweeps(c, c->stream, nM, nOR, 2, 0, swap_every, c->h_ctr[kCtrSweep], nullptr);
+  };
+  // Time of two sweeps with a set of tiles: an untimed call first (it
+  // builds the call's graph: capture and instantiation are host work that
+  // would otherwise fall inside the timed region), then the faster of two
+  // timed calls; 1e30 for a set the execution mode cannot run.
+  auto time_set = [&](const std::vector<LatHost>& set) -> float {
+    c->lat = set;
+    for (int i = 0; i < c->n_lat; ++i) ensure_storage(i, c->lat[i].kind);
+    if (rc != XY_OK) return 1e30f;
+    drop_graphs(c);
+    if ((rc = sync_lats(c)) != XY_OK) return 1e30f;
+    if (two_sweeps() != XY_OK) {
+      rc = c->sticky;
+      return 1e30f;
     }
-    // The shapes came from per-launch timings: refine the kept set in the
-    // persistent launch itself, one lattice at a time (largest first), by
-    // doubling or halving its tile's rows or planes, keeping a change that
-    // is at least 1% faster.
-    std::vector<LatHost> cur = sets[best_q];
+    float ms = 1e30f;
+    for (int round = 0; round < 2 && rc == XY_OK; ++round) {
+      if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = fail_cuda(c, cudaGetLastError(), "autotune"); break; }
+      if ((rc = two_sweeps()) != XY_OK) break;
+      float t = 0.f;
+      if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
+        rc = fail_cuda(c, cudaGetLastError(), "autotune");
+        break;
+      }
+      ms = std::min(ms, t);
+    }
+    return ms;
+  };
+  // The shapes come from per-launch timings of one lattice at a time:
+  // refine a set on whole sweeps of every lattice together, one lattice at
+  // a time (largest first), by doubling or halving its tile's rows or
+  // planes within the blocks of at most max_threads threads, keeping a
+  // change that is at least 1% faster.
+  auto refine = [&](std::vector<LatHost> cur, float best, int max_threads) {
     std::vector<int> order(c->n_lat);
     for (int i = 0; i < c->n_lat; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
@@ -1691,7 +1676,7 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
         if (h.ty < 1 || h.tz < 1 || h.ty > h.L || h.tz > h.L || h.L % h.ty != 0 || h.L % h.tz != 0) continue;
         if (h.kind != kTileBlock && h.tz < 2) continue;
         if (h.tz > 32) continue;  // the range the per-launch search covers
-        if (h.threads() > std::min(kPersistentBlockThreads, kind_max_threads(c, h.kind)) || h.threads() < 32) continue;
+        if (h.threads() > std::min(max_threads, kind_max_threads(c, h.kind)) || h.threads() < 32) continue;
         if (h.nyt() * h.nzt() > h.part_cap || h.smem() > 200 * 1024) continue;
         std::vector<LatHost> cand = cur;
         cand[i] = h;
@@ -1702,6 +1687,41 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
         }
       }
     }
+    return cur;
+  };
+  if (!persistent) {
+    for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, 0, kind_end, c->max_block);
+    if (rc == XY_OK) {
+      const std::vector<LatHost> found = c->lat;
+      const std::vector<LatHost> cur = refine(found, time_set(found), c->max_block);
+      if (rc == XY_OK) c->lat = cur;
+    }
+  } else {
+    // One tile kind and one block size serve every lattice of a persistent
+    // launch (the block is as wide as the widest tile): for each kind (not
+    // the stream kind) and each cap on the tile's threads (64, 128, 256),
+    // take each lattice's best tile under the cap, then time the persistent
+    // launch itself with each set, keep the fastest and refine it.
+    const int kinds[4] = {kTileMarch, kTileBlock, kTileDirect, kTileAngle};
+    const int n_sets = 3 * (allow_angle ? 4 : 3);
+    std::vector<std::vector<LatHost>> sets(n_sets);
+    const std::vector<LatHost> start = c->lat;
+    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
+      const int kind = kinds[q / 3], cap = 64 << (q % 3);
+      c->lat = start;
+      for (int i = 0; i < c->n_lat && rc == XY_OK; ++i) search(i, kind, kind + 1, cap);
+      sets[q] = c->lat;
+    }
+    float best = 1e30f;
+    int best_q = n_sets - 1;
+    for (int q = 0; q < n_sets && rc == XY_OK; ++q) {
+      const float ms = time_set(sets[q]);
+      if (rc == XY_OK && ms < best) {
+        best = ms;
+        best_q = q;
+      }
+    }
+    const std::vector<LatHost> cur = refine(sets[best_q], best, kPersistentBlockThreads);
     if (rc == XY_OK) c->lat = cur;
   }
   cudaEventDestroy(e0);
