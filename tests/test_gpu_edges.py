@@ -96,12 +96,13 @@ def test_autotune_cache_reuses_tiles(tmp_path):
     assert len(xy.load_tile_cache(path)) == 2
 
 
-@pytest.mark.parametrize("mode", [0, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2])
 def test_autotune_leaves_the_state(mode):
-    """Autotuning runs trial sweeps (in persistent mode with an exchange at
-    every sweep's end) but restores the spins, the ladder's permutation and
-    couplings, and the counters and accept counts: the context then sweeps
-    exactly as a fresh one set to the tiles autotune chose."""
+    """Autotuning runs trial sweeps (whole sweeps with an exchange at every
+    sweep's end in each execution mode: plain launches, the CUDA graph,
+    persistent launches) but restores the spins, the ladder's permutation
+    and couplings, and the counters and accept counts: the context then
+    sweeps exactly as a fresh one set to the tiles autotune chose."""
     from paper_1211_0780_b300 import xy
     betas = [0.42, 0.44, 0.46, 0.48]
     a = xy.Simulation([16, 24], [4, 2], betas + [0.44, 0.45], 11, series_capacity=16)
