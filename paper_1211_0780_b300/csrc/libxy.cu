@@ -1586,10 +1586,10 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
             return r2;
           };
           if ((rc = run(1)) != XY_OK) break;
-          // the faster of two timed rounds (close candidates are otherwise
+          // the faster of two timed trials (close candidates are otherwise
           // ordered by timing noise)
           float ms = 1e30f;
-          for (int round = 0; round < 2 && rc == XY_OK; ++round) {
+          for (int trial = 0; trial < 2 && rc == XY_OK; ++trial) {
             if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = fail_cuda(c, cudaGetLastError(), "autotune"); break; }
             if ((rc = run(3)) != XY_OK) break;
             float t = 0.f;
@@ -1641,7 +1641,7 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
       return 1e30f;
     }
     float ms = 1e30f;
-    for (int round = 0; round < 2 && rc == XY_OK; ++round) {
+    for (int trial = 0; trial < 2 && rc == XY_OK; ++trial) {
       if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = fail_cuda(c, cudaGetLastError(), "autotune"); break; }
       if ((rc = two_sweeps()) != XY_OK) break;
       float t = 0.f;
