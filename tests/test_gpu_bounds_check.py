@@ -1,6 +1,7 @@
 """The bounds-checked debug build (libxy_check.so, XY_BOUNDS_CHECK): over
-every tile kind, lattice size class, execution mode, the measurement and the
-exchange, no spin access falls outside its slot (the status word stays 0, so
+every tile kind, lattice size class, execution mode, the measurement (every
+sum, or the energy alone on sweeps that only exchange) and the exchange, no
+spin access falls outside its slot (the status word stays 0, so
 no XY_ERR_BOUNDS) and the spins and records equal the release library's, bit
 for bit.  This is the project's stand-in for compute-sanitizer's memcheck on
 the sweep kernels."""
@@ -38,6 +39,9 @@ for i, (Ls, Rs, tiles) in enumerate(cases):
         s.set_exec(mode)
         s.sweep(1, 2, 3, measure_every=1, pt_swap_every=1)
         s.sweep(2, 0, 1, measure_every=1, pt_swap_every=1)
+        # exchanges without records: the energy-only measuring kernels
+        s.sweep(1, 2, 2, measure_every=0, pt_swap_every=1)
+        s.sweep(2, 0, 1, measure_every=0, pt_swap_every=1)
         assert s.device_status() == 0, (i, mode)
         out[f"{i}-{mode}-p"] = s.get_packed()
         out[f"{i}-{mode}-r"] = s.read_series()
