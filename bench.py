@@ -391,7 +391,9 @@ def bench_ragged(steps: int, warmup: int):
                                    "12 on angle storage and 24 on the (cos, sin) layout, weighted by each "
                                    "lattice's share of the updates (the 128^3 half-sweeps read exactly their "
                                    "bytes from DRAM: profiles/overrelax_L128x16_direct4x8_dram.md, "
-                                   "profiles/angle_L128x16_ncu.md)"}
+                                   "profiles/angle_L128x16_ncu.md; the angle-storage kernels of L = 96 and 128 "
+                                   "take two thirds of the kernel time: "
+                                   "profiles/ragged_L16-128x16_launch_list.md)"}
     return out
 
 
