@@ -647,7 +647,8 @@ def run_gpu(args):
         if kv.get("tile") == ",".join(str(v) for v in tile):
             traffic = int(kv["dram_bytes_per_launch"])
             l2_bytes = int(kv["l2_read_bytes_per_launch"]) if "l2_read_bytes_per_launch" in kv else None
-            traffic_note = (f"cold-cache ncu capture (profiles/overrelax_L160_{tile_name}_ncu.md): the whole "
+            traffic_note = (f"cold-cache ncu capture (profiles/overrelax_L160_{tile_name}_traffic.txt, "
+                            f"profiles/overrelax_L160_{tile_name}_ncu.md): the whole "
                             "(cos, sin) state read once, 8 B per site against the 4 B per site of the "
                             "12 B/update angle figure")
     roofline = {"bound": "hbm", "achieved": ach, "peak": hbm, "unit": "GB/s", "frac": ach / hbm,
