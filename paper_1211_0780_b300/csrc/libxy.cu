@@ -1616,19 +1616,21 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
   // context's execution mode.
   int swap_every = 0;
   for (const LatHost& h : c->lat) swap_every = h.R > 1 ? 1 : swap_every;
-  auto two_sweeps = [&]() -> int {
-    if (persistent) return persistent_sweeps(c, nM, nOR, 2, 0, swap_every);
+  // four sweeps: long enough that timing noise orders close sets rarely
+  constexpr int kTrialSweeps = 4;
+  auto trial_sweeps = [&]() -> int {
+    if (persistent) return persistent_sweeps(c, nM, nOR, kTrialSweeps, 0, swap_every);
     if (exec == XY_EXEC_GRAPH) {
       c->exec = XY_EXEC_GRAPH;
-      const int r = xy_sweep(c, nM, nOR, 2, 0, swap_every);
+      const int r = xy_sweep(c, nM, nOR, kTrialSweeps, 0, swap_every);
       c->exec = XY_EXEC_PLAIN;
       return r;
     }
-    return issue_sweeps(c, c->stream, nM, nOR, 2, 0, swap_every, c->h_ctr[kCtrSweep], nullptr);
+    return issue_sweeps(c, c->stream, nM, nOR, kTrialSweeps, 0, swap_every, c->h_ctr[kCtrSweep], nullptr);
   };
-  // Time of two sweeps with a set of tiles: an untimed call first (it
+  // Time of a few sweeps with a set of tiles: an untimed call first (it
   // builds the call's graph: capture and instantiation are host work that
-  // would otherwise fall inside the timed region), then the faster of two
+  // would otherwise fall inside the timed region), then the fastest of three
   // timed calls; 1e30 for a set the execution mode cannot run.
   auto time_set = [&](const std::vector<LatHost>& set) -> float {
     c->lat = set;
@@ -1636,14 +1638,14 @@ int xy_autotune(xy_ctx* c, int nM, int nOR) {
     if (rc != XY_OK) return 1e30f;
     drop_graphs(c);
     if ((rc = sync_lats(c)) != XY_OK) return 1e30f;
-    if (two_sweeps() != XY_OK) {
+    if (trial_sweeps() != XY_OK) {
       rc = c->sticky;
       return 1e30f;
     }
     float ms = 1e30f;
-    for (int trial = 0; trial < 2 && rc == XY_OK; ++trial) {
+    for (int trial = 0; trial < 3 && rc == XY_OK; ++trial) {
       if (cudaEventRecord(e0, c->stream) != cudaSuccess) { rc = fail_cuda(c, cudaGetLastError(), "autotune"); break; }
-      if ((rc = two_sweeps()) != XY_OK) break;
+      if ((rc = trial_sweeps()) != XY_OK) break;
       float t = 0.f;
       if (cudaEventRecord(e1, c->stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
           cudaEventElapsedTime(&t, e0, e1) != cudaSuccess) {
