@@ -135,8 +135,8 @@ def test_readme_usage_runs():
     L, R = 16, 4
     betas = np.linspace(0.450, 0.458, R)
     sim = xy.Simulation(L, R, betas, seed=0x5EED2012)
-    sim.autotune(1, 3)
     sim.set_exec(xy.EXEC_GRAPH)
+    sim.autotune(1, 3)
     sim.sweep(1, 3, 20, measure_every=1, pt_swap_every=1)
     rec = sim.read_series()
     assert len(rec) == 20 * R
